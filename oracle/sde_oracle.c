@@ -1,0 +1,961 @@
+/*
+ * sde_oracle.c -- plain FP64 CPU oracle of the jump-SDE proton transport of
+ * arXiv 2511.03115 (Sec. 2.1, Eq. VSDE and the parameterisations of
+ * Secs. 2.1.3-2.1.5, scoring of Sec. 2.2.2).
+ *
+ * TEST INFRASTRUCTURE ONLY: this code checks the CUDA path and is never part
+ * of it.  Slow on purpose: every step evaluates the printed formulas directly
+ * in double precision, element by element; there are no tables, no fusion and
+ * no reordering beyond what the paper states.
+ *
+ * What pins each part (tests/test_oracle_*.py):
+ *   Philox4x32-10 ............ published known-answer vectors (Salmon et al.
+ *                              2011, Random123 distribution), golden file
+ *   varsigma_1 (Bethe) ....... NIST PSTAR / ICRU 49 water stopping powers and
+ *                              CSDA ranges (golden file, 1-2 %: no corrections)
+ *   varsigma_2 ............... Bohr's low-energy limit 0.1569 Z/A rho MeV^2/cm
+ *   sigma(E) Lynch-Dahl ...... Highland formula within its stated 11 %
+ *   Rutherford rate/sampler .. textbook Rutherford in E_cm and sin(theta/2)
+ *   Mott (hydrogen) .......... textbook spin-1/2 Mott formula; antiderivative
+ *                              against quadrature of the cross section
+ *   CM -> lab ................ explicit Lorentz boost of four-vectors; the
+ *                              non-relativistic limit tan = sin/(cos + 1/A)
+ *   Kalbach-Mann sampler ..... KS test against the CDF of the printed pdf
+ *   Euler step ............... mean loss = varsigma_1 Delta exactly, clamped
+ *                              Gaussian variance closed form, E[cos] = e^-t,
+ *                              jump probability 1 - exp(-Delta sigma)
+ *   CSDA quadrature .......... independent quadrature; deterministic Euler
+ *                              track converges to it at first order
+ *   energy balance ........... exact integer identity every run
+ *   non-elastic rate ......... PARITY UNPINNED beyond the ~1 %/cm water
+ *                              fluence-loss rate: the ENDF data the paper uses
+ *                              is not available, a named public
+ *                              parameterisation stands in (see below).
+ *
+ * Readings of passages that are silent, garbled or inconsistent are marked
+ * "Reading:" beside the code.
+ */
+#include "sde_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+/* ---------------------------------------------------------------- constants
+ * CODATA 2018 values (MeV, cm, fm). */
+#define OR_MP 938.27208816          /* proton rest energy, MeV */
+#define OR_ME 0.51099895000         /* electron rest energy, MeV */
+#define OR_AMU 931.49410242         /* atomic mass unit, MeV */
+#define OR_NA 6.02214076e23         /* Avogadro, 1/mol */
+#define OR_ALPHA (1.0 / 137.035999084)
+#define OR_HBARC_FM 197.3269804     /* MeV fm */
+#define OR_HBARC_CM 1.973269804e-11 /* MeV cm */
+#define OR_MEV_J 1.602176634e-13
+#define OR_PI 3.14159265358979323846
+
+static __thread char g_err[256];
+static int g_threads = 0;
+
+static int fail(int code, const char* msg) {
+    snprintf(g_err, sizeof g_err, "%s", msg);
+    return code;
+}
+const char* oracle_last_error(void) { return g_err; }
+int oracle_set_threads(int n) {
+    g_threads = n > 0 ? n : 0;
+    return 0;
+}
+
+/* --------------------------------------------------------- element data
+ * Z, standard atomic weight A (g/mol, IUPAC), mean excitation energy I (eV).
+ * Reading (Sec. 2.1.3 uses one I per medium; Bragg additivity of ln I is the
+ * requested construction when the medium's I is not given): I_i are the
+ * ICRU Report 37 values for constituents of condensed compounds for H, C, N,
+ * O, F, Cl and the elemental ICRU 37 values for the others.  With them,
+ * water comes out at 75.3 eV. */
+typedef struct {
+    int Z;
+    double A;
+    double I;
+} or_elem;
+
+static const or_elem k_elems[] = {
+    {1, 1.008, 19.2},    {2, 4.002602, 41.8}, {6, 12.011, 81.0},   {7, 14.007, 82.0},
+    {8, 15.999, 106.0},  {9, 18.998403, 112.0}, {11, 22.989769, 149.0}, {12, 24.305, 156.0},
+    {13, 26.981538, 166.0}, {14, 28.085, 173.0}, {15, 30.973762, 173.0}, {16, 32.06, 180.0},
+    {17, 35.45, 180.0},  {18, 39.948, 188.0}, {19, 39.0983, 190.0}, {20, 40.078, 191.0},
+    {22, 47.867, 233.0}, {26, 55.845, 286.0}, {29, 63.546, 322.0}, {30, 65.38, 330.0},
+};
+
+int oracle_element(int Z, double* A, double* I_eV) {
+    for (size_t i = 0; i < sizeof k_elems / sizeof k_elems[0]; ++i)
+        if (k_elems[i].Z == Z) {
+            if (A) *A = k_elems[i].A;
+            if (I_eV) *I_eV = k_elems[i].I;
+            return ORACLE_OK;
+        }
+    return fail(ORACLE_EINVAL, "element not in the oracle's table");
+}
+
+/* A material resolved against the element table. */
+typedef struct {
+    int n;
+    int Z[ORACLE_MAX_EL];
+    double A[ORACLE_MAX_EL];
+    double w[ORACLE_MAX_EL];
+    double I_MeV;
+} or_mat;
+
+static int resolve_material(const oracle_material* m, or_mat* out) {
+    if (!m || !m->el || m->n_el <= 0 || m->n_el > ORACLE_MAX_EL)
+        return fail(ORACLE_EINVAL, "material needs 1..16 elements");
+    double wsum = 0.0, num = 0.0, den = 0.0;
+    out->n = m->n_el;
+    for (int i = 0; i < m->n_el; ++i) {
+        double A, I;
+        if (oracle_element(m->el[i].Z, &A, &I) != ORACLE_OK) return ORACLE_EINVAL;
+        if (!(m->el[i].mass_fraction > 0.0)) return fail(ORACLE_EINVAL, "mass fraction <= 0");
+        out->Z[i] = m->el[i].Z;
+        out->A[i] = A;
+        out->w[i] = m->el[i].mass_fraction;
+        wsum += m->el[i].mass_fraction;
+        /* Bragg additivity of ln I weighted by electron density w_i Z_i / A_i */
+        num += out->w[i] * out->Z[i] / A * log(I);
+        den += out->w[i] * out->Z[i] / A;
+    }
+    /* Reading: mass fractions are renormalised to sum to one. */
+    for (int i = 0; i < out->n; ++i) out->w[i] /= wsum;
+    out->I_MeV = (m->I_eV > 0.0 ? m->I_eV : exp(num / den)) * 1e-6;
+    return ORACLE_OK;
+}
+
+/* ----------------------------------------------------------- Philox4x32-10
+ * Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+ * SC'11: ten rounds of two 32x32->64 multiplies with a Weyl key schedule. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* Stream layout: counter = (step index n, stream tag, history lo, history hi),
+ * key = (seed lo, seed hi).  Each 32-bit word becomes a uniform in (0,1). */
+enum { TAG_STEP = 0, TAG_JUMP_A = 1, TAG_JUMP_B = 2, TAG_SRC_A = 3, TAG_SRC_B = 4, TAG_BERN = 5 };
+
+static void draw4(uint64_t seed, uint64_t h, uint32_t n, uint32_t tag, double U[4]) {
+    uint32_t ctr[4] = {n, tag, (uint32_t)h, (uint32_t)(h >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    oracle_philox4x32_10(ctr, key, x);
+    for (int i = 0; i < 4; ++i) U[i] = ((double)x[i] + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* ------------------------------------------------------------ kinematics */
+static double beta2_of(double E) { return (2.0 * OR_MP + E) * E / ((OR_MP + E) * (OR_MP + E)); }
+
+static double target_mass(int Z, double A) { return Z == 1 ? OR_MP : A * OR_AMU; }
+
+/* Sec. 2.1.4 (large-angle elastic): Sommerfeld parameter eta = Z alpha c/v and
+ * wave number k = mu_red v / hbar of the two-body Coulomb problem.
+ * Reading: the printed prefactors (x1e-26, x1e6) are unit conversions; the
+ * physical definitions are used, non-relativistic as in the ENDF Coulomb
+ * formulae, with the reduced mass from the target mass. */
+int oracle_coulomb_eta_k(int Z, double E, double* eta, double* k_fm) {
+    double A;
+    if (oracle_element(Z, &A, NULL) != ORACLE_OK) return ORACLE_EINVAL;
+    double m2 = target_mass(Z, A);
+    double v = sqrt(2.0 * E / OR_MP); /* v/c */
+    double mu_red = OR_MP * m2 / (OR_MP + m2);
+    *eta = Z * OR_ALPHA / v;
+    *k_fm = mu_red * v / OR_HBARC_FM;
+    return ORACLE_OK;
+}
+
+/* CM Rutherford, electronic screening ignored: eta^2 / (k^2 (1-mu)^2), fm^2/sr. */
+double oracle_rutherford_dsigma(double mu, double eta, double k_fm) {
+    double r = eta / k_fm;
+    return r * r / ((1.0 - mu) * (1.0 - mu));
+}
+
+/* Identical-particle (Mott) Coulomb term for hydrogen, fm^2/sr. */
+double oracle_mott_dsigma(double mu, double eta, double k_fm) {
+    double r = eta / k_fm;
+    double om2 = 1.0 - mu * mu;
+    return 2.0 * r * r / om2 *
+           ((1.0 + mu * mu) / om2 - 0.5 * cos(eta * log((1.0 + mu) / (1.0 - mu))));
+}
+
+/* Antiderivative of the Mott term in units of (eta/k)^2 (Appendix A.2).
+ * Reading: the printed second term carries sin(2 eta ln((1+mu)/(1-mu)));
+ * differentiating shows the argument is eta ln((1+mu)/(1-mu)) with the
+ * prefactor -1/(2 eta) (after dividing by (eta/k)^2). */
+double oracle_mott_antiderivative(double mu, double eta) {
+    double L = log((1.0 + mu) / (1.0 - mu));
+    double s = eta > 0.0 ? sin(eta * L) / (2.0 * eta) : 0.5 * L;
+    return 2.0 * mu / (1.0 - mu * mu) - s;
+}
+
+/* Inverse CDF of the Rutherford law on [-1, mu_c]:
+ * F(mu) = (1/(1-mu) - 1/2) / (1/(1-mu_c) - 1/2). */
+double oracle_sample_mu_rutherford(double U, double mu_c) {
+    double y = 0.5 + U * (1.0 / (1.0 - mu_c) - 0.5);
+    return 1.0 - 1.0 / y;
+}
+
+/* Inverse CDF of the Mott law on [mu_lo, mu_c] by bisection of the closed-form
+ * antiderivative (Eq. large_elastic_cdf with the Appendix A.2 integral). */
+double oracle_sample_mu_mott(double U, double eta, double mu_lo, double mu_c) {
+    double g0 = oracle_mott_antiderivative(mu_lo, eta);
+    double g1 = oracle_mott_antiderivative(mu_c, eta);
+    double target = g0 + U * (g1 - g0);
+    double lo = mu_lo, hi = mu_c;
+    for (int it = 0; it < 200 && hi - lo > 1e-15; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (oracle_mott_antiderivative(mid, eta) < target)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Kalbach-Mann angular law pi_ne(mu|E,u) = a/(2 sinh a) (cosh(a mu) + r sinh(a mu)).
+ * Reading: the printed inverse gives T = exp(a mu), not mu; integrating the pdf
+ * yields (1+r) T^2 - 2 C T - (1-r) = 0 with C as printed, so mu = ln(T)/a. */
+double oracle_sample_mu_kalbach(double U, double a, double r) {
+    if (a < 1e-4) return 2.0 * U - 1.0; /* a -> 0: the law tends to uniform */
+    double C = 2.0 * sinh(a) * U + r * cosh(a) - sinh(a);
+    double T = (C + sqrt(C * C + 1.0 - r * r)) / (1.0 + r);
+    double mu = log(T) / a;
+    return mu < -1.0 ? -1.0 : (mu > 1.0 ? 1.0 : mu);
+}
+
+/* Kalbach's slope parameter a (Kalbach 1988 systematics, the formula of the
+ * ENDF-6 manual Sec. 6.2.3 for incident and emitted protons).
+ * Reading: ENDF's tabulated data are unavailable; separation energies are
+ * neglected, e_a = E m2/(m_p+m2) and e_b = (1-u) e_a. */
+double oracle_kalbach_a(double E, double u, double A) {
+    double m2 = A * OR_AMU;
+    double ea = E * m2 / (OR_MP + m2);
+    double eb = (1.0 - u) * ea;
+    double R1 = ea < 130.0 ? ea : 130.0;
+    double R3 = ea < 41.0 ? ea : 41.0;
+    double X1 = R1 * eb / ea, X3 = R3 * eb / ea;
+    return 0.04 * X1 + 1.8e-6 * X1 * X1 * X1 + 6.7e-7 * X3 * X3 * X3 * X3;
+}
+
+/* Appendix A.1: lab polar angle from the CM angle for a proton of lab kinetic
+ * energy E_in on a target of mass m2; E_out is the outgoing lab kinetic energy
+ * (E_out = E_in for elastic scattering).  Reading: v'_1C of the printed
+ * collinear Lorentz transformation is used as a speed (its magnitude). */
+double oracle_cm_to_lab(double E_in, double E_out, double m2, double cos_cm) {
+    double E1 = E_in + OR_MP;
+    double p1 = sqrt(E1 * E1 - OR_MP * OR_MP);
+    double ucm = p1 / (E1 + m2);
+    double gu = 1.0 / sqrt(1.0 - ucm * ucm);
+    double E1o = E_out + OR_MP;
+    double p1o = sqrt(fmax(E1o * E1o - OR_MP * OR_MP, 0.0));
+    double vc = fabs((p1o - ucm * E1o) / (E1o - ucm * p1o));
+    double sin_cm = sqrt(fmax(0.0, 1.0 - cos_cm * cos_cm));
+    return atan2(vc * sin_cm, gu * (vc * cos_cm + ucm));
+}
+
+/* Non-elastic p-nucleus cross section, mb.
+ * PARITY UNPINNED: the ENDF/B-VIII.1 and JEFF-4.0 tables of Sec. 2.1.5 are not
+ * available.  Stand-in: Letaw, Silberberg & Tsao (ApJS 51, 271, 1983)
+ * sigma = 45 A^0.7 [1 + 0.016 sin(5.3 - 2.63 ln A)] [1 - 0.62 e^{-E/200}
+ * sin(10.9 E^-0.28)] mb, times a classical Coulomb-barrier factor
+ * (1 - B/E_cm)_+ with B = Z e^2 / (1.3 fm (A^1/3 + 1)); zero for hydrogen
+ * (no p-p non-elastic channel below the pion threshold). */
+double oracle_sigma_ne_element_mb(int Z, double E) {
+    double A;
+    if (Z == 1 || oracle_element(Z, &A, NULL) != ORACLE_OK) return 0.0;
+    double lnA = log(A);
+    double s_he = 45.0 * pow(A, 0.7) * (1.0 + 0.016 * sin(5.3 - 2.63 * lnA));
+    double f = 1.0 - 0.62 * exp(-E / 200.0) * sin(10.9 * pow(E, -0.28));
+    double m2 = A * OR_AMU;
+    double ecm = E * m2 / (OR_MP + m2);
+    double B = Z * OR_ALPHA * OR_HBARC_FM / (1.3 * (cbrt(A) + 1.0));
+    double bar = ecm > B ? 1.0 - B / ecm : 0.0;
+    return s_he * f * bar;
+}
+
+/* ------------------------------------------------- physics of one medium */
+static void physics_eval(const or_mat* m, double rho, const oracle_params* p, double E,
+                         oracle_physics_out* o) {
+    memset(o, 0, sizeof *o);
+    double b2 = beta2_of(E);
+    double gam = (E + OR_MP) / OR_MP;
+    double pm = sqrt(E * (E + 2.0 * OR_MP));
+    double pbeta = pm * pm / (E + OR_MP);
+    o->beta2 = b2;
+    o->gamma = gam;
+    o->p_MeV = pm;
+    o->I_eV = m->I_MeV * 1e6;
+    o->n_el = m->n;
+
+    /* Eq. BraggAditivty: varsigma_1 = K sum_i Z_i rho_i / (A_i beta^2) (ln(2 m_e c^2 beta^2 /
+     * (I (1-beta^2))) - beta^2), one I for the medium. */
+    double log_term = log(2.0 * OR_ME * b2 / (m->I_MeV * (1.0 - b2))) - b2;
+    double s1 = 0.0, s2 = 0.0;
+    double ahc = OR_ALPHA * OR_HBARC_CM;
+    for (int i = 0; i < m->n; ++i) {
+        double rho_i = m->w[i] * rho;
+        s1 += p->K * m->Z[i] * rho_i / (m->A[i] * b2) * log_term;
+        /* Eq. energystraggling with Bragg additivity */
+        s2 += 4.0 * OR_PI * OR_NA * m->Z[i] * rho_i / m->A[i] * ahc * ahc * (gam * gam * (1.0 - 0.5 * b2));
+    }
+    o->s1 = s1;
+    o->s2sq = s2;
+
+    /* Lynch-Dahl (Sec. 2.1.4): chi_c^2 summed over elements; ln chi_alpha^2
+     * averaged with weights Z_i (Z_i+1)/A_i.  Reading: the weights also carry
+     * the mass fraction w_i (the element's share of the path's mass
+     * thickness), as in Lynch & Dahl's compound rule. */
+    double z = p->msc_z_cm;
+    double chic2 = 0.0, num = 0.0, den = 0.0;
+    for (int i = 0; i < m->n; ++i) {
+        double Zi = m->Z[i];
+        double rho_i = m->w[i] * rho;
+        chic2 += 0.157 * Zi * (Zi + 1.0) * rho_i * z / (m->A[i] * pbeta * pbeta);
+        double za = Zi * OR_ALPHA;
+        double chia2_i = 2.007e-5 * pow(Zi, 2.0 / 3.0) * (1.0 + 3.34 * za * za / b2) / (pm * pm);
+        double wt = m->w[i] * Zi * (Zi + 1.0) / m->A[i];
+        num += wt * log(chia2_i);
+        den += wt;
+    }
+    double chia2 = exp(num / den);
+    o->chi_c2 = chic2;
+    o->chi_a2 = chia2;
+    if (chic2 > 0.0) {
+        double F = p->F;
+        double w = chic2 / (2.0 * chia2 * (1.0 - F));
+        double sig2 = chic2 / (1.0 + F * F) * ((1.0 + w) / w * log1p(w) - 1.0);
+        o->w = w;
+        o->sigma_msc = sqrt(sig2);
+        /* m = sigma/sqrt(z); Brownian time over one step: m^2 Delta */
+        o->t_sbm = sig2 * p->step_cm / z;
+    }
+
+    /* Eq. large_elastic_cm (non-H, Rutherford part) and
+     * Eq. large_elastic_cm_hydrogen (Mott part): rate per cm. */
+    double mu_c = cos(p->theta_cut_rad);
+    double mu_lo = -cos(p->backscatter_rad); /* -1 + delta, delta = 1 + cos(pi - theta_b) */
+    for (int i = 0; i < m->n; ++i) {
+        double n_i = OR_NA * m->w[i] * rho / m->A[i]; /* atoms per cm^3 */
+        double eta, k;
+        oracle_coulomb_eta_k(m->Z[i], E, &eta, &k);
+        double r2_cm2 = (eta / k) * (eta / k) * 1e-26; /* fm^2 -> cm^2 */
+        double integ;
+        if (m->Z[i] == 1)
+            integ = oracle_mott_antiderivative(mu_c, eta) - oracle_mott_antiderivative(mu_lo, eta);
+        else
+            integ = 1.0 / (1.0 - mu_c) - 0.5;
+        double se = (p->physics_mask & ORACLE_PHYS_ELASTIC) ? n_i * 2.0 * OR_PI * r2_cm2 * integ : 0.0;
+        double sne = (p->physics_mask & ORACLE_PHYS_INELASTIC)
+                         ? n_i * oracle_sigma_ne_element_mb(m->Z[i], E) * 1e-27
+                         : 0.0;
+        o->sig_e_el[i] = se;
+        o->sig_ne_el[i] = sne;
+        o->sig_e += se;
+        o->sig_ne += sne;
+    }
+}
+
+int oracle_physics(const oracle_material* mat, double rho, const oracle_params* p, double E,
+                   oracle_physics_out* out) {
+    or_mat m;
+    if (!p || !out || !(E > 0.0) || !(rho >= 0.0)) return fail(ORACLE_EINVAL, "bad physics args");
+    int rc = resolve_material(mat, &m);
+    if (rc) return rc;
+    physics_eval(&m, rho, p, E, out);
+    return ORACLE_OK;
+}
+
+/* CSDA range: integral of 1/varsigma_1 over [e_min, E0] by adaptive Simpson
+ * in ln E (tolerance 1e-12 relative). */
+static double inv_s1_lnE(const or_mat* m, double rho, const oracle_params* p, double lnE) {
+    oracle_physics_out o;
+    double E = exp(lnE);
+    physics_eval(m, rho, p, E, &o);
+    return E / o.s1;
+}
+static double simpson_rec(const or_mat* m, double rho, const oracle_params* p, double a, double b,
+                          double fa, double fm, double fb, double whole, double tol, int depth) {
+    double c = 0.5 * (a + b), l = 0.5 * (a + c), r = 0.5 * (c + b);
+    double fl = inv_s1_lnE(m, rho, p, l), fr = inv_s1_lnE(m, rho, p, r);
+    double left = (c - a) / 6.0 * (fa + 4.0 * fl + fm);
+    double right = (b - c) / 6.0 * (fm + 4.0 * fr + fb);
+    if (depth <= 0 || fabs(left + right - whole) <= 15.0 * tol)
+        return left + right + (left + right - whole) / 15.0;
+    return simpson_rec(m, rho, p, a, c, fa, fl, fm, left, 0.5 * tol, depth - 1) +
+           simpson_rec(m, rho, p, c, b, fm, fr, fb, right, 0.5 * tol, depth - 1);
+}
+int oracle_csda_range(const oracle_material* mat, double rho, const oracle_params* p, double E0,
+                      double* range_cm) {
+    or_mat m;
+    int rc = resolve_material(mat, &m);
+    if (rc) return rc;
+    if (!(E0 > p->e_min_MeV) || !(rho > 0.0)) return fail(ORACLE_EINVAL, "bad CSDA args");
+    double a = log(p->e_min_MeV), b = log(E0);
+    double fa = inv_s1_lnE(&m, rho, p, a), fb = inv_s1_lnE(&m, rho, p, b);
+    double fm = inv_s1_lnE(&m, rho, p, 0.5 * (a + b));
+    double whole = (b - a) / 6.0 * (fa + 4.0 * fm + fb);
+    *range_cm = simpson_rec(&m, rho, p, a, b, fa, fm, fb, whole, 1e-13 * whole, 40);
+    return ORACLE_OK;
+}
+
+/* -------------------------------------------------------- direction maths
+ * Orthonormal basis (e1, e2) perpendicular to a unit vector, the branch-free
+ * construction of Duff et al., "Building an orthonormal basis, revisited",
+ * JCGT 6(1), 2017.  Rotating by polar angle theta and azimuth phi about it. */
+static void rotate_dir(double u[3], double cos_t, double sin_t, double phi) {
+    double x = u[0], y = u[1], z = u[2];
+    double s = copysign(1.0, z);
+    double a = -1.0 / (s + z);
+    double b = x * y * a;
+    double e1[3] = {1.0 + s * x * x * a, s * b, -s * x};
+    double e2[3] = {b, s + y * y * a, -y};
+    double cp = cos(phi), sp = sin(phi);
+    for (int i = 0; i < 3; ++i) u[i] = cos_t * u[i] + sin_t * (cp * e1[i] + sp * e2[i]);
+    double nrm = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int i = 0; i < 3; ++i) u[i] /= nrm;
+}
+
+/* ------------------------------------------------------------ the dose grid */
+struct oracle_dose {
+    int nx, ny, nz;
+    double h[3], o[3];
+    float* rho;
+    uint8_t* mid;
+    int n_mats;
+    or_mat* mats;
+    oracle_params p;
+    uint64_t* edep;
+    oracle_balance bal;
+};
+
+void oracle_default_params(oracle_params* p) {
+    p->step_cm = 0.05;
+    p->msc_z_cm = 0.05;
+    p->F = 0.98;
+    p->theta_cut_rad = 0.02;
+    p->backscatter_rad = 0.04;
+    p->e_min_MeV = 0.05;
+    p->K = 0.3072;
+    p->inel_u_lo = 0.0;
+    p->inel_u_hi = 1.0;
+    p->km_r = 0.5;
+    p->tally_mode = 0;
+    p->fixed_point_shift = 24;
+    p->jump_clock = 0;
+    p->max_steps = 100000;
+    p->physics_mask = ORACLE_PHYS_ALL;
+}
+
+static int check_params(const oracle_params* p) {
+    if (!(p->step_cm > 0.0) || !(p->msc_z_cm > 0.0) || !(p->F > 0.0 && p->F < 1.0) ||
+        !(p->theta_cut_rad > 0.0 && p->theta_cut_rad < 3.0) ||
+        !(p->backscatter_rad > 0.0 && p->backscatter_rad < 1.5) || !(p->e_min_MeV > 0.0) ||
+        !(p->K > 0.0) || !(p->inel_u_lo >= 0.0 && p->inel_u_hi <= 1.0 && p->inel_u_lo <= p->inel_u_hi) ||
+        !(p->km_r >= 0.0 && p->km_r < 1.0) || (p->tally_mode != 0 && p->tally_mode != 1) ||
+        p->fixed_point_shift < 0 || p->fixed_point_shift > 30 || p->max_steps <= 0 ||
+        (p->jump_clock != 0 && p->jump_clock != 1) || p->physics_mask < 0 || p->physics_mask > 15)
+        return fail(ORACLE_EINVAL, "invalid parameters");
+    return ORACLE_OK;
+}
+
+int oracle_create(oracle_dose** out, int nx, int ny, int nz, const double voxel_mm[3],
+                  const double origin_mm[3], const float* density, const uint8_t* material_id,
+                  const oracle_material* mats, int n_mats, const oracle_params* p) {
+    if (!out || nx <= 0 || ny <= 0 || nz <= 0 || !voxel_mm || !origin_mm || !density ||
+        !material_id || !mats || n_mats <= 0 || n_mats > 256)
+        return fail(ORACLE_EINVAL, "bad create arguments");
+    oracle_params prm;
+    if (p)
+        prm = *p;
+    else
+        oracle_default_params(&prm);
+    if (check_params(&prm)) return ORACLE_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(voxel_mm[a] > 0.0)) return fail(ORACLE_EINVAL, "voxel size must be > 0");
+    size_t nv = (size_t)nx * ny * nz;
+    for (size_t v = 0; v < nv; ++v) {
+        if (material_id[v] >= n_mats) return fail(ORACLE_EINVAL, "material id out of range");
+        if (!(density[v] >= 0.0f) || !(density[v] < 1e3f)) return fail(ORACLE_EINVAL, "bad density");
+    }
+    oracle_dose* d = (oracle_dose*)calloc(1, sizeof *d);
+    if (!d) return fail(ORACLE_ENOMEM, "out of memory");
+    d->nx = nx;
+    d->ny = ny;
+    d->nz = nz;
+    for (int a = 0; a < 3; ++a) {
+        d->h[a] = voxel_mm[a];
+        d->o[a] = origin_mm[a];
+    }
+    d->p = prm;
+    d->rho = (float*)malloc(nv * sizeof(float));
+    d->mid = (uint8_t*)malloc(nv);
+    d->edep = (uint64_t*)calloc(nv, sizeof(uint64_t));
+    d->mats = (or_mat*)calloc((size_t)n_mats, sizeof(or_mat));
+    d->n_mats = n_mats;
+    if (!d->rho || !d->mid || !d->edep || !d->mats) {
+        oracle_destroy(d);
+        return fail(ORACLE_ENOMEM, "out of memory");
+    }
+    memcpy(d->rho, density, nv * sizeof(float));
+    memcpy(d->mid, material_id, nv);
+    for (int i = 0; i < n_mats; ++i) {
+        int rc = resolve_material(&mats[i], &d->mats[i]);
+        if (rc) {
+            oracle_destroy(d);
+            return rc;
+        }
+    }
+    *out = d;
+    return ORACLE_OK;
+}
+
+void oracle_destroy(oracle_dose* d) {
+    if (!d) return;
+    free(d->rho);
+    free(d->mid);
+    free(d->edep);
+    free(d->mats);
+    free(d);
+}
+
+int oracle_reset(oracle_dose* d) {
+    if (!d) return fail(ORACLE_EINVAL, "null handle");
+    memset(d->edep, 0, (size_t)d->nx * d->ny * d->nz * sizeof(uint64_t));
+    memset(&d->bal, 0, sizeof d->bal);
+    return ORACLE_OK;
+}
+
+/* Voxel containing a point (mm).  Reading: floor convention; a point with a
+ * coordinate below the origin or at/after origin + n h lies outside D. */
+static long voxel_of(const oracle_dose* d, const double r[3]) {
+    int n[3] = {d->nx, d->ny, d->nz};
+    long idx[3];
+    for (int a = 0; a < 3; ++a) {
+        double f = floor((r[a] - d->o[a]) / d->h[a]);
+        if (f < 0.0 || f >= (double)n[a]) return -1;
+        idx[a] = (long)f;
+    }
+    return idx[0] + (long)d->nx * (idx[1] + (long)d->ny * idx[2]);
+}
+
+/* Fixed-point energy: one unit is 2^-S MeV. */
+static uint64_t Q(const oracle_dose* d, double E) {
+    return (uint64_t)llround(ldexp(E, d->p.fixed_point_shift));
+}
+
+typedef struct {
+    uint64_t* edep;
+    oracle_balance bal;
+    int error;
+} or_acc;
+
+static void deposit_at(or_acc* acc, long v, uint64_t q) {
+    if (q == 0) return;
+    if (v < 0)
+        acc->bal.escaped += q;
+    else {
+        acc->edep[v] += q;
+        acc->bal.deposited += q;
+    }
+}
+
+/* Split q along the chord a -> b (mm) in proportion to the length inside each
+ * voxel.  Independent construction: every crossing of a voxel plane is listed,
+ * the crossings are sorted, and each piece is assigned by its midpoint. */
+static int cmp_double(const void* x, const void* y) {
+    double a = *(const double*)x, b = *(const double*)y;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+static void deposit_chord(const oracle_dose* d, or_acc* acc, const double a[3], const double b[3],
+                          uint64_t q) {
+    if (q == 0) return;
+    double ts[64];
+    int nt = 0;
+    int n[3] = {d->nx, d->ny, d->nz};
+    ts[nt++] = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        double da = b[ax] - a[ax];
+        if (da == 0.0) continue;
+        double lo = fmin(a[ax], b[ax]), hi = fmax(a[ax], b[ax]);
+        long k0 = (long)ceil((lo - d->o[ax]) / d->h[ax]);
+        long k1 = (long)floor((hi - d->o[ax]) / d->h[ax]);
+        if (k0 < -1) k0 = -1;
+        if (k1 > n[ax] + 1) k1 = n[ax] + 1;
+        for (long k = k0; k <= k1 && nt < 62; ++k) {
+            double t = (d->o[ax] + k * d->h[ax] - a[ax]) / da;
+            if (t > 0.0 && t < 1.0) ts[nt++] = t;
+        }
+    }
+    ts[nt++] = 1.0;
+    qsort(ts, (size_t)nt, sizeof(double), cmp_double);
+    uint64_t done = 0;
+    for (int j = 0; j + 1 < nt; ++j) {
+        double t1 = ts[j + 1];
+        uint64_t upto = (j + 2 == nt) ? q : (uint64_t)llround((double)q * t1);
+        if (upto < done) upto = done;
+        uint64_t part = upto - done;
+        done = upto;
+        double tm = 0.5 * (ts[j] + t1), m[3];
+        for (int ax = 0; ax < 3; ++ax) m[ax] = a[ax] + tm * (b[ax] - a[ax]);
+        deposit_at(acc, voxel_of(d, m), part);
+    }
+}
+
+/* Source sampling at the spot (Sec. 2.2.2 beam; general Gaussian spot). */
+static void sample_source(const oracle_dose* d, const oracle_spot* s, uint64_t seed, uint64_t h,
+                          double* E, double r[3], double u[3], double* tau) {
+    double A[4], B[4];
+    draw4(seed, h, 0u, TAG_SRC_A, A);
+    draw4(seed, h, 0u, TAG_SRC_B, B);
+    double rr = sqrt(-2.0 * log(A[0]));
+    double g1 = rr * cos(2.0 * OR_PI * A[1]), g2 = rr * sin(2.0 * OR_PI * A[1]);
+    double g3 = sqrt(-2.0 * log(A[2])) * cos(2.0 * OR_PI * A[3]);
+    double e = s->E_MeV + s->sigma_E_MeV * g3;
+    if (e < d->p.e_min_MeV) e = d->p.e_min_MeV;
+    *E = e;
+    double nrm = sqrt(s->ux * s->ux + s->uy * s->uy + s->uz * s->uz);
+    u[0] = s->ux / nrm;
+    u[1] = s->uy / nrm;
+    u[2] = s->uz / nrm;
+    /* lateral offset in the plane perpendicular to the spot direction */
+    double x = u[0], y = u[1], z = u[2];
+    double sg = copysign(1.0, z);
+    double a = -1.0 / (sg + z);
+    double b = x * y * a;
+    double e1[3] = {1.0 + sg * x * x * a, sg * b, -sg * x};
+    double e2[3] = {b, sg + y * y * a, -y};
+    double pos[3] = {s->x_mm, s->y_mm, s->z_mm};
+    for (int i = 0; i < 3; ++i) r[i] = pos[i] + s->sigma_xy_mm * (g1 * e1[i] + g2 * e2[i]);
+    if (s->sigma_angle_rad > 0.0) {
+        double th = s->sigma_angle_rad * sqrt(-2.0 * log(B[0]));
+        rotate_dir(u, cos(th), sin(th), 2.0 * OR_PI * B[1]);
+    }
+    *tau = -log(B[2]);
+}
+
+/* One Euler-Maruyama step of Eq. VSDE from Y_n = (E, r, u) in a medium with
+ * resolved composition m and density rho.  On return: E1 = energy after the
+ * continuous loss, *E = energy after any inelastic jump, r advanced along the
+ * pre-step direction, u the new direction.  jump: 0 none, 1 elastic, 2 inel. */
+typedef struct {
+    double E0, E1, E2;
+    double r0[3];
+    int jump;
+} or_step_ev;
+
+static void sde_step(const or_mat* m, double rho, const oracle_params* p, uint64_t seed, uint64_t h,
+                     uint32_t n, double* E, double r[3], double u[3], double* tau, or_step_ev* ev) {
+    oracle_physics_out ph;
+    physics_eval(m, rho, p, *E, &ph);
+    double U[4];
+    draw4(seed, h, n, TAG_STEP, U);
+    double D = p->step_cm;
+    ev->E0 = *E;
+    for (int i = 0; i < 3; ++i) ev->r0[i] = r[i];
+
+    /* Energy line of Eq. VSDE: E - s1 Delta + clamp(s2 B_n, -s1 Delta, s1 Delta),
+     * B_n ~ N(0, Delta).  Reading: a loss larger than E_n (possible only just
+     * above e_min) is capped at E_n. */
+    double s1d = ph.s1 * D;
+    double zE = sqrt(-2.0 * log(U[0])) * cos(2.0 * OR_PI * U[1]);
+    double st = (p->physics_mask & ORACLE_PHYS_STRAGGLING) ? sqrt(ph.s2sq) * sqrt(D) * zE : 0.0;
+    if (st < -s1d) st = -s1d;
+    if (st > s1d) st = s1d;
+    double E1 = *E - s1d + st;
+    if (E1 < 0.0) E1 = 0.0;
+    ev->E1 = E1;
+
+    /* Position line: R_{n+1} = R_n + Omega_n Delta (mm). */
+    for (int i = 0; i < 3; ++i) r[i] += u[i] * D * 10.0;
+
+    /* Direction line, diffusive part: spherical Brownian increment over time
+     * m^2 Delta.  Reading: the exact small-time algorithm cited by the paper is
+     * not reproduced in it; the polar angle is drawn from the small-time heat
+     * kernel theta^2 = -2 t ln U (per-axis tangent variance t) and the azimuth
+     * uniformly.  E[cos theta] = e^{-t} + O(t^2). */
+    if ((p->physics_mask & ORACLE_PHYS_MCS) && ph.t_sbm > 0.0) {
+        double th = sqrt(-2.0 * ph.t_sbm * log(U[2]));
+        rotate_dir(u, cos(th), sin(th), 2.0 * OR_PI * U[3]);
+    }
+
+    /* Jump part: (u_n, D_n) = 0 with probability exp(-Delta (sigma_e + sigma_ne)),
+     * else drawn from the mixture Eq. Npi.  Reading: the printed statement swaps
+     * the two cases; a jump happens with probability 1 - exp(-Delta sigma). */
+    double sig = ph.sig_e + ph.sig_ne;
+    int jump = 0;
+    if (sig > 0.0) {
+        if (p->jump_clock == 0) {
+            double B[4];
+            draw4(seed, h, n, TAG_BERN, B);
+            jump = B[0] < -expm1(-D * sig);
+        } else {
+            *tau -= D * sig;
+            jump = *tau <= 0.0;
+        }
+    }
+    ev->jump = 0;
+    if (jump) {
+        double J[4];
+        draw4(seed, h, n, TAG_JUMP_A, J);
+        /* channel and element by rate (Eq. Npi and Bragg additivity of the
+         * point processes): elastic of element 0..n-1, then non-elastic. */
+        double target = J[0] * sig, acc = 0.0;
+        int pick = 2 * m->n - 1;
+        for (int k = 0; k < 2 * m->n; ++k) {
+            acc += k < m->n ? ph.sig_e_el[k] : ph.sig_ne_el[k - m->n];
+            if (target < acc) {
+                pick = k;
+                break;
+            }
+        }
+        /* guard against picking a zero-rate channel at the rounding edge */
+        while (pick > 0 && (pick < m->n ? ph.sig_e_el[pick] : ph.sig_ne_el[pick - m->n]) <= 0.0) --pick;
+        int el = pick < m->n ? pick : pick - m->n;
+        double m2 = target_mass(m->Z[el], m->A[el]);
+        if (pick < m->n) {
+            double mu_c = cos(p->theta_cut_rad);
+            double mu;
+            if (m->Z[el] == 1) {
+                double eta, k;
+                oracle_coulomb_eta_k(1, *E, &eta, &k);
+                mu = oracle_sample_mu_mott(J[1], eta, -cos(p->backscatter_rad), mu_c);
+            } else {
+                mu = oracle_sample_mu_rutherford(J[1], mu_c);
+            }
+            double thL = oracle_cm_to_lab(*E, *E, m2, mu);
+            rotate_dir(u, cos(thL), sin(thL), 2.0 * OR_PI * J[2]);
+            ev->jump = 1;
+        } else {
+            double J2[4];
+            draw4(seed, h, n, TAG_JUMP_B, J2);
+            double uu = p->inel_u_lo + (p->inel_u_hi - p->inel_u_lo) * J[1];
+            double a = oracle_kalbach_a(*E, uu, m->A[el]);
+            double mu = oracle_sample_mu_kalbach(J2[0], a, p->km_r);
+            double thL = oracle_cm_to_lab(*E, *E * (1.0 - uu), m2, mu);
+            rotate_dir(u, cos(thL), sin(thL), 2.0 * OR_PI * J[2]);
+            /* energy line: the inelastic factor (1 - u_n) multiplies the
+             * energy after the continuous loss */
+            E1 = E1 * (1.0 - uu);
+            ev->jump = 2;
+        }
+        *tau = -log(J[3]);
+    }
+    ev->E2 = E1;
+    *E = E1;
+}
+
+typedef struct {
+    const oracle_dose* d;
+    const oracle_spot* spots;
+    const uint64_t* prefix;
+    int n_spots;
+    uint64_t seed, h_begin, h_end;
+    or_acc acc;
+} or_job;
+
+static void transport_history(const oracle_dose* d, const oracle_spot* s, uint64_t seed, uint64_t h,
+                              or_acc* acc) {
+    double E, r[3], u[3], tau;
+    sample_source(d, s, seed, h, &E, r, u, &tau);
+    acc->bal.incident += Q(d, E);
+    acc->bal.histories += 1;
+    for (uint32_t n = 0;; ++n) {
+        if ((int)n >= d->p.max_steps) {
+            acc->error = ORACLE_ESTEPCAP;
+            acc->bal.escaped += Q(d, E); /* keep the balance exact */
+            return;
+        }
+        long v = voxel_of(d, r);
+        if (v < 0) { /* left the domain D */
+            acc->bal.escaped += Q(d, E);
+            return;
+        }
+        const or_mat* m = &d->mats[d->mid[v]];
+        double rho = d->rho[v];
+        or_step_ev ev;
+        sde_step(m, rho, &d->p, seed, h, n, &E, r, u, &tau, &ev);
+        acc->bal.steps += 1;
+        uint64_t dq = Q(d, ev.E0) - Q(d, ev.E1);
+        if (d->p.tally_mode == 0) {
+            /* Sec. 2.2.2: the deposit of the step is assigned at its midpoint */
+            double mid[3];
+            for (int i = 0; i < 3; ++i) mid[i] = 0.5 * (ev.r0[i] + r[i]);
+            deposit_at(acc, voxel_of(d, mid), dq);
+        } else {
+            deposit_chord(d, acc, ev.r0, r, dq);
+        }
+        if (ev.jump == 1) acc->bal.jumps_elastic += 1;
+        if (ev.jump == 2) {
+            acc->bal.jumps_inelastic += 1;
+            acc->bal.removed += Q(d, ev.E1) - Q(d, ev.E2);
+        }
+        /* Termination (Sec. 2.1.3): absorbed below e_min, the rest deposited
+         * at the current position. */
+        if (E < d->p.e_min_MeV) {
+            deposit_at(acc, voxel_of(d, r), Q(d, E));
+            return;
+        }
+    }
+}
+
+static size_t find_spot(const uint64_t* prefix, int n_spots, uint64_t h) {
+    size_t lo = 0, hi = (size_t)n_spots; /* prefix[lo] <= h < prefix[hi] */
+    while (hi - lo > 1) {
+        size_t mid = (lo + hi) / 2;
+        if (prefix[mid] <= h)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+static void* run_job(void* arg) {
+    or_job* j = (or_job*)arg;
+    for (uint64_t h = j->h_begin; h < j->h_end; ++h) {
+        size_t s = find_spot(j->prefix, j->n_spots, h);
+        transport_history(j->d, &j->spots[s], j->seed, h, &j->acc);
+    }
+    return NULL;
+}
+
+int oracle_run(oracle_dose* d, const oracle_spot* spots, int n_spots, uint64_t seed) {
+    if (!d || !spots || n_spots <= 0) return fail(ORACLE_EINVAL, "bad run arguments");
+    uint64_t* prefix = (uint64_t*)malloc(((size_t)n_spots + 1) * sizeof(uint64_t));
+    if (!prefix) return fail(ORACLE_ENOMEM, "out of memory");
+    prefix[0] = 0;
+    for (int s = 0; s < n_spots; ++s) {
+        const oracle_spot* sp = &spots[s];
+        double un = sp->ux * sp->ux + sp->uy * sp->uy + sp->uz * sp->uz;
+        if (!(sp->E_MeV > 0.0) || !(sp->sigma_E_MeV >= 0.0) || !(sp->sigma_xy_mm >= 0.0) ||
+            !(sp->sigma_angle_rad >= 0.0) || !(un > 0.0)) {
+            free(prefix);
+            return fail(ORACLE_EINVAL, "bad spot");
+        }
+        prefix[s + 1] = prefix[s] + sp->n_hist;
+    }
+    uint64_t total = prefix[n_spots];
+    int T = g_threads;
+    if (T <= 0) {
+        const char* env = getenv("ORACLE_THREADS");
+        T = env ? atoi(env) : 0;
+        if (T <= 0) {
+            long nc = 8;
+#ifdef _SC_NPROCESSORS_ONLN
+            nc = sysconf(_SC_NPROCESSORS_ONLN);
+#endif
+            T = nc > 0 ? (int)nc : 1;
+        }
+    }
+    if ((uint64_t)T > total) T = total > 0 ? (int)total : 1;
+    size_t nv = (size_t)d->nx * d->ny * d->nz;
+    or_job* jobs = (or_job*)calloc((size_t)T, sizeof(or_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)T, sizeof(pthread_t));
+    int rc = ORACLE_OK;
+    if (!jobs || !th) rc = fail(ORACLE_ENOMEM, "out of memory");
+    for (int t = 0; t < T && rc == ORACLE_OK; ++t) {
+        jobs[t].d = d;
+        jobs[t].spots = spots;
+        jobs[t].prefix = prefix;
+        jobs[t].n_spots = n_spots;
+        jobs[t].seed = seed;
+        jobs[t].h_begin = total * (uint64_t)t / (uint64_t)T;
+        jobs[t].h_end = total * (uint64_t)(t + 1) / (uint64_t)T;
+        jobs[t].acc.edep = (uint64_t*)calloc(nv, sizeof(uint64_t));
+        if (!jobs[t].acc.edep) rc = fail(ORACLE_ENOMEM, "out of memory");
+    }
+    if (rc == ORACLE_OK) {
+        for (int t = 0; t < T; ++t) pthread_create(&th[t], NULL, run_job, &jobs[t]);
+        for (int t = 0; t < T; ++t) pthread_join(th[t], NULL);
+        /* Integer sums: the result does not depend on T. */
+        for (int t = 0; t < T; ++t) {
+            for (size_t v = 0; v < nv; ++v) d->edep[v] += jobs[t].acc.edep[v];
+            oracle_balance* b = &jobs[t].acc.bal;
+            d->bal.incident += b->incident;
+            d->bal.deposited += b->deposited;
+            d->bal.escaped += b->escaped;
+            d->bal.removed += b->removed;
+            d->bal.histories += b->histories;
+            d->bal.steps += b->steps;
+            d->bal.jumps_elastic += b->jumps_elastic;
+            d->bal.jumps_inelastic += b->jumps_inelastic;
+            if (jobs[t].acc.error) rc = fail(jobs[t].acc.error, "step cap reached");
+        }
+    }
+    if (jobs)
+        for (int t = 0; t < T; ++t) free(jobs[t].acc.edep);
+    free(jobs);
+    free(th);
+    free(prefix);
+    return rc;
+}
+
+int oracle_fetch(oracle_dose* d, double* dose_Gy, uint64_t* edep_fixed, oracle_balance* bal) {
+    if (!d) return fail(ORACLE_EINVAL, "null handle");
+    size_t nv = (size_t)d->nx * d->ny * d->nz;
+    if (edep_fixed) memcpy(edep_fixed, d->edep, nv * sizeof(uint64_t));
+    if (dose_Gy) {
+        /* Dose-to-medium (Sec. 2.2.2): energy over voxel mass. */
+        double vol_cm3 = d->h[0] * d->h[1] * d->h[2] * 1e-3;
+        double unit_J = ldexp(1.0, -d->p.fixed_point_shift) * OR_MEV_J;
+        for (size_t v = 0; v < nv; ++v) {
+            double mass_kg = (double)d->rho[v] * vol_cm3 * 1e-3;
+            dose_Gy[v] = mass_kg > 0.0 ? (double)d->edep[v] * unit_J / mass_kg : 0.0;
+        }
+    }
+    if (bal) *bal = d->bal;
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------ single-step probe */
+int oracle_single_step(const oracle_material* mat, double rho, const oracle_params* p, double E,
+                       uint64_t seed, uint64_t h0, int n, double* E_out, double* cos_out,
+                       int* jump_out, double* ux_out, double* uy_out) {
+    or_mat m;
+    int rc = resolve_material(mat, &m);
+    if (rc) return rc;
+    if (!p || check_params(p) || !(E > 0.0) || !(rho >= 0.0) || n < 0)
+        return fail(ORACLE_EINVAL, "bad single-step arguments");
+    for (int i = 0; i < n; ++i) {
+        uint64_t h = h0 + (uint64_t)i;
+        double e = E, r[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 1.0}, tau;
+        double B[4];
+        draw4(seed, h, 0u, TAG_SRC_B, B);
+        tau = -log(B[2]);
+        or_step_ev ev;
+        sde_step(&m, rho, p, seed, h, 0u, &e, r, u, &tau, &ev);
+        if (E_out) E_out[i] = e;
+        if (cos_out) cos_out[i] = u[2];
+        if (jump_out) jump_out[i] = ev.jump;
+        if (ux_out) ux_out[i] = u[0];
+        if (uy_out) uy_out[i] = u[1];
+    }
+    return ORACLE_OK;
+}

@@ -1,0 +1,277 @@
+"""Pins of the oracle's physics against values fixed outside the oracle itself.
+
+Each test checks one function of the oracle (Secs. 2.1.3-2.1.5 and Appendix A of the
+paper) against a published value, a textbook special case, an independent quadrature
+or an independent construction, chosen so that a dropped term, a wrong sign, index or
+constant in the oracle fails it.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle as O
+from sde_workloads import WATER
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+# physical constants used by the textbook formulas below (CODATA 2018)
+MP = 938.27208816
+AMU = 931.49410242
+E2 = 1.439964548  # e^2 = alpha hbar c, MeV fm
+NA = 6.02214076e23
+
+
+def _rows(name):
+    out = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                out.append(line.split())
+    return out
+
+
+def test_philox_known_answers(oracle_lib):
+    rows = _rows("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        assert O.philox(v[0:4], v[4:6]) == v[6:10]
+
+
+PSTAR = [tuple(float(x) for x in r) for r in _rows("pstar_water.txt")]
+
+
+@pytest.mark.parametrize("E,S,R", PSTAR)
+def test_stopping_power_vs_pstar(oracle_lib, E, S, R):
+    s1 = O.physics(WATER, 1.0, E).s1
+    tol = 0.01 if E >= 50 else 0.015
+    assert abs(s1 / S - 1.0) < tol, (E, s1, S)
+
+
+@pytest.mark.parametrize("E,S,R", PSTAR)
+def test_csda_range_vs_pstar(oracle_lib, E, S, R):
+    r = O.csda_range(WATER, 1.0, E)
+    tol = 0.01 if E >= 50 else 0.03
+    assert abs(r / R - 1.0) < tol, (E, r, R)
+
+
+def test_stopping_scales_with_density(oracle_lib):
+    a = O.physics(WATER, 1.0, 80.0)
+    b = O.physics(WATER, 0.26, 80.0)
+    assert b.s1 == pytest.approx(0.26 * a.s1, rel=1e-12)
+    assert b.s2sq == pytest.approx(0.26 * a.s2sq, rel=1e-12)
+
+
+@pytest.mark.parametrize("E0", [20.0, 100.0, 230.0])
+def test_csda_quadrature_independent_rule(oracle_lib, E0):
+    """The oracle's adaptive Simpson in ln E against scipy's adaptive Gauss-Kronrod in E."""
+    f = lambda E: 1.0 / O.physics(WATER, 1.0, E).s1
+    ref, err = integrate.quad(f, 0.05, E0, limit=400, epsabs=0, epsrel=1e-11, points=[0.2, 1, 5])
+    assert O.csda_range(WATER, 1.0, E0) == pytest.approx(ref, rel=1e-7)
+
+
+def _water_Z_over_A():
+    wsum = sum(w for _, w in WATER["elements"])
+    return sum(w / wsum * Z / O.element(Z)[0] for Z, w in WATER["elements"])
+
+
+def test_straggling_bohr_low_energy_limit(oracle_lib):
+    """Bohr: varsigma_2^2 -> 4 pi N_A r_e^2 (m_e c^2)^2 Z/A rho = 0.1569 Z/A rho MeV^2/cm as
+    beta -> 0 (the relativistic factor gamma^2 (1 - beta^2/2) -> 1)."""
+    s2 = O.physics(WATER, 1.0, 0.05).s2sq
+    assert s2 == pytest.approx(0.1569 * _water_Z_over_A(), rel=1.5e-3)
+
+
+@pytest.mark.parametrize("E", [20.0, 50.0, 100.0, 200.0])
+@pytest.mark.parametrize("z", [0.05, 0.5, 2.0])
+def test_lynch_dahl_width_vs_highland(oracle_lib, E, z):
+    """Highland's formula (PDG form) reproduces the Lynch-Dahl Gaussian width of the central
+    98 % of the Moliere distribution to 11 % for 1e-3 < x/X0 < 100."""
+    X0 = 36.08  # water radiation length, cm (PDG)
+    p = math.sqrt(E * (E + 2 * MP))
+    beta = p / (E + MP)
+    x = z / X0
+    theta0 = 13.6 / (p * beta) * math.sqrt(x) * (1 + 0.038 * math.log(x / beta ** 2))
+    sig = O.physics(WATER, 1.0, E, msc_z_cm=z).sigma_msc
+    assert abs(sig / theta0 - 1.0) < 0.11, (E, z, sig, theta0)
+
+
+def test_sbm_time_is_sigma_squared_over_steps(oracle_lib):
+    """m = sigma/sqrt(z): the Brownian time of one step Delta is sigma^2 Delta / z."""
+    ph = O.physics(WATER, 1.0, 100.0, msc_z_cm=0.05, step_cm=0.025)
+    assert ph.t_sbm == pytest.approx(ph.sigma_msc ** 2 * 0.5, rel=1e-12)
+
+
+def _ecm(Z, E):
+    A = O.element(Z)[0]
+    m2 = MP if Z == 1 else A * AMU
+    return E * (m2 / (MP + m2)), m2
+
+
+@pytest.mark.parametrize("Z", [6, 8, 20])
+@pytest.mark.parametrize("E", [1.0, 10.0, 150.0])
+def test_rutherford_matches_textbook(oracle_lib, Z, E):
+    """eta^2/(k^2 (1-mu)^2) equals (Z e^2 / (4 E_cm))^2 / sin^4(theta/2)."""
+    eta, k = O.coulomb_eta_k(Z, E)
+    ecm, _ = _ecm(Z, E)
+    f = O.fn("oracle_rutherford_dsigma")
+    for th in (0.03, 0.5, 2.0):
+        ref = (Z * E2 / (4 * ecm)) ** 2 / math.sin(th / 2) ** 4
+        assert f(math.cos(th), eta, k) == pytest.approx(ref, rel=1e-9)
+
+
+@pytest.mark.parametrize("Z", [1])
+@pytest.mark.parametrize("E", [0.5, 10.0, 150.0])
+def test_mott_matches_textbook(oracle_lib, Z, E):
+    """Identical spin-1/2 particles: (e^2/(4 E_cm))^2 [1/s^4 + 1/c^4 - cos(eta ln(s^2/c^2))/(s^2 c^2)]
+    with s = sin(theta/2), c = cos(theta/2)."""
+    eta, k = O.coulomb_eta_k(Z, E)
+    ecm, _ = _ecm(Z, E)
+    f = O.fn("oracle_mott_dsigma")
+    for th in (0.05, 1.0, 2.6):
+        s, c = math.sin(th / 2) ** 2, math.cos(th / 2) ** 2
+        ref = (E2 / (4 * ecm)) ** 2 * (1 / s ** 2 + 1 / c ** 2 - math.cos(eta * math.log(s / c)) / (s * c))
+        assert f(math.cos(th), eta, k) == pytest.approx(ref, rel=1e-9)
+
+
+@pytest.mark.parametrize("eta", [1e-3, 0.2, 0.7])
+@pytest.mark.parametrize("ab", [(-0.99, 0.5), (0.1, 0.9998), (-0.9992, 0.9998)])
+def test_mott_antiderivative_is_the_integral(oracle_lib, eta, ab):
+    k = 1.0
+    f = O.fn("oracle_mott_dsigma")
+    G = O.fn("oracle_mott_antiderivative")
+    a, b = ab
+    val, _ = integrate.quad(lambda m: f(m, eta, k) / eta ** 2, a, b, limit=500, epsrel=1e-12,
+                            points=[-0.9, 0.9, 0.99])
+    assert G(b, eta) - G(a, eta) == pytest.approx(val, rel=1e-8)
+
+
+def _pure(Z):
+    return {"name": f"Z{Z}", "elements": [(Z, 1.0)], "I_eV": 0.0}
+
+
+@pytest.mark.parametrize("Z", [1, 8, 20])
+@pytest.mark.parametrize("E", [2.0, 60.0, 200.0])
+def test_elastic_rate_is_the_solid_angle_integral(oracle_lib, Z, E):
+    """Eqs. large_elastic_cm(_hydrogen): rate = n * integral of the CM cross section over
+    theta_c < theta (< pi - theta_b for hydrogen), n = N_A rho / A; fm^2 = 1e-26 cm^2."""
+    rho = 1.0
+    A = O.element(Z)[0]
+    n = NA * rho / A
+    eta, k = O.coulomb_eta_k(Z, E)
+    ecm, _ = _ecm(Z, E)
+    thc, thb = 0.02, 0.04
+    if Z == 1:
+        def dsig(th):
+            s, c = math.sin(th / 2) ** 2, math.cos(th / 2) ** 2
+            return (E2 / (4 * ecm)) ** 2 * (1 / s ** 2 + 1 / c ** 2 - math.cos(eta * math.log(s / c)) / (s * c))
+        hi = math.pi - thb
+    else:
+        dsig = lambda th: (Z * E2 / (4 * ecm)) ** 2 / math.sin(th / 2) ** 4
+        hi = math.pi
+    val, _ = integrate.quad(lambda th: dsig(th) * 2 * math.pi * math.sin(th), thc, hi, limit=500,
+                            epsrel=1e-12, points=[0.05, 0.2, 1.0])
+    ph = O.physics(_pure(Z), rho, E)
+    assert ph.sig_e == pytest.approx(n * val * 1e-26, rel=1e-7)
+    assert ph.sig_e_el[0] == pytest.approx(ph.sig_e, rel=1e-15)
+
+
+def _cdf_by_quadrature(pdf, lo, hi, x, points=None):
+    tot, _ = integrate.quad(pdf, lo, hi, limit=500, epsrel=1e-13, points=points)
+    part, _ = integrate.quad(pdf, lo, x, limit=500, epsrel=1e-13, points=points)
+    return part / tot
+
+
+def test_rutherford_sampler_inverts_the_cdf(oracle_lib):
+    mu_c = math.cos(0.02)
+    samp = O.fn("oracle_sample_mu_rutherford")
+    pdf = lambda m: 1.0 / (1.0 - m) ** 2
+    for U in (1e-6, 0.1, 0.5, 0.9, 0.999999):
+        mu = samp(U, mu_c)
+        assert -1.0 <= mu <= mu_c
+        assert _cdf_by_quadrature(pdf, -1.0, mu_c, mu, points=[0.9, 0.99, 0.999]) == pytest.approx(U, abs=1e-9)
+
+
+@pytest.mark.parametrize("eta", [0.0158, 0.3, 0.7])
+def test_mott_sampler_inverts_the_cdf(oracle_lib, eta):
+    mu_c, mu_lo = math.cos(0.02), -math.cos(0.04)
+    samp = O.fn("oracle_sample_mu_mott")
+    f = O.fn("oracle_mott_dsigma")
+    pdf = lambda m: f(m, eta, 1.0)
+    for U in (1e-5, 0.2, 0.5, 0.8, 0.99999):
+        mu = samp(U, eta, mu_lo, mu_c)
+        assert mu_lo <= mu <= mu_c
+        got = _cdf_by_quadrature(pdf, mu_lo, mu_c, mu, points=[-0.999, -0.99, 0.99, 0.999])
+        assert got == pytest.approx(U, abs=1e-8)
+
+
+@pytest.mark.parametrize("a,r", [(0.5, 0.3), (2.3, 0.8), (6.0, 0.0), (0.01, 0.5)])
+def test_kalbach_sampler_inverts_the_printed_pdf(oracle_lib, a, r):
+    """pi_ne(mu|E,u) = a/(2 sinh a) (cosh(a mu) + r sinh(a mu)) on [-1, 1] (Sec. 2.1.5)."""
+    samp = O.fn("oracle_sample_mu_kalbach")
+    pdf = lambda m: a / (2 * math.sinh(a)) * (math.cosh(a * m) + r * math.sinh(a * m))
+    for U in (1e-6, 0.25, 0.5, 0.75, 0.999999):
+        mu = samp(U, a, r)
+        assert _cdf_by_quadrature(pdf, -1.0, 1.0, mu) == pytest.approx(U, abs=1e-9)
+
+
+def test_kalbach_sampler_small_a_is_uniform(oracle_lib):
+    samp = O.fn("oracle_sample_mu_kalbach")
+    for U in (0.1, 0.5, 0.9):
+        assert samp(U, 1e-6, 0.5) == pytest.approx(2 * U - 1, abs=1e-12)
+
+
+@pytest.mark.parametrize("Z", [1, 8, 20])
+@pytest.mark.parametrize("E", [1.0, 50.0, 220.0])
+def test_cm_to_lab_equals_explicit_lorentz_boost(oracle_lib, Z, E):
+    """Appendix A.1 for elastic scattering against a four-vector construction: the CM momentum
+    from the invariant mass, rotated by theta_cm, boosted back along the beam."""
+    _, m2 = _ecm(Z, E)
+    f = O.fn("oracle_cm_to_lab")
+    Etot = E + MP
+    p = math.sqrt(Etot ** 2 - MP ** 2)
+    s = MP ** 2 + m2 ** 2 + 2 * Etot * m2
+    pstar = math.sqrt((s - (MP + m2) ** 2) * (s - (MP - m2) ** 2) / (4 * s))
+    Estar = math.sqrt(pstar ** 2 + MP ** 2)
+    bcm = p / (Etot + m2)
+    g = 1 / math.sqrt(1 - bcm ** 2)
+    for th in (0.01, 0.5, 1.5, 2.8):
+        px = pstar * math.sin(th)
+        pz = g * (pstar * math.cos(th) + bcm * Estar)
+        assert f(E, E, m2, math.cos(th)) == pytest.approx(math.atan2(px, pz), abs=1e-12)
+
+
+def test_cm_to_lab_nonrelativistic_limit(oracle_lib):
+    f = O.fn("oracle_cm_to_lab")
+    E = 1e-4
+    for Z in (1, 8):
+        _, m2 = _ecm(Z, E)
+        Ar = m2 / MP
+        for th in (0.3, 1.2, 2.5):
+            ref = math.atan2(math.sin(th), math.cos(th) + 1 / Ar)
+            assert f(E, E, m2, math.cos(th)) == pytest.approx(ref, rel=1e-4)
+
+
+def test_nonelastic_rate_of_water_is_about_one_percent_per_cm(oracle_lib):
+    """Sanity only (the ENDF data are absent; the rate is a stand-in): primary fluence in
+    water falls by roughly 1 % per cm at therapeutic energies."""
+    for E in (100.0, 150.0, 200.0):
+        r = O.physics(WATER, 1.0, E).sig_ne
+        assert 0.007 < r < 0.013, (E, r)
+    assert O.fn("oracle_sigma_ne_element_mb")(1, 150.0) == 0.0
+
+
+def test_physics_mask_switches_rates(oracle_lib):
+    a = O.physics(WATER, 1.0, 50.0, physics_mask=O.PHYS_ALL)
+    b = O.physics(WATER, 1.0, 50.0, physics_mask=O.PHYS_MCS)
+    assert a.sig_e > 0 and a.sig_ne > 0 and b.sig_e == 0 and b.sig_ne == 0
+    assert a.s1 == b.s1
+
+
+def test_bragg_additive_I_of_water_close_to_75eV(oracle_lib):
+    ph = O.physics({"name": "w", "elements": WATER["elements"], "I_eV": 0.0}, 1.0, 100.0)
+    assert 74.0 < ph.I_eV < 76.5

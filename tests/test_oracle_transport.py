@@ -1,0 +1,137 @@
+"""Whole-transport pins of the oracle: exact energy balance, determinism, thread-count
+invariance, equivalence of the two jump clocks, the chord/midpoint tallies against an
+independent geometric computation, and the reference dose metrics."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import analysis as A
+from sde_workloads import WATER, Workload, pencil, slab150, water100
+
+
+def _balanced(b):
+    return b["incident"] == b["deposited"] + b["escaped"] + b["removed"]
+
+
+def test_energy_balance_is_exact(oracle_lib):
+    for wl, kw in ((water100(3000), {}), (water100(2000), {"tally_mode": 1}),
+                   (slab150(300), {})):
+        dose, edep, b = O.run_workload(wl, **kw)
+        assert _balanced(b)
+        assert int(edep.sum(dtype=np.uint64)) == b["deposited"]
+        assert b["histories"] == wl.n_histories
+
+
+def test_thread_count_does_not_change_the_result(oracle_lib):
+    wl = water100(1500)
+    _, e1, b1 = O.run_workload(wl, threads=1)
+    _, e4, b4 = O.run_workload(wl, threads=4)
+    O.set_threads(0)
+    assert np.array_equal(e1, e4) and b1 == b4
+
+
+def test_same_seed_same_tally_other_seed_differs(oracle_lib):
+    wl = water100(1000)
+    _, a, _ = O.run_workload(wl, seed=7)
+    _, b, _ = O.run_workload(wl, seed=7)
+    _, c, _ = O.run_workload(wl, seed=8)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c)
+
+
+def test_bernoulli_and_exponential_jump_clocks_agree_in_distribution(oracle_lib):
+    wl = water100(20_000)
+    _, ea, ba = O.run_workload(wl, jump_clock=0)
+    _, eb, bb = O.run_workload(wl, jump_clock=1, seed=1)
+    for key in ("jumps_inelastic", "jumps_elastic"):
+        n1, n2 = ba[key], bb[key]
+        assert abs(n1 - n2) < 4.5 * math.sqrt(n1 + n2), key
+    z = A.z_centres(120, 1.0)
+    ra = A.distal_range(A.idd(ea.astype(float)), z, 0.8)
+    rb = A.distal_range(A.idd(eb.astype(float)), z, 0.8)
+    assert abs(ra - rb) < 0.1
+
+
+def _straight_track_workload(E0, start, u, shape=(20, 20, 30)):
+    nx, ny, nz = shape
+    dens = np.ones((nz, ny, nx), np.float32)
+    mid = np.zeros((nz, ny, nx), np.uint8)
+    spot = pencil(E0, 1, x=start[0], y=start[1], z=start[2], u=u)
+    return Workload("track", shape, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), dens, mid, [WATER], spot)
+
+
+def _energy_sequence(E0):
+    Es = [E0]
+    while Es[-1] >= 0.05:
+        Es.append(O.single_step(WATER, 1.0, Es[-1], 1, physics_mask=0)["E"][0])
+    return Es
+
+
+def _Q(E):
+    return int(round(math.ldexp(E, 24)))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tally_geometry_on_a_straight_track(oracle_lib, mode):
+    """A deterministic oblique track (all noise off): the per-voxel tally equals the step
+    deposits Q(E_n) - Q(E_n+1) placed at each chord's midpoint voxel (mode 0, exactly) or
+    spread over the voxels in proportion to the chord length inside each (mode 1, found here
+    by dense sampling of the chord), plus the final residual at the end point."""
+    E0 = 25.0
+    start = np.array([6.3, 4.7, 0.0])
+    u = np.array([0.35, 0.2, 1.0])
+    u = u / np.linalg.norm(u)
+    wl = _straight_track_workload(E0, start, u)
+    _, edep, b = O.run_workload(wl, physics_mask=0, tally_mode=mode)
+    Es = _energy_sequence(E0)
+    nx, ny, nz = wl.shape
+    expect = np.zeros((nz, ny, nx))
+
+    def vox(p):
+        i = np.floor(p).astype(int)
+        return i[..., 2], i[..., 1], i[..., 0]
+
+    L = 0.5  # mm per step
+    for n in range(len(Es) - 1):
+        dq = _Q(Es[n]) - _Q(Es[n + 1])
+        a = start + n * L * u
+        if mode == 0:
+            expect[vox(a + 0.5 * L * u)] += dq
+        else:
+            t = (np.arange(20000) + 0.5) / 20000
+            iz, iy, ix = vox(a[None, :] + t[:, None] * L * u[None, :])
+            np.add.at(expect, (iz, iy, ix), dq / len(t))
+    expect[vox(start + (len(Es) - 1) * L * u)] += _Q(Es[-1])
+    assert _balanced(b) and b["escaped"] == 0 and b["removed"] == 0
+    if mode == 0:
+        assert np.array_equal(edep.astype(np.float64), expect)
+    else:
+        assert np.allclose(edep.astype(np.float64), expect, rtol=0, atol=2e-4 * expect.max())
+
+
+def test_distal_range_on_a_linear_falloff():
+    z = np.arange(10) + 0.5
+    c = np.array([1, 1, 1, 2, 4, 10, 8, 4, 0, 0], float)
+    # 80 % of 10 = 8 is reached exactly at z=6.5; 50 % = 5 lies between 8 (6.5) and 4 (7.5)
+    assert A.distal_range(c, z, 0.8) == pytest.approx(6.5)
+    assert A.distal_range(c, z, 0.5) == pytest.approx(6.5 + 3 / 4)
+
+
+def test_gamma_special_cases():
+    zz, yy, xx = np.meshgrid(np.arange(12), np.arange(10), np.arange(10), indexing="ij")
+    ref = 1.0 + 0.1 * zz + 0.02 * xx
+    assert A.gamma_pass_rate(ref, ref.copy(), (1, 1, 1)) == 1.0
+    # a uniform 5 % excess fails the 2 % local criterion where the gradient cannot help
+    flat = np.ones((8, 8, 8))
+    assert A.gamma_pass_rate(flat, flat * 1.05, (1, 1, 1)) == 0.0
+    # a 0.3 mm shift of a steep profile fails by dose difference but passes by distance
+    steep = np.exp(np.linspace(0, 8, 40))[:, None, None] * np.ones((40, 6, 6))
+    z = np.arange(40) * 1.0
+    shifted = np.exp(np.interp(z + 0.3, z, np.linspace(0, 8, 40)))[:, None, None] * np.ones((40, 6, 6))
+    assert np.mean(np.abs(shifted / steep - 1)[5:-5] > 0.02) > 0.9
+    assert A.gamma_pass_rate(steep, shifted, (1, 1, 1)) > 0.9
+    # a 0.7 mm shift exceeds the 0.5 mm distance criterion
+    shifted2 = np.exp(np.interp(z + 0.7, z, np.linspace(0, 8, 40)))[:, None, None] * np.ones((40, 6, 6))
+    assert A.gamma_pass_rate(steep, shifted2, (1, 1, 1)) < 0.2
