@@ -1,0 +1,320 @@
+"""Benchmark of the GB300 jump-SDE proton dose engine.
+
+One step = one pass of the whole transport path over one batch: zero the tally, prepare
+the spots (device-resident), and transport every history of the workload (persistent
+kernel: source sampling, Euler-Maruyama steps, jumps, voxel lookup, fixed-point tally).
+The default workload is the longitudinally heterogeneous slab phantom: 150 MeV beam,
+lateral sigma 3 mm, 10^6 protons, 60 x 60 x 200 mm at 0.5 mm voxels (water / bone-like /
+lung-like / water).  Its inputs (29 MB phantom + 46 MB tally) fit in L2, so L2 is flushed
+(256 MB write) before every timed step, outside the timed events.
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank transports its own
+10^6 histories with its own seeds (weak scaling, no collective on the data path) and the
+step time is the maximum over ranks.
+
+``--impl reference`` times the FP64 CPU oracle instead (on the host cores, rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic lane operations per Euler-Maruyama step of the transport kernel (one
+# Philox4x32-10 block, two Box-Muller transforms, table interpolation of five fields,
+# kinematic factors, Lynch-Dahl width, spherical Brownian rotation, exponential jump
+# clock, two voxel lookups, fixed-point conversion and one 64-bit atomic).  The
+# breakdown is listed with the roofline in the design notes.
+ALGO_OPS_PER_STEP = 220
+SMS = 152
+LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per clock each
+# DRAM traffic (read + write bytes) per transport launch from the ncu capture of the
+# same launch configuration; None until captured for the current kernel.
+TRANSPORT_DRAM_BYTES = None
+
+WORKLOAD_DESC = ("slab150: 150 MeV pencil beam (sigma_xy 3 mm), 1e6 protons per GPU, "
+                 "60x60x200 mm at 0.5 mm (120x120x400 voxels), water/bone-like/lung-like/water slabs")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(target_s: float = 12.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload."""
+    import oracle
+    from sde_workloads import slab150
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    cal = 4000
+    t0 = time.perf_counter()
+    oracle.run_workload(slab150(cal), seed=12345)
+    dt = time.perf_counter() - t0
+    n = int(min(2_000_000, max(cal, cal * target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    _, _, bal = oracle.run_workload(slab150(n), seed=777)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "histories/s", "cores": cores, "kind": "oracle",
+            "sample": f"slab150 workload, {n} histories (seed 777), FP64 oracle, {cores} threads, "
+                      f"{dt:.1f} s", "steps_per_s": bal["steps"] / dt}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from sde_workloads import slab150
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    n = args.ref_histories
+    for w in range(args.warmup):
+        oracle.run_workload(slab150(n), seed=10_000 + w)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run_workload(slab150(n), seed=20_000 + k)
+        times.append(time.perf_counter() - t0)
+    T = sum(times) / len(times)
+    v = n / T
+    line = {
+        "impl": "reference", "metric": "proton histories/s on 1 GB300", "value": v,
+        "unit": "histories/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": T * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC.replace("1e6 protons per GPU", f"{n} protons per step (bounded sample)"),
+                   "histories_per_step": n, "parallelism": f"{cores} host threads"},
+        "cpu_baseline": {"value": v, "unit": "histories/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} histories of the slab150 workload per step"},
+        "e2e": {"value": v, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--histories", type=int, default=1_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-histories", type=int, default=20_000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2511_03115_gb300 as S
+    from sde_workloads import slab150
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = slab150(args.histories)
+    stream = torch.cuda.Stream(device=dev)
+    d = S.SdeDose(wl, stream=stream)
+    spots_dev = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    seed_base = 1_000_003 * (rank + 1)
+
+    def step(k):
+        d.reset()
+        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + k)
+
+    for w in range(args.warmup):
+        step(10_000 + w)
+    d.sync()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        m = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        d.reset()
+        m.record(stream)
+        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + k)
+        e.record(stream)
+        evs.append((s, m, e))
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, _, e in evs]
+    kern_ms = [m.elapsed_time(e) for _, m, e in evs]
+    T = sum(step_ms) / len(step_ms)
+    Tk = sum(kern_ms) / len(kern_ms)
+    _, _, bal = d.fetch(dose=False, edep=False)
+    if ws > 1:
+        t = torch.tensor([T, Tk], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T, Tk = float(t[0]), float(t[1])
+    hist_per_step = wl.n_histories * ws
+    value = hist_per_step / (T * 1e-3)
+    steps_per_launch = bal["steps"]
+
+    # end to end through the public API with host buffers: spots H2D, dose D2H (pinned)
+    host_dose = torch.empty(wl.n_voxels, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d.reset()
+        d.run(wl.spots, seed=seed_base + 50_000 + k)
+        d.fetch_into(dose_ptr=host_dose.data_ptr())
+        t1 = time.perf_counter()
+        if k > 0:
+            e2e_times.append(t1 - t0)
+    e2e_T = sum(e2e_times) / len(e2e_times)
+    if ws > 1:
+        t = torch.tensor([e2e_T], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_T = float(t[0])
+
+    peaks = _peaks()
+    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = SMS * LANE_OPS_PER_CLK_PER_SM * clk_mhz * 1e6
+    achieved = steps_per_launch * ALGO_OPS_PER_STEP / (Tk * 1e-3)
+    line = {
+        "metric": "proton histories/s on 1 GB300",
+        "value": value,
+        "unit": "histories/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": T,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "histories_per_step": hist_per_step,
+                   "euler_steps_per_launch": steps_per_launch, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed (256 MB write) before every timed step", "tally": "int64 fixed point 2^-24 MeV",
+                   "tuning": d.get_tuning()},
+        "e2e": {"value": hist_per_step / e2e_T, "unit": "histories/s",
+                "h2d_bytes_per_step": int(wl.spots.nbytes),
+                "d2h_bytes_per_step": int(wl.n_voxels * 8 + 64)},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+                     "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": TRANSPORT_DRAM_BYTES,
+                     "kernel": "k_transport (+ single-block spot prep)", "kernel_ms": Tk,
+                     "ops_per_step": ALGO_OPS_PER_STEP,
+                     "peak_note": f"{SMS} SMs x {LANE_OPS_PER_CLK_PER_SM} lane-ops/clk x {clk_mhz:.0f} MHz (max SM clock)"},
+        "clocks": clocks,
+        "balance_exact": bal["incident"] == bal["deposited"] + bal["escaped"] + bal["removed"],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    d.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * sde_dose.h -- C ABI of the GB300 (sm_103a) jump-SDE proton dose engine.
+ *
+ * The engine advances pencil-beam protons through a voxelised phantom with the
+ * Euler-Maruyama scheme of the jump SDE of arXiv 2511.03115 (Sec. 2.1.2,
+ * Eq. VSDE): Bethe stopping drift, clamped Gaussian straggling, a spherical
+ * Brownian direction increment from the Lynch-Dahl width, and Poisson-clocked
+ * large-angle elastic and non-elastic nuclear jumps (Secs. 2.1.3-2.1.5).  The
+ * energy lost in each step is tallied per voxel as 64-bit fixed-point integers
+ * (one unit = 2^-S MeV), assigned at the step midpoint (Sec. 2.2.2) or split
+ * along the step's chord, so the tally of a given seed is bit-identical run
+ * to run.  Dose is dose-to-medium: deposited energy over voxel mass
+ * (Sec. 2.2.2).
+ *
+ * Conventions for every call:
+ *  - Return value: SDE_OK (0) or a negative SDE_E* code; sde_last_error()
+ *    then describes the failure (thread-local string owned by the library).
+ *  - Host pointers are read during the call only; the caller keeps ownership.
+ *    The library owns all device memory it allocates; sde_dose_destroy frees it.
+ *  - Device work is enqueued on the handle's stream (default: the legacy
+ *    default stream; see sde_dose_set_stream) and is asynchronous unless the
+ *    call says otherwise.  Errors raised on the device (step cap, invalid
+ *    device-resident spot) are reported by the next sde_dose_sync /
+ *    sde_dose_fetch* call as SDE_EDEVICE.
+ *  - Arrays of voxels are x-fastest: index = ix + nx*(iy + ny*iz).
+ *  - Coordinates are mm; energies MeV; densities g/cm^3.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef SDE_DOSE_H
+#define SDE_DOSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SDE_OK 0
+#define SDE_EINVAL (-1)  /* bad argument (null pointer, size, range)      */
+#define SDE_ENOMEM (-2)  /* device or pinned host allocation failed       */
+#define SDE_ECUDA (-3)   /* a CUDA runtime call failed                     */
+#define SDE_EDEVICE (-4) /* the device flagged an error (see message)      */
+
+/* physics_mask bits (a set bit switches the term of Eq. VSDE on) */
+#define SDE_PHYS_STRAGGLING 1 /* clamped Gaussian term of the energy line       */
+#define SDE_PHYS_MCS 2        /* spherical Brownian increment Xi_n              */
+#define SDE_PHYS_ELASTIC 4    /* large-angle elastic jumps (sigma_e, pi_e)      */
+#define SDE_PHYS_INELASTIC 8  /* non-elastic jumps (sigma_ne, pi_ne)            */
+#define SDE_PHYS_ALL 15
+
+#define SDE_MAX_ELEMENTS 16
+#define SDE_MAX_MATERIALS 16
+
+typedef struct sde_dose sde_dose; /* opaque engine handle */
+
+/* One element of a material: atomic number and mass fraction (fractions are
+ * renormalised to sum to one).  Supported Z: 1,2,6,7,8,9,11-20,22,26,29,30. */
+typedef struct {
+    int Z;
+    double mass_fraction;
+} sde_element_frac;
+
+/* A material composition (Sec. 2.1.1: materials enter through their chemical
+ * composition and mean excitation energy).  I_eV <= 0 selects Bragg additivity
+ * of ln I over the elements. */
+typedef struct {
+    const sde_element_frac* el;
+    int n_el; /* 1..SDE_MAX_ELEMENTS */
+    double I_eV;
+} sde_material;
+
+/* A beam spot (Sec. 2.2.2): mean energy and Gaussian energy spread, entry
+ * point, direction (normalised by the library), Gaussian lateral sigma in the
+ * plane perpendicular to the direction, Gaussian angular sigma (per axis),
+ * and the number of histories to run from it. */
+typedef struct {
+    double E_MeV, sigma_E_MeV;
+    double x_mm, y_mm, z_mm;
+    double ux, uy, uz;
+    double sigma_xy_mm, sigma_angle_rad;
+    uint64_t n_hist;
+} sde_spot;
+
+/* Free parameters of the model and of the engine.  Defaults
+ * (sde_default_params) are the paper's values, Sec. 2.2.2. */
+typedef struct {
+    double step_cm;         /* Delta of Eq. VSDE (0.05 cm)                          */
+    double msc_z_cm;        /* z of the Lynch-Dahl width, m = sigma/sqrt(z) (0.05)  */
+    double F;               /* Lynch-Dahl central fraction (0.98)                   */
+    double theta_cut_rad;   /* large-angle elastic cut-off, CM frame (0.02)         */
+    double backscatter_rad; /* hydrogen backscatter limit (0.04)                    */
+    double e_min_MeV;       /* absorption energy (0.05)                             */
+    double K;               /* Bethe prefactor of Eq. bethbloch (0.3072)            */
+    double inel_u_lo;       /* non-elastic energy-loss fraction u ~ U(lo, hi) (0,1)  */
+    double inel_u_hi;
+    double km_r;            /* Kalbach-Mann pre-equilibrium fraction r (0.5)        */
+    double e_max_MeV;       /* top of the physics-table energy grid (300)           */
+    int tally_mode;         /* 0: midpoint deposit; 1: split along the chord (DDA)  */
+    int fixed_point_shift;  /* S: one tally unit = 2^-S MeV (24)                    */
+    int max_steps;          /* step cap per history; exceeding it is SDE_EDEVICE    */
+    int physics_mask;       /* SDE_PHYS_* (SDE_PHYS_ALL)                            */
+    int table_points;       /* points of the ln-E table grid, 64..4096 (512)        */
+} sde_params;
+
+/* Energy balance in tally units: incident == deposited + escaped + removed
+ * holds exactly (escaped: carried out of the phantom; removed: lost in
+ * non-elastic events and not tallied, Sec. 2.1.1). */
+typedef struct {
+    uint64_t incident, deposited, escaped, removed;
+    uint64_t histories, steps, jumps_elastic, jumps_inelastic;
+} sde_balance;
+
+/* Launch shape of the transport kernel.  Zero fields keep the current value.
+ * blocks_per_sm * warps_per_block warps run persistently; each warp claims
+ * batch histories at a time from the shared work queue. */
+typedef struct {
+    int blocks_per_sm;   /* 1..8                    */
+    int warps_per_block; /* 1..32                   */
+    int batch;           /* 32..4096, multiple of 32 */
+} sde_tuning;
+
+/* Fill p with the defaults listed above.  Returns SDE_OK or SDE_EINVAL (p NULL). */
+int sde_default_params(sde_params* p);
+
+/* Message of the last failing call on this host thread (never NULL). */
+const char* sde_last_error(void);
+
+/* Create an engine for a phantom of nx*ny*nz voxels of size voxel_mm with its
+ * first corner at origin_mm.  density_g_cm3 (>= 0) and material_id (< n_mats)
+ * are x-fastest host arrays; mats[n_mats] are the compositions.  p may be
+ * NULL (defaults).  Copies the phantom to the device, builds the FP32 physics
+ * tables (FP64 evaluation on the device) and the CSDA range table.
+ * Synchronous.  Errors: SDE_EINVAL, SDE_ENOMEM, SDE_ECUDA. */
+int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const double voxel_mm[3],
+                    const double origin_mm[3], const float* density_g_cm3,
+                    const uint8_t* material_id, const sde_material* mats, int n_mats,
+                    const sde_params* p);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*, NULL = legacy default
+ * stream) for all later work of the handle.  The caller keeps the stream
+ * alive while the handle uses it. */
+int sde_dose_set_stream(sde_dose* d, void* cuda_stream);
+
+/* Set the transport launch shape (see sde_tuning). */
+int sde_dose_set_tuning(sde_dose* d, const sde_tuning* t);
+int sde_dose_get_tuning(const sde_dose* d, sde_tuning* t);
+
+/* Transport the histories of spots[0..n_spots) (host array) with the given
+ * seed and add their deposits to the tally (accumulates until reset).  History
+ * ids run 0..sum(n_hist)-1 in spot order; the random stream of history h is
+ * keyed by (seed, h), so a run is reproducible bit for bit.  The spots are
+ * copied before the call returns; the transport itself is asynchronous.
+ * Errors: SDE_EINVAL (bad spot, energy above e_max/1.05), SDE_ECUDA. */
+int sde_dose_run(sde_dose* d, const sde_spot* spots, int n_spots, uint64_t seed);
+
+/* As sde_dose_run, with spots already in device memory (d_spots, device
+ * pointer to n_spots sde_spot records, caller-owned, must stay valid until
+ * the work completes).  Fully asynchronous: invalid spots are reported as
+ * SDE_EDEVICE by the next sync/fetch and their histories are not run. */
+int sde_dose_run_device(sde_dose* d, const sde_spot* d_spots, int n_spots, uint64_t seed);
+
+/* Wait for the handle's work; SDE_EDEVICE if the device flagged an error
+ * (the flag is cleared by the call). */
+int sde_dose_sync(sde_dose* d);
+
+/* Copy results to host buffers (any may be NULL): dose_Gy[n_vox] (dose to
+ * medium, 0 where density is 0), edep_fixed[n_vox] (tally units), bal.
+ * Synchronous. */
+int sde_dose_fetch(sde_dose* d, double* dose_Gy, uint64_t* edep_fixed, sde_balance* bal);
+
+/* As sde_dose_fetch with device output buffers d_dose_Gy / d_edep_fixed
+ * (caller-owned device memory, n_vox elements; either may be NULL).  The
+ * conversion runs on the device; bal (host, may be NULL) is read back.
+ * Synchronous when bal is non-NULL, else asynchronous. */
+int sde_dose_fetch_device(sde_dose* d, double* d_dose_Gy, uint64_t* d_edep_fixed,
+                          sde_balance* bal);
+
+/* Zero the tally and the balance counters (asynchronous). */
+int sde_dose_reset(sde_dose* d);
+
+/* Release all device and host memory of the handle (synchronises first). */
+void sde_dose_destroy(sde_dose* d);
+
+/* Grid and table facts: n_vox, the number of table points, the ln-E grid
+ * (e_min, e_max) and the number of materials.  Any output may be NULL. */
+int sde_dose_info(const sde_dose* d, uint64_t* n_vox, int* table_points, double* e_min_MeV,
+                  double* e_max_MeV, int* n_mats);
+
+/* Copy the FP32 per-step physics tables of material m to host memory.
+ * out[table_points * 5] receives, per grid energy E_k = e_min (e_max/e_min)^(k/(N-1)):
+ * varsigma_1/rho (MeV cm^2/g), varsigma_2^2/rho (MeV^2 cm^2/g), chi_c^2/rho
+ * (rad^2 cm^3/g, over the path z), 1/(2 chi_alpha^2 (1-F)) (rad^-2) and
+ * (sigma_e + sigma_ne)/rho (cm^2/g).  rates_out[table_points * 2 * n_el]
+ * (may be NULL) receives the per-element elastic then non-elastic rates per
+ * unit density.  csda_out[table_points] (may be NULL) receives the CSDA range
+ * at unit density (g/cm^2, FP64 quadrature).  Synchronous. */
+int sde_dose_tables(const sde_dose* d, int m, float* out, float* rates_out, double* csda_out);
+
+/* Single-step probe: for n independent histories h0..h0+n-1 at energy E (MeV)
+ * along +z in an unbounded medium of material m and density rho, take one
+ * step of the transport kernel's step function (same tables, same random
+ * stream: step 0 of history h, exponential jump clock started from the
+ * history's source draw) and write (each may be NULL) E_out (energy after the
+ * step), cos_out (new direction . old), jump_out (0 none, 1 elastic,
+ * 2 non-elastic), ux_out/uy_out.  All outputs are HOST arrays of n elements.
+ * Synchronous.  For tests of the step against the oracle. */
+int sde_dose_probe_steps(sde_dose* d, int m, double rho, double E, uint64_t seed, uint64_t h0,
+                         int n, float* E_out, float* cos_out, int* jump_out, float* ux_out,
+                         float* uy_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,275 @@
+"""Python binding of the GB300 jump-SDE proton dose engine (``libsde_dose.so``).
+
+Argument marshalling only: every step of the transport runs in the library's
+CUDA kernels.  The C functions keep their names (``sde_dose_create``,
+``sde_dose_run``, ``sde_dose_fetch`` ...; see ``include/sde_dose.h``); the
+``SdeDose`` class wraps a handle for numpy / torch callers.  Importing this
+package does not build or load anything; the first call that needs the
+library loads it and raises ``SdeError`` if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libsde_dose.so")
+_lock = threading.Lock()
+_lib = None
+
+SDE_OK, SDE_EINVAL, SDE_ENOMEM, SDE_ECUDA, SDE_EDEVICE = 0, -1, -2, -3, -4
+PHYS_STRAGGLING, PHYS_MCS, PHYS_ELASTIC, PHYS_INELASTIC, PHYS_ALL = 1, 2, 4, 8, 15
+MAX_ELEMENTS = 16
+
+EXPORTED = [
+    "sde_default_params", "sde_last_error", "sde_dose_create", "sde_dose_set_stream",
+    "sde_dose_set_tuning", "sde_dose_get_tuning", "sde_dose_run", "sde_dose_run_device",
+    "sde_dose_sync", "sde_dose_fetch", "sde_dose_fetch_device", "sde_dose_reset",
+    "sde_dose_destroy", "sde_dose_info", "sde_dose_tables", "sde_dose_probe_steps",
+]
+
+
+class SdeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sde error {code}: {msg}")
+        self.code = code
+
+
+class ElementFrac(C.Structure):
+    _fields_ = [("Z", C.c_int), ("mass_fraction", C.c_double)]
+
+
+class Material(C.Structure):
+    _fields_ = [("el", C.POINTER(ElementFrac)), ("n_el", C.c_int), ("I_eV", C.c_double)]
+
+
+class Spot(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("E_MeV", "sigma_E_MeV", "x_mm", "y_mm", "z_mm", "ux",
+                                          "uy", "uz", "sigma_xy_mm", "sigma_angle_rad")] + [
+        ("n_hist", C.c_uint64)]
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("step_cm", "msc_z_cm", "F", "theta_cut_rad",
+                                          "backscatter_rad", "e_min_MeV", "K", "inel_u_lo",
+                                          "inel_u_hi", "km_r", "e_max_MeV")] + [
+        (n, C.c_int) for n in ("tally_mode", "fixed_point_shift", "max_steps", "physics_mask",
+                               "table_points")]
+
+
+class Balance(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("incident", "deposited", "escaped", "removed",
+                                          "histories", "steps", "jumps_elastic",
+                                          "jumps_inelastic")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class Tuning(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int), ("warps_per_block", C.c_int), ("batch", C.c_int)]
+
+
+assert C.sizeof(Spot) == 88
+
+
+def lib():
+    """Load ``libsde_dose.so`` (raises SdeError when it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise SdeError(SDE_ECUDA, f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d, u64 = C.c_void_p, C.c_int, C.c_double, C.c_uint64
+        L.sde_default_params.argtypes = [C.POINTER(Params)]
+        L.sde_last_error.restype = C.c_char_p
+        L.sde_dose_create.argtypes = [C.POINTER(vp), i, i, i, C.POINTER(d), C.POINTER(d), vp, vp,
+                                      C.POINTER(Material), i, C.POINTER(Params)]
+        L.sde_dose_set_stream.argtypes = [vp, vp]
+        L.sde_dose_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.sde_dose_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.sde_dose_run.argtypes = [vp, C.POINTER(Spot), i, u64]
+        L.sde_dose_run_device.argtypes = [vp, vp, i, u64]
+        L.sde_dose_sync.argtypes = [vp]
+        L.sde_dose_fetch.argtypes = [vp, vp, vp, C.POINTER(Balance)]
+        L.sde_dose_fetch_device.argtypes = [vp, vp, vp, C.POINTER(Balance)]
+        L.sde_dose_reset.argtypes = [vp]
+        L.sde_dose_destroy.argtypes = [vp]
+        L.sde_dose_destroy.restype = None
+        L.sde_dose_info.argtypes = [vp, C.POINTER(u64), C.POINTER(i), C.POINTER(d), C.POINTER(d),
+                                    C.POINTER(i)]
+        L.sde_dose_tables.argtypes = [vp, i, vp, vp, vp]
+        L.sde_dose_probe_steps.argtypes = [vp, i, d, d, u64, u64, i, vp, vp, vp, vp, vp]
+        _lib = L
+        return L
+
+
+def _check(rc):
+    if rc != SDE_OK:
+        raise SdeError(rc, lib().sde_last_error().decode())
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _check(lib().sde_default_params(C.byref(p)))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class _Materials:
+    def __init__(self, materials):
+        self._keep = []
+        self.arr = (Material * len(materials))()
+        for n, m in enumerate(materials):
+            els = (ElementFrac * len(m["elements"]))(*[ElementFrac(z, w) for z, w in m["elements"]])
+            self._keep.append(els)
+            self.arr[n] = Material(C.cast(els, C.POINTER(ElementFrac)), len(m["elements"]),
+                                   float(m.get("I_eV", 0.0)))
+
+
+def spots_to_ctypes(spots: np.ndarray):
+    """A numpy structured spot array (88-byte records) viewed as ``Spot`` records."""
+    a = np.ascontiguousarray(spots)
+    if a.dtype.itemsize != C.sizeof(Spot):
+        raise ValueError("spot records must be 88 bytes (10 float64 + uint64)")
+    return a, C.cast(a.ctypes.data, C.POINTER(Spot))
+
+
+class SdeDose:
+    """One engine handle: phantom, tables and tally on the current CUDA device.
+
+    ``wl`` is a workload with ``shape`` (nx, ny, nz), ``voxel_mm``, ``origin_mm``,
+    ``density`` / ``material_id`` (x-fastest, shape (nz, ny, nx)), ``materials``.
+    """
+
+    def __init__(self, wl, stream=None, tuning=None, **param_kw):
+        L = lib()
+        self.shape = tuple(wl.shape)
+        self.wl = wl
+        dens = np.ascontiguousarray(wl.density, np.float32)
+        mid = np.ascontiguousarray(wl.material_id, np.uint8)
+        mats = _Materials(wl.materials)
+        self.params = default_params(**param_kw)
+        h = C.c_void_p()
+        nx, ny, nz = self.shape
+        _check(L.sde_dose_create(C.byref(h), nx, ny, nz, (C.c_double * 3)(*wl.voxel_mm),
+                                 (C.c_double * 3)(*wl.origin_mm), dens.ctypes.data, mid.ctypes.data,
+                                 mats.arr, len(wl.materials), C.byref(self.params)))
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+        if tuning:
+            self.set_tuning(**tuning)
+
+    # -- configuration
+    def set_stream(self, stream):
+        ptr = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
+        _check(lib().sde_dose_set_stream(self.h, C.c_void_p(ptr)))
+
+    def set_tuning(self, blocks_per_sm=0, warps_per_block=0, batch=0):
+        _check(lib().sde_dose_set_tuning(self.h, C.byref(Tuning(blocks_per_sm, warps_per_block, batch))))
+
+    def get_tuning(self):
+        t = Tuning()
+        _check(lib().sde_dose_get_tuning(self.h, C.byref(t)))
+        return {"blocks_per_sm": t.blocks_per_sm, "warps_per_block": t.warps_per_block, "batch": t.batch}
+
+    # -- work
+    def run(self, spots, seed=0):
+        a, ptr = spots_to_ctypes(spots)
+        _check(lib().sde_dose_run(self.h, ptr, len(a), C.c_uint64(seed)))
+
+    def run_device(self, d_spots_ptr: int, n_spots: int, seed=0):
+        _check(lib().sde_dose_run_device(self.h, C.c_void_p(d_spots_ptr), int(n_spots), C.c_uint64(seed)))
+
+    def sync(self):
+        _check(lib().sde_dose_sync(self.h))
+
+    def reset(self):
+        _check(lib().sde_dose_reset(self.h))
+
+    def fetch(self, dose=True, edep=True):
+        nx, ny, nz = self.shape
+        d = np.empty((nz, ny, nx), np.float64) if dose else None
+        e = np.empty((nz, ny, nx), np.uint64) if edep else None
+        bal = Balance()
+        _check(lib().sde_dose_fetch(self.h, d.ctypes.data if dose else None,
+                                    e.ctypes.data if edep else None, C.byref(bal)))
+        return d, e, bal.as_dict()
+
+    def fetch_into(self, dose_ptr=None, edep_ptr=None, balance=True):
+        """Host (pinned or pageable) output pointers; returns the balance dict."""
+        bal = Balance()
+        _check(lib().sde_dose_fetch(self.h, C.c_void_p(dose_ptr) if dose_ptr else None,
+                                    C.c_void_p(edep_ptr) if edep_ptr else None,
+                                    C.byref(bal) if balance else None))
+        return bal.as_dict()
+
+    def fetch_device(self, dose_ptr=None, edep_ptr=None, balance=False):
+        bal = Balance()
+        _check(lib().sde_dose_fetch_device(self.h, C.c_void_p(dose_ptr) if dose_ptr else None,
+                                           C.c_void_p(edep_ptr) if edep_ptr else None,
+                                           C.byref(bal) if balance else None))
+        return bal.as_dict() if balance else None
+
+    # -- introspection
+    def info(self):
+        nv, tp, n_m = C.c_uint64(), C.c_int(), C.c_int()
+        emin, emax = C.c_double(), C.c_double()
+        _check(lib().sde_dose_info(self.h, C.byref(nv), C.byref(tp), C.byref(emin), C.byref(emax),
+                                   C.byref(n_m)))
+        return {"n_vox": nv.value, "table_points": tp.value, "e_min": emin.value, "e_max": emax.value,
+                "n_mats": n_m.value}
+
+    def tables(self, m):
+        inf = self.info()
+        N = inf["table_points"]
+        n_el = len(self.wl.materials[m]["elements"])
+        raw = np.empty((N, 5), np.float32)
+        rates = np.empty((N, 2, n_el), np.float32)
+        csda = np.empty(N, np.float64)
+        _check(lib().sde_dose_tables(self.h, int(m), raw.ctypes.data, rates.ctypes.data, csda.ctypes.data))
+        E = inf["e_min"] * (inf["e_max"] / inf["e_min"]) ** (np.arange(N) / (N - 1))
+        return {"E": E, "s1": raw[:, 0], "s2sq": raw[:, 1], "chi_c2": raw[:, 2], "bfac": raw[:, 3],
+                "sig_jump": raw[:, 4], "rates": rates, "csda": csda}
+
+    def probe_steps(self, m, rho, E, n, seed=0, h0=0):
+        out = {k: np.empty(n, np.float32) for k in ("E", "cos", "ux", "uy")}
+        out["jump"] = np.empty(n, np.int32)
+        _check(lib().sde_dose_probe_steps(self.h, int(m), float(rho), float(E), C.c_uint64(seed),
+                                          C.c_uint64(h0), int(n), out["E"].ctypes.data,
+                                          out["cos"].ctypes.data, out["jump"].ctypes.data,
+                                          out["ux"].ctypes.data, out["uy"].ctypes.data))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sde_dose_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_workload(wl, seed=None, spots=None, **param_kw):
+    """Create, run and fetch in one call; returns (dose_Gy, edep_fixed, balance)."""
+    with SdeDose(wl, **param_kw) as d:
+        d.run(wl.spots if spots is None else spots, wl.seed if seed is None else seed)
+        return d.fetch()

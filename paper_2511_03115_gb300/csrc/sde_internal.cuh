@@ -1,0 +1,154 @@
+// sde_internal.cuh -- shared definitions of the GB300 jump-SDE proton dose
+// engine (arXiv 2511.03115): device data layouts, kernel parameter block,
+// Philox4x32-10 stream, and the device-side samplers of the large-angle laws.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sde_dose.h"
+
+namespace sde {
+
+// ----------------------------------------------------------------- constants
+// CODATA 2018 (MeV, cm, fm).
+constexpr double kProtonMass = 938.27208816;
+constexpr double kElectronMass = 0.51099895000;
+constexpr double kAtomicMassUnit = 931.49410242;
+constexpr double kAvogadro = 6.02214076e23;
+constexpr double kFineStructure = 1.0 / 137.035999084;
+constexpr double kHbarcMeVfm = 197.3269804;
+constexpr double kJoulePerMeV = 1.602176634e-13;
+constexpr double kPi = 3.14159265358979323846;
+constexpr float kTwoPiF = 6.28318530717958648f;
+
+// Random stream tags (second counter word of Philox).
+enum : uint32_t { kTagStep = 0, kTagJumpA = 1, kTagJumpB = 2, kTagSrcA = 3, kTagSrcB = 4 };
+
+// Error flag bits raised on the device.
+enum : uint32_t { kErrStepCap = 1u, kErrBadSpot = 2u, kErrNaN = 4u };
+
+// Hot table row per (material, energy point E_k): three float4 =
+//   {f1, df1, f2, df2}  f1 = varsigma_1 beta^2 Delta / rho, f2 = sqrt(varsigma_2^2 Delta / rho)
+//   {bt, dbt, fe, dfe}  bt = 1/(2 chi_alpha^2 (1-F) p^2), fe = sigma_e E^2 Delta / rho
+//   {fn, dfn, cw, ct}   fn = sigma_ne Delta / rho; material constants
+//                       cw = chi_c^2 (p beta)^2 / rho, ct = cw Delta / (z (1+F^2))
+// Value at fractional grid position k + f is v + f dv (linear in ln E).  The
+// fields are scaled by kinematic factors so that they are nearly linear in
+// ln E; the kernel multiplies the factors back from E.
+constexpr int kRowFloat4 = 3;
+constexpr int kRawFields = 5;
+
+// Element data of a material as seen by the jump sampler.
+struct MatJump {
+    int n_el;
+    int Z[SDE_MAX_ELEMENTS];
+    float A[SDE_MAX_ELEMENTS];   // standard atomic weight
+    float m2[SDE_MAX_ELEMENTS];  // target rest energy, MeV
+};
+
+// Beam spot in device form: position relative to the phantom origin (mm),
+// unit direction and the two unit vectors spanning the lateral plane.
+struct SpotDev {
+    float E, sE, sxy, sang;
+    float px, py, pz, pad0;
+    float ux, uy, uz, pad1;
+    float e1x, e1y, e1z, pad2;
+    float e2x, e2y, e2z, pad3;
+};
+
+// Balance counters (device, u64) in this order, then the work-queue cursor.
+enum { kCntIncident = 0, kCntDeposited, kCntEscaped, kCntRemoved, kCntHistories, kCntSteps,
+       kCntJumpEl, kCntJumpInel, kCntCursor, kCntWords };
+
+// Everything the transport kernel reads, passed by value (constant bank).
+struct KParams {
+    int nx, ny, nz, n_mats;
+    float inv_hx, inv_hy, inv_hz;
+    float step_mm, half_step_mm;
+    float e_min, e_max;
+    float qscale;  // 2^S
+    int max_steps, mask, tally_mode, N;
+    float lg2_emin, inv_dlg2;  // grid position = (log2 E - lg2_emin) * inv_dlg2
+    float s_cut;               // 1 - cos(theta_cut)
+    float ruth_span;           // 1/s_cut - 1/2
+    float s_back;              // 1 - cos(backscatter limit)
+    float inel_lo, inel_span, km_r;
+    int batch;
+    uint32_t rk0[10], rk1[10];  // Philox round keys
+    const float* __restrict__ rho;
+    const uint8_t* __restrict__ mat;
+    unsigned long long* __restrict__ edep;
+    const float4* __restrict__ table;  // [n_mats][N][kRowFloat4]
+    const float* __restrict__ jrates;  // [n_mats][N][2*SDE_MAX_ELEMENTS] per unit density
+    const MatJump* __restrict__ mats;
+    const SpotDev* __restrict__ spots;
+    const unsigned long long* __restrict__ prefix;  // [n_spots+1]
+    int n_spots;
+    unsigned long long* counters;  // kCntWords
+    unsigned int* err;
+};
+
+// ------------------------------------------------------------ Philox4x32-10
+// Salmon et al., SC'11.  Counter (n, tag, h_lo, h_hi); the ten round keys of
+// the seed are precomputed on the host (Weyl sequence 0x9E3779B9, 0xBB67AE85).
+__device__ __forceinline__ uint4 philox(const KParams& P, uint32_t n, uint32_t tag, uint64_t h) {
+    uint32_t c0 = n, c1 = tag, c2 = (uint32_t)h, c3 = (uint32_t)(h >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ P.rk0[r];
+        uint32_t n2 = hi0 ^ c3 ^ P.rk1[r];
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// 24 high bits of x as a float strictly inside (0,1).
+__device__ __forceinline__ float u01(uint32_t x) {
+    return __uint2float_rz(x >> 8) * 5.9604644775390625e-8f + 2.98023223876953125e-8f;
+}
+
+__device__ __forceinline__ unsigned long long qfix(const KParams& P, float E) {
+    return __float2ull_rn(E * P.qscale);
+}
+
+// cos and sin of a small polar angle given theta^2 (series when small).
+__device__ __forceinline__ void cos_sin_from_sq(float th2, float& c, float& s) {
+    if (th2 < 0.05f) {
+        // Taylor series of cos and sin/theta in theta^2
+        c = 1.f + th2 * (-0.5f + th2 * (1.f / 24.f + th2 * (-1.f / 720.f)));
+        float so = 1.f + th2 * (-1.f / 6.f + th2 * (1.f / 120.f + th2 * (-1.f / 5040.f)));
+        s = so * sqrtf(th2);
+    } else {
+        sincosf(sqrtf(th2), &s, &c);
+    }
+}
+
+// Rotate unit vector u by polar angle (cos_t, sin_t) and azimuth (cos_p, sin_p)
+// about itself, with the branch-free orthonormal basis of Duff et al. (JCGT
+// 2017); renormalised.
+__device__ __forceinline__ void rotate(float& ux, float& uy, float& uz, float cos_t, float sin_t,
+                                       float cos_p, float sin_p) {
+    float sg = copysignf(1.f, uz);
+    float a = -1.f / (sg + uz);
+    float b = ux * uy * a;
+    float e1x = 1.f + sg * ux * ux * a, e1y = sg * b, e1z = -sg * ux;
+    float e2x = b, e2y = sg + uy * uy * a, e2z = -uy;
+    float tx = cos_p * e1x + sin_p * e2x;
+    float ty = cos_p * e1y + sin_p * e2y;
+    float tz = cos_p * e1z + sin_p * e2z;
+    float nx = cos_t * ux + sin_t * tx;
+    float ny = cos_t * uy + sin_t * ty;
+    float nz = cos_t * uz + sin_t * tz;
+    float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
+    ux = nx * inv;
+    uy = ny * inv;
+    uz = nz * inv;
+}
+
+}  // namespace sde

@@ -1,0 +1,37 @@
+// sde_tables.h -- host interface of the physics-table builder.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "sde_dose.h"
+
+namespace sde {
+
+// A material resolved against the element table (host and device copy).
+struct MatHost {
+    int n_el;
+    int Z[SDE_MAX_ELEMENTS];
+    double A[SDE_MAX_ELEMENTS];
+    double w[SDE_MAX_ELEMENTS];  // renormalised mass fractions
+    double I_eV_el[SDE_MAX_ELEMENTS];
+    double I_eV;  // of the medium (given or Bragg-additive)
+};
+
+bool element_row(int Z, double* A, double* I_eV);
+int resolve_material(const sde_material& m, MatHost* out, char* err, size_t errlen);
+
+struct TableBuild {
+    int N, n_mats;
+    double e_min, e_max, K, F, z, step, theta_cut, theta_back;
+    int mask;
+    const MatHost* d_mats;
+    float* d_raw;
+    float* d_jrates;
+    double* d_csda;
+    float4* d_table;
+};
+
+cudaError_t build_tables(const TableBuild& tb, cudaStream_t st);
+
+}  // namespace sde

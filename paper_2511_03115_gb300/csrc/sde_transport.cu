@@ -1,0 +1,616 @@
+// sde_transport.cu -- persistent transport kernel of the jump-SDE proton
+// engine (arXiv 2511.03115, Sec. 2.1.2, Eq. VSDE) and its small companions
+// (spot preparation, single-step probe, dose conversion).
+//
+// Execution model: one proton history per lane.  Warps are persistent: a warp
+// claims a batch of history ids from a global cursor, hands them to its idle
+// lanes, and advances all live lanes one Euler-Maruyama step per iteration.
+// When lanes die (absorbed or escaped) the warp refills them from its batch
+// (ballot + popc ranks), so every warp keeps 32 lanes busy until the queue is
+// drained.  The per-step physics comes from FP32 tables staged in shared
+// memory; each step draws one Philox4x32-10 block keyed by (seed, history,
+// step); the energy lost in the step is committed as a 64-bit fixed-point
+// integer atomic, so the tally does not depend on execution order.
+#include <math.h>
+
+#include "sde_internal.cuh"
+#include "sde_transport.h"
+
+namespace sde {
+
+// Per-unit-density step quantities at one energy (see the hot-row layout in
+// sde_internal.cuh): c = varsigma_1 Delta, s = sqrt(varsigma_2^2 Delta),
+// w = Lynch-Dahl w, tg = t / g(w) (Brownian time over g), sj = jump rate x Delta.
+struct Phys {
+    float c, s, w, tg, sj;
+};
+
+__device__ __forceinline__ void grid_pos(const KParams& P, float E, int& k, float& f) {
+    float xf = (__log2f(E) - P.lg2_emin) * P.inv_dlg2;
+    xf = fminf(fmaxf(xf, 0.f), (float)(P.N - 1));
+    k = min((int)xf, P.N - 2);
+    f = xf - (float)k;
+}
+
+__device__ __forceinline__ Phys lookup(const float4* tab, const KParams& P, int m, float E) {
+    int k;
+    float f;
+    grid_pos(P, E, k, f);
+    const float4* r = tab + ((size_t)m * P.N + k) * kRowFloat4;
+    float4 a = r[0], b = r[1], c = r[2];
+    const float mp = (float)kProtonMass;
+    float tot = E + mp;
+    float rp2 = __fdividef(1.f, E * (E + 2.f * mp));  // 1/p^2
+    float ib2 = tot * tot * rp2;                      // 1/beta^2
+    float rE = __fdividef(1.f, E);
+    Phys ph;
+    ph.c = fmaf(a.y, f, a.x) * ib2;
+    ph.s = fmaf(a.w, f, a.z);
+    ph.w = c.z * fmaf(b.y, f, b.x) * ib2;
+    ph.tg = c.w * ib2 * rp2;
+    ph.sj = fmaf(fmaf(b.w, f, b.z), rE * rE, fmaf(c.y, f, c.x));
+    return ph;
+}
+
+// ------------------------------------------------------------ jump samplers
+// Identical-particle Coulomb law of hydrogen on [-cos(theta_b), cos(theta_c)]
+// (CM cosine), inverted by Newton's method on its closed-form primitive
+// G(mu) = 2 mu/(1-mu^2) - sin(eta ln((1+mu)/(1-mu)))/(2 eta), which is odd in
+// mu: the root is sought in the forward variable s = 1 - |mu| and mirrored.
+__device__ void mott_sample(float U, float eta, float s_cut, float s_back, float& c, float& sn) {
+    auto prim = [&](float s) {
+        float L = logf((2.f - s) / s);
+        return 2.f * (1.f - s) / (s * (2.f - s)) - sinf(eta * L) / (2.f * eta);
+    };
+    float g_hi = prim(s_cut), g_lo = -prim(s_back);
+    float target = g_lo + U * (g_hi - g_lo);
+    float sg = target >= 0.f ? 1.f : -1.f;
+    float y = fabsf(target);
+    float q = sqrtf(1.f + y * y);
+    float s = (1.f + 1.f / (q + y)) / (1.f + q);  // root without the sine term
+    float s_min = sg > 0.f ? s_cut : s_back;
+    for (int it = 0; it < 6; ++it) {
+        float mu = 1.f - s, om2 = s * (2.f - s);
+        float L = logf((2.f - s) / s);
+        float G = 2.f * mu / om2 - sinf(eta * L) / (2.f * eta);
+        float dG = 2.f * (1.f + mu * mu) / (om2 * om2) - cosf(eta * L) / om2;
+        s = fminf(fmaxf(s + (G - y) / dG, s_min), 1.f);
+    }
+    c = sg * (1.f - s);
+    sn = sqrtf(s * (2.f - s));
+}
+
+// Kalbach-Mann angular law a/(2 sinh a) (cosh(a mu) + r sinh(a mu)): the CDF
+// is quadratic in T = exp(a mu); the stable root is taken on either sign of C.
+__device__ float kalbach_mu(float U, float a, float r) {
+    if (a < 1e-4f) return 2.f * U - 1.f;
+    float ea = expf(a), eb = 1.f / ea;
+    float sh = 0.5f * (ea - eb), ch = 0.5f * (ea + eb);
+    float C = 2.f * sh * U + r * ch - sh;
+    float q = sqrtf(C * C + (1.f - r) * (1.f + r));
+    float T = C >= 0.f ? (C + q) / (1.f + r) : (1.f - r) / (q - C);
+    return fminf(fmaxf(logf(T) / a, -1.f), 1.f);
+}
+
+// Kalbach (1988) slope parameter for proton in / proton out, separation
+// energies neglected: e_a = E m2/(m_p+m2) (CM), e_b = (1-u) e_a.
+__device__ float kalbach_a(float E, float u, float A) {
+    float m2 = A * (float)kAtomicMassUnit;
+    float ea = E * m2 / ((float)kProtonMass + m2);
+    float X1 = fminf(ea, 130.f) * (1.f - u);
+    float X3 = fminf(ea, 41.f) * (1.f - u);
+    return 0.04f * X1 + 1.8e-6f * X1 * X1 * X1 + 6.7e-7f * (X3 * X3) * (X3 * X3);
+}
+
+// CM -> lab polar angle (Appendix A.1).  Elastic: v'_1C = p m2/(m_p^2 + E_tot m2)
+// (the collinear Lorentz transform simplified); non-elastic: the printed
+// collinear transform of the outgoing lab energy, used as a speed.
+__device__ void cm_to_lab(float E, float Eout, bool elastic, float m2, float cc, float sc, float& cl,
+                          float& sl) {
+    const float mp = (float)kProtonMass;
+    float p1 = sqrtf(E * (E + 2.f * mp)), Et = E + mp;
+    float ucm = p1 / (Et + m2);
+    float gu = rsqrtf((1.f - ucm) * (1.f + ucm));
+    float v;
+    if (elastic) {
+        v = p1 * m2 / (mp * mp + Et * m2);
+    } else {
+        float po = sqrtf(Eout * (Eout + 2.f * mp)), Eo = Eout + mp;
+        v = fabsf(po - ucm * Eo) / (Eo - ucm * po);
+    }
+    float X = v * sc, Y = gu * (v * cc + ucm);
+    float inv = rsqrtf(X * X + Y * Y);
+    cl = Y * inv;
+    sl = X * inv;
+}
+
+// A large-angle event of Eq. Npi at pre-step energy E: pick channel and element
+// by rate, sample the CM angle, convert to the lab, rotate; non-elastic events
+// scale the post-loss energy E1 by (1-u).  Refreshes the exponential clock.
+__device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1, float& ux, float& uy,
+                                    float& uz, float& tau, uint64_t h, uint32_t n) {
+    uint4 J = philox(P, n, kTagJumpA, h);
+    const MatJump& mj = P.mats[m];
+    int k;
+    float f;
+    grid_pos(P, E, k, f);
+    const float* r0 = P.jrates + ((size_t)m * P.N + k) * (2 * SDE_MAX_ELEMENTS);
+    const float* r1 = r0 + 2 * SDE_MAX_ELEMENTS;
+    const float rE2 = __fdividef(1.f, E * E);  // elastic rates are stored times E^2
+    float total = 0.f;
+    for (int i = 0; i < mj.n_el; ++i) {
+        total += fmaf(r1[i] - r0[i], f, r0[i]) * rE2;
+        total += fmaf(r1[SDE_MAX_ELEMENTS + i] - r0[SDE_MAX_ELEMENTS + i], f, r0[SDE_MAX_ELEMENTS + i]);
+    }
+    float target = u01(J.x) * total, acc = 0.f;
+    int pick = -1, last = -1;
+    for (int ch = 0; ch < 2 && pick < 0; ++ch)
+        for (int i = 0; i < mj.n_el; ++i) {
+            int o = ch * SDE_MAX_ELEMENTS + i;
+            float rate = fmaf(r1[o] - r0[o], f, r0[o]) * (ch == 0 ? rE2 : 1.f);
+            if (rate <= 0.f) continue;
+            last = o;
+            acc += rate;
+            if (target < acc) {
+                pick = o;
+                break;
+            }
+        }
+    if (pick < 0) pick = last;
+    if (pick < 0) return 0;  // no channel open (cannot happen when the clock fired)
+    int el = pick % SDE_MAX_ELEMENTS;
+    bool elastic = pick < SDE_MAX_ELEMENTS;
+    float m2 = mj.m2[el];
+    float cc, sc, cl, sl;
+    if (elastic) {
+        if (mj.Z[el] == 1) {
+            float eta = (float)kFineStructure * rsqrtf(2.f * E / (float)kProtonMass);
+            mott_sample(u01(J.y), eta, P.s_cut, P.s_back, cc, sc);
+        } else {
+            float s = 1.f / (0.5f + u01(J.y) * P.ruth_span);
+            cc = 1.f - s;
+            sc = sqrtf(s * (2.f - s));
+        }
+        cm_to_lab(E, E, true, m2, cc, sc, cl, sl);
+    } else {
+        uint4 J2 = philox(P, n, kTagJumpB, h);
+        float uu = P.inel_lo + P.inel_span * u01(J.y);
+        float mu = kalbach_mu(u01(J2.x), kalbach_a(E, uu, mj.A[el]), P.km_r);
+        cc = mu;
+        sc = sqrtf(fmaxf(0.f, (1.f - mu) * (1.f + mu)));
+        cm_to_lab(E, E * (1.f - uu), false, m2, cc, sc, cl, sl);
+        E1 *= (1.f - uu);
+    }
+    float sp, cp;
+    __sincosf(kTwoPiF * u01(J.z), &sp, &cp);
+    rotate(ux, uy, uz, cl, sl, cp, sp);
+    tau = -__logf(u01(J.w));
+    return elastic ? 1 : 2;
+}
+
+// One Euler-Maruyama step of Eq. VSDE at Y_n = (E, ., u) in material m of
+// density rho.  On return E1 = energy after the continuous loss, E = energy
+// after any non-elastic event, u = new direction.  Returns 0/1/2 (no jump,
+// elastic, non-elastic).  The jump clock is exponential: tau ~ Exp(1) is
+// spent at rate sigma per unit path; crossing zero within a step is the
+// step's jump, which has probability 1 - exp(-Delta sigma) as in the paper.
+__device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int m, float rho, float& E,
+                                        float& ux, float& uy, float& uz, float& tau, uint64_t h,
+                                        uint32_t n, float& E1_out) {
+    Phys ph = lookup(tab, P, m, E);
+    uint4 x = philox(P, n, kTagStep, h);
+    float c = rho * ph.c;  // varsigma_1 Delta
+    float E1 = E - c;
+    if (P.mask & SDE_PHYS_STRAGGLING) {
+        float s = sqrtf(rho) * ph.s;  // varsigma_2 sqrt(Delta)
+        float r = sqrtf(-2.f * __logf(u01(x.x)));
+        float zE = r * __cosf(kTwoPiF * u01(x.y));
+        E1 += fminf(fmaxf(s * zE, -c), c);
+    }
+    E1 = fmaxf(E1, 0.f);
+    if (P.mask & SDE_PHYS_MCS) {
+        // Lynch-Dahl: w = chi_c^2/(2 chi_alpha^2 (1-F)), sigma^2 = chi_c^2/(1+F^2) g(w),
+        // g(w) = (1+w)/w ln(1+w) - 1; Brownian time t = sigma^2 Delta / z.
+        float w = rho * ph.w;
+        float g;
+        if (w >= 1.f)
+            g = (1.f + w) / w * __logf(1.f + w) - 1.f;
+        else if (w >= 0.01f)
+            g = (1.f + w) / w * log1pf(w) - 1.f;
+        else
+            g = w * (0.5f + w * (-1.f / 6.f + w * (1.f / 12.f)));
+        float t = rho * ph.tg * g;
+        float th2 = -2.f * t * __logf(u01(x.z));
+        float ct, st;
+        cos_sin_from_sq(th2, ct, st);
+        float sp, cp;
+        __sincosf(kTwoPiF * u01(x.w), &sp, &cp);
+        rotate(ux, uy, uz, ct, st, cp, sp);
+    }
+    E1_out = E1;
+    int jump = 0;
+    tau -= rho * ph.sj;
+    if (tau <= 0.f) jump = do_jump(P, m, E, E1, ux, uy, uz, tau, h, n);
+    E = E1;
+    return jump;
+}
+
+// Sample Y_0 of history h from its spot (binary search of the history prefix).
+__device__ __forceinline__ void init_history(const KParams& P, uint64_t h, float& E, float& px, float& py,
+                                             float& pz, float& ux, float& uy, float& uz, float& tau) {
+    int lo = 0, hi = P.n_spots;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (P.prefix[mid] <= h)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const SpotDev& s = P.spots[lo];
+    uint4 A = philox(P, 0u, kTagSrcA, h);
+    uint4 B = philox(P, 0u, kTagSrcB, h);
+    float r = sqrtf(-2.f * __logf(u01(A.x)));
+    float sa, ca;
+    __sincosf(kTwoPiF * u01(A.y), &sa, &ca);
+    float g1 = r * ca, g2 = r * sa;
+    float g3 = sqrtf(-2.f * __logf(u01(A.z))) * __cosf(kTwoPiF * u01(A.w));
+    E = fminf(fmaxf(s.E + s.sE * g3, P.e_min), P.e_max);
+    px = s.px + s.sxy * (g1 * s.e1x + g2 * s.e2x);
+    py = s.py + s.sxy * (g1 * s.e1y + g2 * s.e2y);
+    pz = s.pz + s.sxy * (g1 * s.e1z + g2 * s.e2z);
+    ux = s.ux;
+    uy = s.uy;
+    uz = s.uz;
+    if (s.sang > 0.f) {
+        float th2 = -2.f * __logf(u01(B.x)) * s.sang * s.sang;
+        float ct, st, sp, cp;
+        cos_sin_from_sq(th2, ct, st);
+        __sincosf(kTwoPiF * u01(B.y), &sp, &cp);
+        rotate(ux, uy, uz, ct, st, cp, sp);
+    }
+    tau = -__logf(u01(B.z));
+}
+
+__device__ __forceinline__ int voxel_index(const KParams& P, float px, float py, float pz) {
+    int ix = __float2int_rd(px * P.inv_hx);
+    int iy = __float2int_rd(py * P.inv_hy);
+    int iz = __float2int_rd(pz * P.inv_hz);
+    if ((unsigned)ix >= (unsigned)P.nx || (unsigned)iy >= (unsigned)P.ny || (unsigned)iz >= (unsigned)P.nz)
+        return -1;
+    return ix + P.nx * (iy + P.ny * iz);
+}
+
+// Split dq along the chord (ax,ay,az) + t (dx,dy,dz), t in [0,1], over the
+// voxels it crosses, in proportion to the length inside each (Amanatides-Woo
+// traversal).  Pieces are cumulative roundings of t dq, so they sum to dq.
+__device__ void deposit_chord(const KParams& P, float ax, float ay, float az, float dx, float dy, float dz,
+                              unsigned long long dq, unsigned long long& a_dep,
+                              unsigned long long& a_esc) {
+    float g[3] = {ax * P.inv_hx, ay * P.inv_hy, az * P.inv_hz};
+    float v[3] = {dx * P.inv_hx, dy * P.inv_hy, dz * P.inv_hz};
+    int n[3] = {P.nx, P.ny, P.nz};
+    int i[3], st[3];
+    float tmax[3], tdel[3];
+    for (int a = 0; a < 3; ++a) {
+        i[a] = __float2int_rd(g[a]);
+        if (v[a] > 0.f) {
+            st[a] = 1;
+            tmax[a] = ((float)(i[a] + 1) - g[a]) / v[a];
+            tdel[a] = 1.f / v[a];
+        } else if (v[a] < 0.f) {
+            st[a] = -1;
+            tmax[a] = ((float)i[a] - g[a]) / v[a];
+            tdel[a] = -1.f / v[a];
+        } else {
+            st[a] = 0;
+            tmax[a] = INFINITY;
+            tdel[a] = INFINITY;
+        }
+    }
+    float fq = (float)dq;
+    unsigned long long done = 0;
+    for (int it = 0; it < 32 && done < dq; ++it) {
+        float tn = fminf(fminf(tmax[0], tmax[1]), tmax[2]);
+        bool last = tn >= 1.f || it == 31;
+        unsigned long long upto = last ? dq : __float2ull_rn(tn * fq);
+        upto = upto < done ? done : (upto > dq ? dq : upto);
+        unsigned long long part = upto - done;
+        done = upto;
+        if (part) {
+            bool in = (unsigned)i[0] < (unsigned)n[0] && (unsigned)i[1] < (unsigned)n[1] &&
+                      (unsigned)i[2] < (unsigned)n[2];
+            if (in) {
+                atomicAdd(&P.edep[i[0] + P.nx * (i[1] + P.ny * i[2])], part);
+                a_dep += part;
+            } else {
+                a_esc += part;
+            }
+        }
+        if (last) break;
+        int ax_ = (tmax[0] <= tmax[1] && tmax[0] <= tmax[2]) ? 0 : (tmax[1] <= tmax[2] ? 1 : 2);
+        i[ax_] += st[ax_];
+        tmax[ax_] += tdel[ax_];
+    }
+}
+
+template <int TALLY, bool SMEM>
+__global__ void __launch_bounds__(256) k_transport(KParams P) {
+    extern __shared__ float4 s_tab[];
+    const float4* tab = P.table;
+    if (SMEM) {
+        int rows = P.n_mats * P.N * kRowFloat4;
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) s_tab[i] = P.table[i];
+        __syncthreads();
+        tab = s_tab;
+    }
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total = P.prefix[P.n_spots];
+    bool alive = false;
+    float E = 0.f, px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 1.f, tau = 1.f;
+    unsigned long long h = 0, qprev = 0;
+    uint32_t n = 0;
+    unsigned long long a_inc = 0, a_dep = 0, a_esc = 0, a_rem = 0;
+    uint32_t a_hist = 0, a_steps = 0, a_jel = 0, a_jin = 0;
+    unsigned long long b_next = 0, b_end = 0;
+    bool drained = false;
+
+    for (;;) {
+        unsigned dead = __ballot_sync(0xffffffffu, !alive);
+        while (dead && !drained) {
+            if (b_next >= b_end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&P.counters[kCntCursor], (unsigned long long)P.batch);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= total) {
+                    drained = true;
+                    break;
+                }
+                b_next = base;
+                b_end = min(base + (unsigned long long)P.batch, total);
+            }
+            int nd = __popc(dead);
+            unsigned long long avail = b_end - b_next;
+            int take = (unsigned long long)nd < avail ? nd : (int)avail;
+            int rank = __popc(dead & ((1u << lane) - 1u));
+            if (((dead >> lane) & 1u) && rank < take) {
+                h = b_next + (unsigned long long)rank;
+                init_history(P, h, E, px, py, pz, ux, uy, uz, tau);
+                qprev = qfix(P, E);
+                a_inc += qprev;
+                a_hist += 1;
+                n = 0;
+                alive = true;
+            }
+            b_next += (unsigned long long)take;
+            dead = __ballot_sync(0xffffffffu, !alive);
+        }
+        if (!__any_sync(0xffffffffu, alive)) break;
+        if (!alive) continue;
+
+        if (n >= (uint32_t)P.max_steps) {
+            atomicOr(P.err, kErrStepCap);
+            a_esc += qprev;
+            alive = false;
+            continue;
+        }
+        int v = voxel_index(P, px, py, pz);
+        if (v < 0) {  // R_n outside the domain D
+            a_esc += qprev;
+            alive = false;
+            continue;
+        }
+        int m = P.mat[v];
+        float rho = P.rho[v];
+        float oux = ux, ouy = uy, ouz = uz;
+        float E1;
+        int jump = sde_step(P, tab, m, rho, E, ux, uy, uz, tau, h, n, E1);
+        unsigned long long q1 = qfix(P, E1);
+        unsigned long long dq = qprev - q1;
+        if (TALLY == 0) {
+            // deposit at the step midpoint (Sec. 2.2.2)
+            int mv = voxel_index(P, px + oux * P.half_step_mm, py + ouy * P.half_step_mm,
+                                 pz + ouz * P.half_step_mm);
+            if (mv >= 0) {
+                if (dq) atomicAdd(&P.edep[mv], dq);
+                a_dep += dq;
+            } else {
+                a_esc += dq;
+            }
+        } else if (dq) {
+            deposit_chord(P, px, py, pz, oux * P.step_mm, ouy * P.step_mm, ouz * P.step_mm, dq, a_dep,
+                          a_esc);
+        }
+        px += oux * P.step_mm;
+        py += ouy * P.step_mm;
+        pz += ouz * P.step_mm;
+        if (jump == 2) {
+            unsigned long long q2 = qfix(P, E);
+            a_rem += q1 - q2;
+            q1 = q2;
+            a_jin += 1;
+        } else if (jump == 1) {
+            a_jel += 1;
+        }
+        qprev = q1;
+        n += 1;
+        a_steps += 1;
+        if (E < P.e_min) {  // absorbed; the rest is deposited where the proton is
+            int tv = voxel_index(P, px, py, pz);
+            if (tv >= 0) {
+                if (qprev) atomicAdd(&P.edep[tv], qprev);
+                a_dep += qprev;
+            } else {
+                a_esc += qprev;
+            }
+            alive = false;
+        }
+    }
+
+    // warp totals, one atomic per counter per warp
+    for (int off = 16; off > 0; off >>= 1) {
+        a_inc += __shfl_down_sync(0xffffffffu, a_inc, off);
+        a_dep += __shfl_down_sync(0xffffffffu, a_dep, off);
+        a_esc += __shfl_down_sync(0xffffffffu, a_esc, off);
+        a_rem += __shfl_down_sync(0xffffffffu, a_rem, off);
+        a_hist += __shfl_down_sync(0xffffffffu, a_hist, off);
+        a_steps += __shfl_down_sync(0xffffffffu, a_steps, off);
+        a_jel += __shfl_down_sync(0xffffffffu, a_jel, off);
+        a_jin += __shfl_down_sync(0xffffffffu, a_jin, off);
+    }
+    if (lane == 0) {
+        atomicAdd(&P.counters[kCntIncident], a_inc);
+        atomicAdd(&P.counters[kCntDeposited], a_dep);
+        atomicAdd(&P.counters[kCntEscaped], a_esc);
+        atomicAdd(&P.counters[kCntRemoved], a_rem);
+        atomicAdd(&P.counters[kCntHistories], (unsigned long long)a_hist);
+        atomicAdd(&P.counters[kCntSteps], (unsigned long long)a_steps);
+        atomicAdd(&P.counters[kCntJumpEl], (unsigned long long)a_jel);
+        atomicAdd(&P.counters[kCntJumpInel], (unsigned long long)a_jin);
+    }
+}
+
+// Spot records -> device form and the inclusive prefix of history counts;
+// resets the work-queue cursor.  One block.
+__global__ void __launch_bounds__(1024) k_prep_spots(const sde_spot* raw, int n, SpotDev* out,
+                                                     unsigned long long* prefix,
+                                                     unsigned long long* counters, unsigned int* err,
+                                                     double ox, double oy, double oz, double e_min,
+                                                     double e_lim) {
+    __shared__ unsigned long long scan[1024];
+    unsigned long long carry = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        unsigned long long nh = 0;
+        if (i < n) {
+            sde_spot s = raw[i];
+            double un = s.ux * s.ux + s.uy * s.uy + s.uz * s.uz;
+            bool ok = s.E_MeV > e_min && s.E_MeV + 5.0 * s.sigma_E_MeV <= e_lim && s.sigma_E_MeV >= 0.0 &&
+                      s.sigma_xy_mm >= 0.0 && s.sigma_xy_mm < 1e4 && s.sigma_angle_rad >= 0.0 &&
+                      s.sigma_angle_rad < 1.0 && un > 0.0 && isfinite(un) && isfinite(s.x_mm) &&
+                      isfinite(s.y_mm) && isfinite(s.z_mm);
+            SpotDev d = {};
+            if (ok) {
+                nh = s.n_hist;
+                double inv = rsqrt(un);
+                double x = s.ux * inv, y = s.uy * inv, z = s.uz * inv;
+                double sg = copysign(1.0, z);
+                double a = -1.0 / (sg + z), b = x * y * a;
+                d.E = (float)s.E_MeV;
+                d.sE = (float)s.sigma_E_MeV;
+                d.sxy = (float)s.sigma_xy_mm;
+                d.sang = (float)s.sigma_angle_rad;
+                d.px = (float)(s.x_mm - ox);
+                d.py = (float)(s.y_mm - oy);
+                d.pz = (float)(s.z_mm - oz);
+                d.ux = (float)x;
+                d.uy = (float)y;
+                d.uz = (float)z;
+                d.e1x = (float)(1.0 + sg * x * x * a);
+                d.e1y = (float)(sg * b);
+                d.e1z = (float)(-sg * x);
+                d.e2x = (float)b;
+                d.e2y = (float)(sg + y * y * a);
+                d.e2z = (float)(-y);
+            } else {
+                atomicOr(err, kErrBadSpot);
+            }
+            out[i] = d;
+        }
+        scan[threadIdx.x] = nh;
+        __syncthreads();
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            unsigned long long add = threadIdx.x >= (unsigned)off ? scan[threadIdx.x - off] : 0ull;
+            __syncthreads();
+            scan[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (i < n) prefix[i + 1] = carry + scan[threadIdx.x];
+        carry += scan[blockDim.x - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        prefix[0] = 0;
+        counters[kCntCursor] = 0;
+    }
+}
+
+__global__ void k_probe(KParams P, int m, float rho, float E0, uint64_t h0, int n, float* Eo, float* co,
+                        int* jo, float* uxo, float* uyo) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t h = h0 + (uint64_t)i;
+    uint4 B = philox(P, 0u, kTagSrcB, h);
+    float tau = -__logf(u01(B.z));
+    float E = E0, ux = 0.f, uy = 0.f, uz = 1.f, E1;
+    int j = sde_step(P, P.table, m, rho, E, ux, uy, uz, tau, h, 0u, E1);
+    Eo[i] = E;
+    co[i] = uz;
+    jo[i] = j;
+    uxo[i] = ux;
+    uyo[i] = uy;
+}
+
+// Dose to medium (Sec. 2.2.2): tally units -> J over voxel mass (kg).
+__global__ void k_convert(const unsigned long long* edep, const float* rho, size_t nv, double unit_J,
+                          double vol_kg_per_rho, double* dose) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        double mass = (double)rho[v] * vol_kg_per_rho;
+        dose[v] = mass > 0.0 ? (double)edep[v] * unit_J / mass : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <int TALLY, bool SMEM>
+static cudaError_t launch_t(const KParams& P, int grid, int block, size_t smem, cudaStream_t st) {
+    if (SMEM) {
+        cudaError_t e = cudaFuncSetAttribute(k_transport<TALLY, SMEM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_transport<TALLY, SMEM><<<grid, block, SMEM ? smem : 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_table, bool use_smem,
+                             cudaStream_t st) {
+    if (P.tally_mode == 0)
+        return use_smem ? launch_t<0, true>(P, grid, block, smem_table, st)
+                        : launch_t<0, false>(P, grid, block, 0, st);
+    return use_smem ? launch_t<1, true>(P, grid, block, smem_table, st)
+                    : launch_t<1, false>(P, grid, block, 0, st);
+}
+
+int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode) {
+    int nb = 0;
+    cudaError_t e;
+    if (tally_mode == 0)
+        e = use_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<0, true>, block, smem)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<0, false>, block, 0);
+    else
+        e = use_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<1, true>, block, smem)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<1, false>, block, 0);
+    return e == cudaSuccess ? nb : 0;
+}
+
+cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,
+                        unsigned long long* counters, unsigned int* err, const double o[3], double e_min,
+                        double e_lim, cudaStream_t st) {
+    k_prep_spots<<<1, 1024, 0, st>>>(raw, n, out, prefix, counters, err, o[0], o[1], o[2], e_min, e_lim);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe(const KParams& P, int m, float rho, float E0, uint64_t h0, int n, float* Eo,
+                         float* co, int* jo, float* uxo, float* uyo, cudaStream_t st) {
+    int threads = 256, blocks = (n + threads - 1) / threads;
+    k_probe<<<blocks, threads, 0, st>>>(P, m, rho, E0, h0, n, Eo, co, jo, uxo, uyo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const unsigned long long* edep, const float* rho, size_t nv, double unit_J,
+                           double vol_kg_per_rho, double* dose, int num_sms, cudaStream_t st) {
+    int blocks = num_sms * 4;
+    k_convert<<<blocks, 256, 0, st>>>(edep, rho, nv, unit_J, vol_kg_per_rho, dose);
+    return cudaGetLastError();
+}
+
+}  // namespace sde

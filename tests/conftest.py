@@ -18,3 +18,17 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def sde_gpu():
+    """The CUDA library, built in-tree, on a machine with a GPU (fails loudly otherwise)."""
+    from paper_2511_03115_gb300 import _build
+    _build.build()
+    import paper_2511_03115_gb300 as S
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("GPU tests need a CUDA device")
+    torch.cuda.init()
+    S.lib()
+    return S

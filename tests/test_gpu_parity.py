@@ -1,0 +1,255 @@
+"""Whole-transport parity of the CUDA path against the oracle on the seeded workloads.
+
+Agreement is statistical (the dose is a random field; see tests/statutil.py for the
+per-voxel criterion), the energy balance is exact, and the tally of a seed is
+bit-identical across runs and launch shapes."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import analysis as A
+from sde_workloads import WATER, insert150, plan2000, slab150, water100
+from statutil import balanced, compare
+
+pytestmark = pytest.mark.gpu
+
+B = 16  # independent batches per side
+
+
+def _gpu_batches(S, wl, n_total, seeds, **kw):
+    wl = wl.with_histories(n_total // len(seeds))
+    out, bals = [], []
+    with S.SdeDose(wl, **kw) as d:
+        for s in seeds:
+            d.reset()
+            d.run(wl.spots, seed=s)
+            dose, edep, bal = d.fetch()
+            assert balanced(bal) and int(edep.sum(dtype=np.uint64)) == bal["deposited"]
+            assert bal["histories"] == wl.n_histories
+            out.append(dose)
+            bals.append(bal)
+    return np.array(out), bals
+
+
+def _oracle_batches(wl, n_total, seeds, **kw):
+    wl = wl.with_histories(n_total // len(seeds))
+    out = []
+    d = O.OracleDose(wl, **kw)
+    try:
+        for s in seeds:
+            d.reset()
+            d.run(seed=s)
+            dose, _, bal = d.fetch()
+            assert balanced(bal)
+            out.append(dose)
+    finally:
+        d.close()
+    return np.array(out)
+
+
+def _r_levels(batches, hz, level):
+    z = A.z_centres(batches.shape[1], hz)
+    per = np.array([A.distal_range(A.idd(b), z, level) for b in batches])
+    full = A.distal_range(A.idd(batches.mean(0)), z, level)
+    return full, per.std(ddof=1) / math.sqrt(len(per))
+
+
+def _check_range(g, o, hz, tol_mm=0.05):
+    for level in (0.8, 0.9):
+        rg, sg = _r_levels(g, hz, level)
+        ro, so = _r_levels(o, hz, level)
+        assert abs(rg - ro) <= max(tol_mm, 3.0 * math.hypot(sg, so)), (level, rg, ro, sg, so)
+
+
+def test_water100_dose_parity(sde_gpu, oracle_lib):
+    """configs[0] workload: 100 MeV pencil beam in water, 40x40x120 mm at 1 mm."""
+    wl = water100()
+    n = 160_000
+    g, _ = _gpu_batches(sde_gpu, wl, n, range(B))
+    o = _oracle_batches(wl, n, range(100, 100 + B))
+    c = compare(g, o)
+    assert c["pass_frac"] >= 0.99, c
+    assert 0.6 < c["mean_z2"] < 1.5, c
+    _check_range(g, o, 1.0)
+
+
+def test_water100_at_its_stated_size(sde_gpu, oracle_lib):
+    """The workload exactly as stated (10^4 protons, seed 0): exact balance, determinism,
+    and a depth-dose range consistent with the oracle's run of the same size."""
+    wl = water100()
+    d1, e1, b1 = sde_gpu.run_workload(wl)
+    d2, e2, b2 = sde_gpu.run_workload(wl)
+    assert np.array_equal(e1, e2) and b1 == b2 and balanced(b1)
+    assert b1["histories"] == 10_000
+    _, eo, bo = O.run_workload(wl)
+    z = A.z_centres(120, 1.0)
+    rg = A.distal_range(A.idd(e1.astype(float)), z, 0.8)
+    ro = A.distal_range(A.idd(eo.astype(float)), z, 0.8)
+    assert abs(rg - ro) < 0.25  # 10^4 histories: statistical spread of R80 ~0.05 mm
+    assert abs(b1["incident"] - bo["incident"]) / bo["incident"] < 1e-9 + 1e-6
+
+
+def test_water100_common_random_numbers(sde_gpu, oracle_lib):
+    """With the oracle on the exponential jump clock both sides draw identical numbers for
+    every history; the tallies then agree far more tightly than independent runs."""
+    wl = water100(20_000)
+    _, eg, bg = sde_gpu.run_workload(wl, seed=3)
+    _, eo, bo = O.run_workload(wl, seed=3, jump_clock=1)
+    ig, io = A.idd(eg.astype(float)), A.idd(eo.astype(float))
+    assert np.max(np.abs(ig - io)) / io.max() < 0.01
+    assert abs(bg["jumps_inelastic"] - bo["jumps_inelastic"]) <= 0.01 * bo["jumps_inelastic"] + 5
+    assert abs(bg["jumps_elastic"] - bo["jumps_elastic"]) <= 0.01 * bo["jumps_elastic"] + 5
+    assert abs(bg["steps"] - bo["steps"]) <= 1e-3 * bo["steps"]
+
+
+def test_tally_is_independent_of_launch_shape(sde_gpu):
+    wl = water100(30_000)
+    outs = []
+    for tune in ({"warps_per_block": 8, "batch": 256}, {"warps_per_block": 2, "batch": 32},
+                 {"warps_per_block": 4, "batch": 1024, "blocks_per_sm": 1}):
+        with sde_gpu.SdeDose(wl, tuning=tune) as d:
+            d.run(wl.spots, seed=11)
+            outs.append(d.fetch()[1:])
+    for e, b in outs[1:]:
+        assert np.array_equal(e, outs[0][0]) and b == outs[0][1]
+
+
+def test_slab150_depth_dose_parity(sde_gpu, oracle_lib):
+    """configs[1] phantom (water / bone-like / lung-like / water slabs, 0.5 mm voxels)."""
+    wl = slab150()
+    n = 64_000
+    g, _ = _gpu_batches(sde_gpu, wl, n, range(B))
+    o = _oracle_batches(wl, n, range(200, 200 + B))
+    gi = np.array([A.idd(x) for x in g])[:, :, None, None]
+    oi = np.array([A.idd(x) for x in o])[:, :, None, None]
+    c = compare(gi, oi)
+    assert c["pass_frac"] >= 0.97, c
+    assert 0.5 < c["mean_z2"] < 1.6, c
+    _check_range(g, o, 0.5)
+    # coarse 3D blocks (2 mm x 2 mm x 2 mm) to keep per-voxel noise manageable
+    def coarse(x):
+        s = x.shape
+        return x.reshape(s[0], s[1] // 4, 4, s[2] // 4, 4, s[3] // 4, 4).sum(axis=(2, 4, 6))
+    c3 = compare(coarse(g), coarse(o))
+    assert c3["pass_frac"] >= 0.98, c3
+
+
+def test_insert150_lateral_profiles(sde_gpu, oracle_lib):
+    """configs[2] phantom: the half-space bone insert shifts half of the beam; lateral
+    profiles at five depths agree with the oracle within the statistical band."""
+    wl = insert150()
+    n = 64_000
+    g, _ = _gpu_batches(sde_gpu, wl, n, range(B))
+    o = _oracle_batches(wl, n, range(300, 300 + B))
+    z_idx = [20, 50, 90]
+    ig = A.idd(g.mean(0))
+    z = A.z_centres(200, 1.0)
+    # the two distal peaks (insert side and water side)
+    left = g.mean(0)[:, :, :40].sum(axis=(1, 2))
+    right = g.mean(0)[:, :, 40:].sum(axis=(1, 2))
+    z_idx += [int(np.argmax(right)), int(np.argmax(left))]
+    prof_g = np.array([[x[zi, 38:42, :].sum(axis=0) for zi in z_idx] for x in g])
+    prof_o = np.array([[x[zi, 38:42, :].sum(axis=0) for zi in z_idx] for x in o])
+    c = compare(prof_g, prof_o)
+    assert c["pass_frac"] >= 0.97, c
+    assert int(np.argmax(right)) < int(np.argmax(left))  # the bone side stops earlier
+
+
+def test_plan2000_block_parity(sde_gpu, oracle_lib):
+    """configs[3] phantom and spot list with a reduced history count (one launch carries all
+    2000 spots); 10 mm blocks agree with the oracle."""
+    wl = plan2000(total=1000)
+    n = 96_000
+    g, _ = _gpu_batches(sde_gpu, wl, n, range(B))
+    o = _oracle_batches(wl, n, range(400, 400 + B))
+    def coarse(x):
+        s = x.shape
+        return x.reshape(s[0], s[1] // 10, 10, s[2] // 10, 10, s[3] // 10, 10).mean(axis=(2, 4, 6))
+    c = compare(coarse(g), coarse(o))
+    assert c["pass_frac"] >= 0.98, c
+    assert 0.5 < c["mean_z2"] < 1.6, c
+
+
+def test_chord_split_tally_parity(sde_gpu, oracle_lib):
+    wl = water100()
+    n = 64_000
+    g, _ = _gpu_batches(sde_gpu, wl, n, range(B), tally_mode=1)
+    o = _oracle_batches(wl, n, range(500, 500 + B), tally_mode=1)
+    c = compare(g, o)
+    assert c["pass_frac"] >= 0.99, c
+    _check_range(g, o, 1.0)
+
+
+def test_device_resident_spots_on_a_torch_stream(sde_gpu):
+    import torch
+    wl = water100(20_000)
+    raw = torch.from_numpy(wl.spots.view(np.uint8).copy()).cuda()
+    st = torch.cuda.Stream()
+    with sde_gpu.SdeDose(wl, stream=st) as d:
+        d.run_device(raw.data_ptr(), len(wl.spots), seed=5)
+        dose_t = torch.empty(wl.n_voxels, dtype=torch.float64, device="cuda")
+        edep_t = torch.empty(wl.n_voxels, dtype=torch.int64, device="cuda")
+        bal = d.fetch_device(dose_t.data_ptr(), edep_t.data_ptr(), balance=True)
+        st.synchronize()
+        dose_h, edep_h, bal_h = d.fetch()
+    assert balanced(bal) and bal == bal_h
+    assert np.array_equal(edep_t.cpu().numpy().view(np.uint64).reshape(edep_h.shape), edep_h)
+    assert np.array_equal(dose_t.cpu().numpy().reshape(dose_h.shape), dose_h)
+    _, e_host, _ = sde_gpu.run_workload(wl, seed=5)
+    assert np.array_equal(e_host, edep_h)
+
+
+def test_step_cap_is_reported_and_balance_stays_exact(sde_gpu):
+    wl = water100(2000)
+    with sde_gpu.SdeDose(wl, max_steps=20) as d:
+        d.run(wl.spots, seed=1)
+        with pytest.raises(sde_gpu.SdeError) as ei:
+            d.sync()
+        assert ei.value.code == sde_gpu.SDE_EDEVICE and "step cap" in str(ei.value)
+        _, _, b = d.fetch()
+        assert balanced(b) and b["steps"] == 20 * 2000
+
+
+def test_invalid_device_spot_is_flagged(sde_gpu):
+    import torch
+    wl = water100(100)
+    bad = wl.spots.copy()
+    bad["E_MeV"] = -5.0
+    raw = torch.from_numpy(bad.view(np.uint8).copy()).cuda()
+    with sde_gpu.SdeDose(wl) as d:
+        d.run_device(raw.data_ptr(), 1, seed=0)
+        with pytest.raises(sde_gpu.SdeError) as ei:
+            d.sync()
+        assert "invalid device-resident spot" in str(ei.value)
+        _, _, b = d.fetch()
+        assert b["histories"] == 0 and b["incident"] == 0
+
+
+def test_host_spot_validation(sde_gpu):
+    wl = water100(10)
+    with sde_gpu.SdeDose(wl) as d:
+        bad = wl.spots.copy()
+        bad["E_MeV"] = 400.0
+        with pytest.raises(sde_gpu.SdeError):
+            d.run(bad)
+        bad = wl.spots.copy()
+        bad["uz"] = 0.0
+        with pytest.raises(sde_gpu.SdeError):
+            d.run(bad)
+
+
+def test_empty_spot_and_escape_only_beams(sde_gpu):
+    """A spot with zero histories runs nothing; a beam aimed away from the phantom only
+    escapes."""
+    wl = water100(1000)
+    sp = np.concatenate([wl.spots, wl.spots])
+    sp["n_hist"][0] = 0
+    _, e, b = sde_gpu.run_workload(wl, spots=sp)
+    assert b["histories"] == 1000 and balanced(b)
+    away = wl.spots.copy()
+    away["uz"] = -1.0
+    away["z_mm"] = -1.0
+    _, e, b = sde_gpu.run_workload(wl, spots=away)
+    assert e.sum() == 0 and b["escaped"] == b["incident"] > 0
