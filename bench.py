@@ -258,7 +258,7 @@ def main():
     # end to end through the public API with host buffers: spots H2D, dose D2H (pinned)
     host_dose = torch.empty(wl.n_voxels, dtype=torch.float64).pin_memory()
     e2e_times = []
-    for k in range(args.e2e_steps + 1):
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d.reset()
@@ -267,7 +267,7 @@ def main():
         t1 = time.perf_counter()
         if k > 0:
             e2e_times.append(t1 - t0)
-    e2e_T = sum(e2e_times) / len(e2e_times)
+    e2e_T = sum(e2e_times) / len(e2e_times) if e2e_times else float("nan")
     if ws > 1:
         t = torch.tensor([e2e_T], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

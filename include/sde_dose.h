@@ -99,7 +99,7 @@ typedef struct {
     int fixed_point_shift;  /* S: one tally unit = 2^-S MeV (24)                    */
     int max_steps;          /* step cap per history; exceeding it is SDE_EDEVICE    */
     int physics_mask;       /* SDE_PHYS_* (SDE_PHYS_ALL)                            */
-    int table_points;       /* points of the ln-E table grid, 64..4096 (512)        */
+    int table_points;       /* points of the ln-E table grid, 64..4096 (256)        */
 } sde_params;
 
 /* Energy balance in tally units: incident == deposited + escaped + removed
@@ -112,11 +112,14 @@ typedef struct {
 
 /* Launch shape of the transport kernel.  Zero fields keep the current value.
  * blocks_per_sm * warps_per_block warps run persistently; each warp claims
- * batch histories at a time from the shared work queue. */
+ * batch histories at a time from the shared work queue and refills its idle
+ * lanes once at least refill_min of them are idle (or all lanes are idle).
+ * The tally does not depend on these settings. */
 typedef struct {
-    int blocks_per_sm;   /* 1..8                    */
-    int warps_per_block; /* 1..32                   */
-    int batch;           /* 32..4096, multiple of 32 */
+    int blocks_per_sm;   /* 1..8 (default: as many as fit)      */
+    int warps_per_block; /* 1..8 (default 8)                     */
+    int batch;           /* 32..4096, multiple of 32 (default 32) */
+    int refill_min;      /* 1..32 (default 32: refill whole warps) */
 } sde_tuning;
 
 /* Fill p with the defaults listed above.  Returns SDE_OK or SDE_EINVAL (p NULL). */

@@ -690,6 +690,7 @@ static void sde_step(const or_mat* m, double rho, const oracle_params* p, uint64
     if (st > s1d) st = s1d;
     double E1 = *E - s1d + st;
     if (E1 < 0.0) E1 = 0.0;
+    if (E1 > *E) E1 = *E; /* (E - s1 Delta) + s1 Delta may round above E */
     ev->E1 = E1;
 
     /* Position line: R_{n+1} = R_n + Omega_n Delta (mm). */

@@ -16,7 +16,7 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libsde_dose.so")
+LIB_PATH = os.environ.get("SDE_DOSE_LIB") or os.path.join(_PKG, "_lib", "libsde_dose.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -70,7 +70,8 @@ class Balance(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("blocks_per_sm", C.c_int), ("warps_per_block", C.c_int), ("batch", C.c_int)]
+    _fields_ = [("blocks_per_sm", C.c_int), ("warps_per_block", C.c_int), ("batch", C.c_int),
+                ("refill_min", C.c_int)]
 
 
 assert C.sizeof(Spot) == 88
@@ -174,13 +175,14 @@ class SdeDose:
         ptr = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
         _check(lib().sde_dose_set_stream(self.h, C.c_void_p(ptr)))
 
-    def set_tuning(self, blocks_per_sm=0, warps_per_block=0, batch=0):
-        _check(lib().sde_dose_set_tuning(self.h, C.byref(Tuning(blocks_per_sm, warps_per_block, batch))))
+    def set_tuning(self, blocks_per_sm=0, warps_per_block=0, batch=0, refill_min=0):
+        t = Tuning(blocks_per_sm, warps_per_block, batch, refill_min)
+        _check(lib().sde_dose_set_tuning(self.h, C.byref(t)))
 
     def get_tuning(self):
         t = Tuning()
         _check(lib().sde_dose_get_tuning(self.h, C.byref(t)))
-        return {"blocks_per_sm": t.blocks_per_sm, "warps_per_block": t.warps_per_block, "batch": t.batch}
+        return {n: getattr(t, n) for n, _ in Tuning._fields_}
 
     # -- work
     def run(self, spots, seed=0):

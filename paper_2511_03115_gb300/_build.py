@@ -36,17 +36,17 @@ def _deps():
     return files
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(OUTDIR, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), lib_path: str = LIB) -> str:
+    os.makedirs(os.path.dirname(lib_path), exist_ok=True)
+    if not force and os.path.exists(lib_path):
+        t = os.path.getmtime(lib_path)
         if all(os.path.getmtime(f) <= t for f in _deps()):
-            return LIB
+            return lib_path
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUTDIR, src.replace(".cu", f".{os.getpid()}.o"))
+        obj = os.path.join(os.path.dirname(lib_path), src.replace(".cu", f".{os.getpid()}.o"))
         cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     for o in objs:
@@ -67,8 +67,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             pass
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -47,7 +47,7 @@ struct sde_dose {
     sde_tuning tune{};
     // device memory owned by the handle
     float* d_rho = nullptr;
-    uint8_t* d_mat = nullptr;
+    uint32_t* d_vox = nullptr;  // packed density | material id
     unsigned long long* d_edep = nullptr;
     MatHost* d_mats = nullptr;
     MatJump* d_mj = nullptr;
@@ -87,7 +87,7 @@ extern "C" int sde_default_params(sde_params* p) {
     p->fixed_point_shift = 24;
     p->max_steps = 100000;
     p->physics_mask = SDE_PHYS_ALL;
-    p->table_points = 512;
+    p->table_points = 256;
     return SDE_OK;
 }
 
@@ -106,7 +106,7 @@ static int check_params(const sde_params& p) {
 }
 
 static void free_all(sde_dose* d) {
-    void* ptrs[] = {d->d_rho,   d->d_mat,      d->d_edep,   d->d_mats,        d->d_mj,
+    void* ptrs[] = {d->d_rho,   d->d_vox,      d->d_edep,   d->d_mats,        d->d_mj,
                     d->d_raw,   d->d_jrates,   d->d_csda,   d->d_table,       d->d_counters,
                     d->d_err,   d->d_raw_spots, d->d_spots, d->d_prefix,      d->d_dose};
     for (void* p : ptrs)
@@ -171,7 +171,8 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     d->n_mats = n_mats;
     d->tune.blocks_per_sm = 0;  // 0: occupancy maximum
     d->tune.warps_per_block = 8;
-    d->tune.batch = 256;
+    d->tune.batch = 32;
+    d->tune.refill_min = 32;
 
     auto fail = [&](int rc) {
         free_all(d);
@@ -190,7 +191,7 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     TRY(cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, d->device));
     const int N = prm.table_points;
     TRY(cudaMalloc(&d->d_rho, nvox * sizeof(float)));
-    TRY(cudaMalloc(&d->d_mat, nvox));
+    TRY(cudaMalloc(&d->d_vox, nvox * sizeof(uint32_t)));
     TRY(cudaMalloc(&d->d_edep, nvox * sizeof(unsigned long long)));
     TRY(cudaMalloc(&d->d_mats, n_mats * sizeof(MatHost)));
     TRY(cudaMalloc(&d->d_mj, n_mats * sizeof(MatJump)));
@@ -204,7 +205,21 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     TRY(cudaMallocHost(&d->h_counters, (kCntWords + 1) * sizeof(unsigned long long)));
     TRY(cudaEventCreateWithFlags(&d->stage_ev, cudaEventDisableTiming));
     TRY(cudaMemcpy(d->d_rho, density, nvox * sizeof(float), cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(d->d_mat, material_id, nvox, cudaMemcpyHostToDevice));
+    {
+        // One 32-bit word per voxel for the transport kernel: the density rounded to
+        // 19 mantissa bits (relative change < 1e-6) with the material id in the low
+        // 4 bits.  The dose conversion keeps the exact densities.
+        uint32_t* packed = (uint32_t*)malloc(nvox * sizeof(uint32_t));
+        if (!packed) return fail(set_err(SDE_ENOMEM, "out of host memory"));
+        for (size_t v = 0; v < nvox; ++v) {
+            uint32_t bits;
+            memcpy(&bits, &density[v], sizeof bits);
+            packed[v] = ((bits + 8u) & ~15u) | (uint32_t)material_id[v];
+        }
+        cudaError_t e = cudaMemcpy(d->d_vox, packed, nvox * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        free(packed);
+        TRY(e);
+    }
     TRY(cudaMemcpy(d->d_mats, d->mats, n_mats * sizeof(MatHost), cudaMemcpyHostToDevice));
     TRY(cudaMemcpy(d->d_mj, d->mj, n_mats * sizeof(MatJump), cudaMemcpyHostToDevice));
     TRY(cudaMemset(d->d_edep, 0, nvox * sizeof(unsigned long long)));
@@ -244,12 +259,16 @@ extern "C" int sde_dose_set_stream(sde_dose* d, void* s) {
 extern "C" int sde_dose_set_tuning(sde_dose* d, const sde_tuning* t) {
     if (!d || !t) return set_err(SDE_EINVAL, "null argument");
     if (t->blocks_per_sm < 0 || t->blocks_per_sm > 8 || t->warps_per_block < 0 ||
-        t->warps_per_block > kMaxWarpsPerBlock || t->batch < 0 || t->batch > 4096 || (t->batch % 32) != 0)
-        return set_err(SDE_EINVAL, "tuning out of range (blocks_per_sm 0..8, warps_per_block 0..%d, batch multiple of 32 <= 4096)",
+        t->warps_per_block > kMaxWarpsPerBlock || t->batch < 0 || t->batch > 4096 || (t->batch % 32) != 0 ||
+        t->refill_min < 0 || t->refill_min > 32)
+        return set_err(SDE_EINVAL,
+                       "tuning out of range (blocks_per_sm 0..8, warps_per_block 0..%d, batch multiple of 32 <= 4096, "
+                       "refill_min 0..32)",
                        kMaxWarpsPerBlock);
     if (t->blocks_per_sm) d->tune.blocks_per_sm = t->blocks_per_sm;
     if (t->warps_per_block) d->tune.warps_per_block = t->warps_per_block;
     if (t->batch) d->tune.batch = t->batch;
+    if (t->refill_min) d->tune.refill_min = t->refill_min;
     return SDE_OK;
 }
 
@@ -305,13 +324,15 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
     P.inel_span = (float)(d->p.inel_u_hi - d->p.inel_u_lo);
     P.km_r = (float)d->p.km_r;
     P.batch = d->tune.batch;
+    P.refill_min = d->tune.refill_min;
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {
         P.rk0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
         P.rk1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
     }
-    P.rho = d->d_rho;
-    P.mat = d->d_mat;
+    P.strag_on = (d->p.physics_mask & SDE_PHYS_STRAGGLING) ? 1.f : 0.f;
+    P.mcs_on = (d->p.physics_mask & SDE_PHYS_MCS) ? 1.f : 0.f;
+    P.vox = d->d_vox;
     P.edep = d->d_edep;
     P.table = d->d_table;
     P.jrates = d->d_jrates;

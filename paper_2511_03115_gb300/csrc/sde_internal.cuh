@@ -74,10 +74,10 @@ struct KParams {
     float ruth_span;           // 1/s_cut - 1/2
     float s_back;              // 1 - cos(backscatter limit)
     float inel_lo, inel_span, km_r;
-    int batch;
+    int batch, refill_min;
     uint32_t rk0[10], rk1[10];  // Philox round keys
-    const float* __restrict__ rho;
-    const uint8_t* __restrict__ mat;
+    float strag_on, mcs_on;  // 1 or 0 (physics_mask)
+    const uint32_t* __restrict__ vox;  // packed voxel words (density | material id)
     unsigned long long* __restrict__ edep;
     const float4* __restrict__ table;  // [n_mats][N][kRowFloat4]
     const float* __restrict__ jrates;  // [n_mats][N][2*SDE_MAX_ELEMENTS] per unit density
@@ -108,9 +108,11 @@ __device__ __forceinline__ uint4 philox(const KParams& P, uint32_t n, uint32_t t
     return make_uint4(c0, c1, c2, c3);
 }
 
-// 24 high bits of x as a float strictly inside (0,1).
+// (x + 1/2) 2^-32 as a float in (0, 1]: full relative precision near 0, where
+// ln U is taken (the value rounds to 1 only for the top 2^7 words, where ln U = 0
+// is harmless).
 __device__ __forceinline__ float u01(uint32_t x) {
-    return __uint2float_rz(x >> 8) * 5.9604644775390625e-8f + 2.98023223876953125e-8f;
+    return fmaf(__uint2float_rn(x), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
 }
 
 __device__ __forceinline__ unsigned long long qfix(const KParams& P, float E) {

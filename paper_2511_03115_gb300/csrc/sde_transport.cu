@@ -189,44 +189,40 @@ __device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1,
 }
 
 // One Euler-Maruyama step of Eq. VSDE at Y_n = (E, ., u) in material m of
-// density rho.  On return E1 = energy after the continuous loss, E = energy
-// after any non-elastic event, u = new direction.  Returns 0/1/2 (no jump,
-// elastic, non-elastic).  The jump clock is exponential: tau ~ Exp(1) is
-// spent at rate sigma per unit path; crossing zero within a step is the
-// step's jump, which has probability 1 - exp(-Delta sigma) as in the paper.
-__device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int m, float rho, float& E,
-                                        float& ux, float& uy, float& uz, float& tau, uint64_t h,
+// density rho, with the step's Philox block x.  On return E1 = energy after the
+// continuous loss, E = energy after any non-elastic event, u = new direction.
+// Returns 0/1/2 (no jump, elastic, non-elastic).  The jump clock is
+// exponential: tau ~ Exp(1) is spent at rate sigma per unit path; crossing zero
+// within a step is the step's jump, which has probability 1 - exp(-Delta sigma)
+// as in the paper.  Switched-off terms are multiplied by zero (no branches).
+__device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int m, float rho, uint4 x,
+                                        float& E, float& ux, float& uy, float& uz, float& tau, uint64_t h,
                                         uint32_t n, float& E1_out) {
     Phys ph = lookup(tab, P, m, E);
-    uint4 x = philox(P, n, kTagStep, h);
-    float c = rho * ph.c;  // varsigma_1 Delta
-    float E1 = E - c;
-    if (P.mask & SDE_PHYS_STRAGGLING) {
-        float s = sqrtf(rho) * ph.s;  // varsigma_2 sqrt(Delta)
-        float r = sqrtf(-2.f * __logf(u01(x.x)));
-        float zE = r * __cosf(kTwoPiF * u01(x.y));
-        E1 += fminf(fmaxf(s * zE, -c), c);
-    }
-    E1 = fmaxf(E1, 0.f);
-    if (P.mask & SDE_PHYS_MCS) {
-        // Lynch-Dahl: w = chi_c^2/(2 chi_alpha^2 (1-F)), sigma^2 = chi_c^2/(1+F^2) g(w),
-        // g(w) = (1+w)/w ln(1+w) - 1; Brownian time t = sigma^2 Delta / z.
-        float w = rho * ph.w;
-        float g;
-        if (w >= 1.f)
-            g = (1.f + w) / w * __logf(1.f + w) - 1.f;
-        else if (w >= 0.01f)
-            g = (1.f + w) / w * log1pf(w) - 1.f;
-        else
-            g = w * (0.5f + w * (-1.f / 6.f + w * (1.f / 12.f)));
-        float t = rho * ph.tg * g;
-        float th2 = -2.f * t * __logf(u01(x.z));
-        float ct, st;
-        cos_sin_from_sq(th2, ct, st);
-        float sp, cp;
-        __sincosf(kTwoPiF * u01(x.w), &sp, &cp);
-        rotate(ux, uy, uz, ct, st, cp, sp);
-    }
+    float c = rho * ph.c;                   // varsigma_1 Delta
+    float s = sqrtf(rho) * ph.s * P.strag_on;  // varsigma_2 sqrt(Delta)
+    float r = sqrtf(-2.f * __logf(u01(x.x)));
+    float zE = r * __cosf(kTwoPiF * u01(x.y));
+    // The clamp keeps the energy non-increasing (Eq. VSDE); in FP32 (E - c) + c can
+    // round one ulp above E, which would make the step's fixed-point deposit negative.
+    float E1 = fminf(fmaxf(E - c + fminf(fmaxf(s * zE, -c), c), 0.f), E);
+    // Lynch-Dahl: w = chi_c^2/(2 chi_alpha^2 (1-F)), sigma^2 = chi_c^2/(1+F^2) g(w),
+    // g(w) = (1+w)/w ln(1+w) - 1; Brownian time t = sigma^2 Delta / z.
+    float w = rho * ph.w;
+    float g;
+    if (w >= 1.f)
+        g = (1.f + w) / w * __logf(1.f + w) - 1.f;
+    else if (w >= 0.01f)
+        g = (1.f + w) / w * log1pf(w) - 1.f;
+    else
+        g = w * (0.5f + w * (-1.f / 6.f + w * (1.f / 12.f)));
+    float t = rho * ph.tg * g * P.mcs_on;
+    float th2 = -2.f * t * __logf(u01(x.z));
+    float ct, st;
+    cos_sin_from_sq(th2, ct, st);
+    float sp, cp;
+    __sincosf(kTwoPiF * u01(x.w), &sp, &cp);
+    rotate(ux, uy, uz, ct, st, cp, sp);
     E1_out = E1;
     int jump = 0;
     tau -= rho * ph.sj;
@@ -279,6 +275,11 @@ __device__ __forceinline__ int voxel_index(const KParams& P, float px, float py,
         return -1;
     return ix + P.nx * (iy + P.ny * iz);
 }
+
+// Packed voxel word: density (FP32, low 4 mantissa bits rounded away) with the
+// material id in those 4 bits.
+__device__ __forceinline__ int vox_mat(uint32_t w) { return (int)(w & 15u); }
+__device__ __forceinline__ float vox_rho(uint32_t w) { return __uint_as_float(w & ~15u); }
 
 // Split dq along the chord (ax,ay,az) + t (dx,dy,dz), t in [0,1], over the
 // voxels it crosses, in proportion to the length inside each (Amanatides-Woo
@@ -333,8 +334,12 @@ __device__ void deposit_chord(const KParams& P, float ax, float ay, float az, fl
     }
 }
 
+#ifndef SDE_MIN_BLOCKS
+#define SDE_MIN_BLOCKS 3
+#endif
+
 template <int TALLY, bool SMEM>
-__global__ void __launch_bounds__(256) k_transport(KParams P) {
+__global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
     extern __shared__ float4 s_tab[];
     const float4* tab = P.table;
     if (SMEM) {
@@ -349,6 +354,11 @@ __global__ void __launch_bounds__(256) k_transport(KParams P) {
     float E = 0.f, px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 1.f, tau = 1.f;
     unsigned long long h = 0, qprev = 0;
     uint32_t n = 0;
+    // Software pipeline: the voxel word of R_n and the Philox block of step n are
+    // fetched/computed during step n-1, so their latency overlaps the step's work.
+    uint32_t vox = 0;
+    int vcur = -1;
+    uint4 x = make_uint4(0u, 0u, 0u, 0u);
     unsigned long long a_inc = 0, a_dep = 0, a_esc = 0, a_rem = 0;
     uint32_t a_hist = 0, a_steps = 0, a_jel = 0, a_jin = 0;
     unsigned long long b_next = 0, b_end = 0;
@@ -356,6 +366,7 @@ __global__ void __launch_bounds__(256) k_transport(KParams P) {
 
     for (;;) {
         unsigned dead = __ballot_sync(0xffffffffu, !alive);
+        if (dead != 0xffffffffu && __popc(dead) < P.refill_min) dead = 0;  // refill later
         while (dead && !drained) {
             if (b_next >= b_end) {
                 unsigned long long base = 0;
@@ -380,6 +391,9 @@ __global__ void __launch_bounds__(256) k_transport(KParams P) {
                 a_hist += 1;
                 n = 0;
                 alive = true;
+                vcur = voxel_index(P, px, py, pz);
+                vox = vcur >= 0 ? __ldg(&P.vox[vcur]) : 0u;
+                x = philox(P, 0u, kTagStep, h);
             }
             b_next += (unsigned long long)take;
             dead = __ballot_sync(0xffffffffu, !alive);
@@ -393,23 +407,31 @@ __global__ void __launch_bounds__(256) k_transport(KParams P) {
             alive = false;
             continue;
         }
-        int v = voxel_index(P, px, py, pz);
-        if (v < 0) {  // R_n outside the domain D
+        if (vcur < 0) {  // R_n outside the domain D
             a_esc += qprev;
             alive = false;
             continue;
         }
-        int m = P.mat[v];
-        float rho = P.rho[v];
-        float oux = ux, ouy = uy, ouz = uz;
+        const int m = vox_mat(vox);
+        const float rho = vox_rho(vox);
+        // Position line of Eq. VSDE along the pre-step direction; the next voxel word
+        // is requested now and consumed by the next step.
+        const float ox = px, oy = py, oz = pz, oux = ux, ouy = uy, ouz = uz;
+        px = fmaf(oux, P.step_mm, px);
+        py = fmaf(ouy, P.step_mm, py);
+        pz = fmaf(ouz, P.step_mm, pz);
+        const int vnext = voxel_index(P, px, py, pz);
+        const uint32_t vox_next = vnext >= 0 ? __ldg(&P.vox[vnext]) : 0u;
+        const uint4 xcur = x;
+        x = philox(P, n + 1u, kTagStep, h);
         float E1;
-        int jump = sde_step(P, tab, m, rho, E, ux, uy, uz, tau, h, n, E1);
+        int jump = sde_step(P, tab, m, rho, xcur, E, ux, uy, uz, tau, h, n, E1);
         unsigned long long q1 = qfix(P, E1);
         unsigned long long dq = qprev - q1;
         if (TALLY == 0) {
             // deposit at the step midpoint (Sec. 2.2.2)
-            int mv = voxel_index(P, px + oux * P.half_step_mm, py + ouy * P.half_step_mm,
-                                 pz + ouz * P.half_step_mm);
+            int mv = voxel_index(P, fmaf(oux, P.half_step_mm, ox), fmaf(ouy, P.half_step_mm, oy),
+                                 fmaf(ouz, P.half_step_mm, oz));
             if (mv >= 0) {
                 if (dq) atomicAdd(&P.edep[mv], dq);
                 a_dep += dq;
@@ -417,12 +439,8 @@ __global__ void __launch_bounds__(256) k_transport(KParams P) {
                 a_esc += dq;
             }
         } else if (dq) {
-            deposit_chord(P, px, py, pz, oux * P.step_mm, ouy * P.step_mm, ouz * P.step_mm, dq, a_dep,
-                          a_esc);
+            deposit_chord(P, ox, oy, oz, oux * P.step_mm, ouy * P.step_mm, ouz * P.step_mm, dq, a_dep, a_esc);
         }
-        px += oux * P.step_mm;
-        py += ouy * P.step_mm;
-        pz += ouz * P.step_mm;
         if (jump == 2) {
             unsigned long long q2 = qfix(P, E);
             a_rem += q1 - q2;
@@ -434,10 +452,11 @@ __global__ void __launch_bounds__(256) k_transport(KParams P) {
         qprev = q1;
         n += 1;
         a_steps += 1;
+        vcur = vnext;
+        vox = vox_next;
         if (E < P.e_min) {  // absorbed; the rest is deposited where the proton is
-            int tv = voxel_index(P, px, py, pz);
-            if (tv >= 0) {
-                if (qprev) atomicAdd(&P.edep[tv], qprev);
+            if (vcur >= 0) {
+                if (qprev) atomicAdd(&P.edep[vcur], qprev);
                 a_dep += qprev;
             } else {
                 a_esc += qprev;
@@ -542,7 +561,7 @@ __global__ void k_probe(KParams P, int m, float rho, float E0, uint64_t h0, int 
     uint4 B = philox(P, 0u, kTagSrcB, h);
     float tau = -__logf(u01(B.z));
     float E = E0, ux = 0.f, uy = 0.f, uz = 1.f, E1;
-    int j = sde_step(P, P.table, m, rho, E, ux, uy, uz, tau, h, 0u, E1);
+    int j = sde_step(P, P.table, m, rho, philox(P, 0u, kTagStep, h), E, ux, uy, uz, tau, h, 0u, E1);
     Eo[i] = E;
     co[i] = uz;
     jo[i] = j;
@@ -561,12 +580,15 @@ __global__ void k_convert(const unsigned long long* edep, const float* rho, size
 
 // ---------------------------------------------------------------- launchers
 template <int TALLY, bool SMEM>
+static cudaError_t allow_smem(size_t smem) {
+    if (!SMEM) return cudaSuccess;
+    return cudaFuncSetAttribute(k_transport<TALLY, SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int TALLY, bool SMEM>
 static cudaError_t launch_t(const KParams& P, int grid, int block, size_t smem, cudaStream_t st) {
-    if (SMEM) {
-        cudaError_t e = cudaFuncSetAttribute(k_transport<TALLY, SMEM>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_smem<TALLY, SMEM>(smem);
+    if (e != cudaSuccess) return e;
     k_transport<TALLY, SMEM><<<grid, block, SMEM ? smem : 0, st>>>(P);
     return cudaGetLastError();
 }
@@ -580,16 +602,19 @@ cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_
                     : launch_t<1, false>(P, grid, block, 0, st);
 }
 
-int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode) {
+template <int TALLY, bool SMEM>
+static int blocks_per_sm(int block, size_t smem) {
+    if (allow_smem<TALLY, SMEM>(smem) != cudaSuccess) return 0;
     int nb = 0;
-    cudaError_t e;
-    if (tally_mode == 0)
-        e = use_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<0, true>, block, smem)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<0, false>, block, 0);
-    else
-        e = use_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<1, true>, block, smem)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<1, false>, block, 0);
-    return e == cudaSuccess ? nb : 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<TALLY, SMEM>, block, SMEM ? smem : 0) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode) {
+    if (tally_mode == 0) return use_smem ? blocks_per_sm<0, true>(block, smem) : blocks_per_sm<0, false>(block, 0);
+    return use_smem ? blocks_per_sm<1, true>(block, smem) : blocks_per_sm<1, false>(block, 0);
 }
 
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,

@@ -5,9 +5,10 @@ Agreement criterion (per-voxel dose): with B independent batches per side (disjo
 random streams: one seed per batch), each voxel's mean dose carries a standard error
 from the batch spread.  In the region where either mean exceeds 1 % of D_max a voxel
 agrees when |D_gpu - D_oracle| <= max(3 sqrt(SE_gpu^2 + SE_oracle^2), 0.005 D_max).
-The test requires at least ``min_pass`` of the region to agree (the expected failure
-rate under identical distributions is below 1 % with B = 16 batches per side) and the
-mean squared z-score to stay near 1 (a systematic offset raises it).
+The tests require at least 98.5 % of the region to agree (with B = 16 batches per side
+the z-score follows a t distribution with about 30 degrees of freedom, so about 0.5 %
+of voxels exceed 3 by chance) and the mean squared z-score to stay near 1 (about 1.1 for
+that t distribution; a systematic offset raises it).
 """
 import numpy as np
 
@@ -40,4 +41,7 @@ def compare(gpu_batches, ora_batches, roi_frac=0.01, floor_frac=0.005):
 
 
 def balanced(b):
-    return b["incident"] == b["deposited"] + b["escaped"] + b["removed"]
+    """Exact balance, and no counter above the incident energy (a wrapped unsigned
+    difference would still balance modulo 2^64)."""
+    parts = (b["deposited"], b["escaped"], b["removed"])
+    return b["incident"] == sum(parts) and all(p <= b["incident"] for p in parts)

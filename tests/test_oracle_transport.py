@@ -12,7 +12,8 @@ from sde_workloads import WATER, Workload, pencil, slab150, water100
 
 
 def _balanced(b):
-    return b["incident"] == b["deposited"] + b["escaped"] + b["removed"]
+    parts = (b["deposited"], b["escaped"], b["removed"])
+    return b["incident"] == sum(parts) and all(x <= b["incident"] for x in parts)
 
 
 def test_energy_balance_is_exact(oracle_lib):
