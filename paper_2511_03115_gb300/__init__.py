@@ -29,6 +29,7 @@ EXPORTED = [
     "sde_dose_set_tuning", "sde_dose_get_tuning", "sde_dose_run", "sde_dose_run_device",
     "sde_dose_sync", "sde_dose_fetch", "sde_dose_fetch_device", "sde_dose_reset",
     "sde_dose_destroy", "sde_dose_info", "sde_dose_tables", "sde_dose_probe_steps",
+    "sde_transport_noalloc",
 ]
 
 
@@ -106,6 +107,8 @@ def lib():
                                     C.POINTER(i)]
         L.sde_dose_tables.argtypes = [vp, i, vp, vp, vp]
         L.sde_dose_probe_steps.argtypes = [vp, i, d, d, u64, u64, i, vp, vp, vp, vp, vp]
+        L.sde_transport_noalloc.argtypes = [i, i, i, C.POINTER(d), C.POINTER(d), vp, C.POINTER(Material), i,
+                                            C.POINTER(Params), vp, i, u64, vp, C.POINTER(Balance), vp]
         _lib = L
         return L
 

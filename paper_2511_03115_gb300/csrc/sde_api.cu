@@ -93,6 +93,11 @@ extern "C" int sde_default_params(sde_params* p) {
 
 extern "C" const char* sde_last_error(void) { return g_err; }
 
+namespace sde {
+// Lets other translation units of the library report through sde_last_error.
+void set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace sde
+
 static int check_params(const sde_params& p) {
     bool ok = p.step_cm > 0.0 && p.step_cm <= 1.0 && p.msc_z_cm > 0.0 && p.F > 0.0 && p.F < 1.0 &&
               p.theta_cut_rad > 0.0 && p.theta_cut_rad < 3.0 && p.backscatter_rad > 0.0 &&

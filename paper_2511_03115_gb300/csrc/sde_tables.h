@@ -34,4 +34,7 @@ struct TableBuild {
 
 cudaError_t build_tables(const TableBuild& tb, cudaStream_t st);
 
+// Message for sde_last_error() (defined with the C ABI).
+void set_last_error(const char* msg);
+
 }  // namespace sde
