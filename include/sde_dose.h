@@ -116,10 +116,15 @@ typedef struct {
  * lanes once at least refill_min of them are idle (or all lanes are idle).
  * The tally does not depend on these settings. */
 typedef struct {
-    int blocks_per_sm;   /* 1..8 (default: as many as fit)      */
-    int warps_per_block; /* 1..8 (default 8)                     */
-    int batch;           /* 32..4096, multiple of 32 (default 32) */
-    int refill_min;      /* 1..32 (default 32: refill whole warps) */
+    int blocks_per_sm;   /* 1..8 (default: as many as fit)                 */
+    int warps_per_block; /* 1..8 (default 8)                                */
+    int batch;           /* 32..4096, multiple of 32 (default 32)           */
+    int refill_min;      /* 1..32 (default 32: refill whole warps)          */
+    int table_smem;      /* 1: stage the physics tables in shared memory;
+                            2: read them through the L1 cache (default 2)   */
+    int aggregate;       /* midpoint tally: 1 one atomic per lane and step
+                            (default); 2 lanes of a warp that hit the same
+                            voxel sum their deposits first                  */
 } sde_tuning;
 
 /* Fill p with the defaults listed above.  Returns SDE_OK or SDE_EINVAL (p NULL). */
@@ -238,7 +243,8 @@ int sde_dose_probe_steps(sde_dose* d, int m, double rho, double E, uint64_t seed
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race and corrupt each other: serialise them.  Work is enqueued on
  * cuda_stream (a cudaStream_t, NULL = legacy default stream); with bal != NULL
- * the call waits for it and fills the balance (SDE_EDEVICE if the step cap was
+ * the call waits for it and fills the balance of this call (its deposited
+ * field is the sum of d_edep after the call; SDE_EDEVICE if the step cap was
  * hit or a spot was invalid), otherwise it returns without waiting. */
 int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_mm[3], const double origin_mm[3],
                           const uint32_t* d_vox, const sde_material* mats, int n_mats,

@@ -72,7 +72,7 @@ class Balance(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("warps_per_block", C.c_int), ("batch", C.c_int),
-                ("refill_min", C.c_int)]
+                ("refill_min", C.c_int), ("table_smem", C.c_int), ("aggregate", C.c_int)]
 
 
 assert C.sizeof(Spot) == 88
@@ -178,8 +178,9 @@ class SdeDose:
         ptr = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
         _check(lib().sde_dose_set_stream(self.h, C.c_void_p(ptr)))
 
-    def set_tuning(self, blocks_per_sm=0, warps_per_block=0, batch=0, refill_min=0):
-        t = Tuning(blocks_per_sm, warps_per_block, batch, refill_min)
+    def set_tuning(self, blocks_per_sm=0, warps_per_block=0, batch=0, refill_min=0, table_smem=0,
+                   aggregate=0):
+        t = Tuning(blocks_per_sm, warps_per_block, batch, refill_min, table_smem, aggregate)
         _check(lib().sde_dose_set_tuning(self.h, C.byref(t)))
 
     def get_tuning(self):

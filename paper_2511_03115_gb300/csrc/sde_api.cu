@@ -178,6 +178,8 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     d->tune.warps_per_block = 8;
     d->tune.batch = 32;
     d->tune.refill_min = 32;
+    d->tune.table_smem = 2;
+    d->tune.aggregate = 1;
 
     auto fail = [&](int rc) {
         free_all(d);
@@ -265,15 +267,18 @@ extern "C" int sde_dose_set_tuning(sde_dose* d, const sde_tuning* t) {
     if (!d || !t) return set_err(SDE_EINVAL, "null argument");
     if (t->blocks_per_sm < 0 || t->blocks_per_sm > 8 || t->warps_per_block < 0 ||
         t->warps_per_block > kMaxWarpsPerBlock || t->batch < 0 || t->batch > 4096 || (t->batch % 32) != 0 ||
-        t->refill_min < 0 || t->refill_min > 32)
+        t->refill_min < 0 || t->refill_min > 32 || t->table_smem < 0 || t->table_smem > 2 || t->aggregate < 0 ||
+        t->aggregate > 2)
         return set_err(SDE_EINVAL,
                        "tuning out of range (blocks_per_sm 0..8, warps_per_block 0..%d, batch multiple of 32 <= 4096, "
-                       "refill_min 0..32)",
+                       "refill_min 0..32, table_smem 0..2, aggregate 0..2)",
                        kMaxWarpsPerBlock);
     if (t->blocks_per_sm) d->tune.blocks_per_sm = t->blocks_per_sm;
     if (t->warps_per_block) d->tune.warps_per_block = t->warps_per_block;
     if (t->batch) d->tune.batch = t->batch;
     if (t->refill_min) d->tune.refill_min = t->refill_min;
+    if (t->table_smem) d->tune.table_smem = t->table_smem;
+    if (t->aggregate) d->tune.aggregate = t->aggregate;
     return SDE_OK;
 }
 
@@ -330,6 +335,7 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
     P.km_r = (float)d->p.km_r;
     P.batch = d->tune.batch;
     P.refill_min = d->tune.refill_min;
+    P.aggregate = d->tune.aggregate == 2 ? 1 : 0;
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {
         P.rk0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
@@ -356,8 +362,9 @@ static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t s
     KParams P = make_kparams(d, n, seed);
     int warps = d->tune.warps_per_block;
     int block = warps * 32;
-    bool smem = d->table_bytes <= 96 * 1024;
-    int per_sm = transport_max_blocks_per_sm(block, smem ? d->table_bytes : 0, smem, d->p.tally_mode);
+    bool smem = d->tune.table_smem == 1 && d->table_bytes <= 96 * 1024;
+    int per_sm = transport_max_blocks_per_sm(block, smem ? d->table_bytes : 0, smem, d->p.tally_mode,
+                                             d->tune.aggregate == 2);
     if (per_sm < 1) return set_err(SDE_ECUDA, "transport kernel cannot be resident with %d warps per block", warps);
     if (d->tune.blocks_per_sm > 0) per_sm = std::min(per_sm, d->tune.blocks_per_sm);
     int grid = d->num_sms * per_sm;
@@ -410,6 +417,11 @@ extern "C" int sde_dose_run_device(sde_dose* d, const sde_spot* d_spots, int n_s
 }
 
 static int read_counters(sde_dose* d, sde_balance* bal) {
+    if (bal) {
+        // the deposited energy of the balance is the sum of the tally
+        CUDA_TRY(cudaMemsetAsync(d->d_counters + kCntDeposited, 0, sizeof(unsigned long long), d->stream));
+        CUDA_TRY(launch_sum_u64(d->d_edep, d->nvox, d->d_counters + kCntDeposited, d->num_sms, d->stream));
+    }
     CUDA_TRY(cudaMemcpyAsync(d->h_counters, d->d_counters, kCntWords * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, d->stream));
     CUDA_TRY(cudaMemcpyAsync(d->h_counters + kCntWords, d->d_err, sizeof(unsigned int),

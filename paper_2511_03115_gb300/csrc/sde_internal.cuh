@@ -74,7 +74,7 @@ struct KParams {
     float ruth_span;           // 1/s_cut - 1/2
     float s_back;              // 1 - cos(backscatter limit)
     float inel_lo, inel_span, km_r;
-    int batch, refill_min;
+    int batch, refill_min, aggregate;
     uint32_t rk0[10], rk1[10];  // Philox round keys
     float strag_on, mcs_on;  // 1 or 0 (physics_mask)
     const uint32_t* __restrict__ vox;  // packed voxel words (density | material id)
@@ -127,7 +127,7 @@ __device__ __forceinline__ void cos_sin_from_sq(float th2, float& c, float& s) {
         float so = 1.f + th2 * (-1.f / 6.f + th2 * (1.f / 120.f + th2 * (-1.f / 5040.f)));
         s = so * sqrtf(th2);
     } else {
-        sincosf(sqrtf(th2), &s, &c);
+        __sincosf(sqrtf(th2), &s, &c);
     }
 }
 
@@ -137,7 +137,7 @@ __device__ __forceinline__ void cos_sin_from_sq(float th2, float& c, float& s) {
 __device__ __forceinline__ void rotate(float& ux, float& uy, float& uz, float cos_t, float sin_t,
                                        float cos_p, float sin_p) {
     float sg = copysignf(1.f, uz);
-    float a = -1.f / (sg + uz);
+    float a = __fdividef(-1.f, sg + uz);  // |sg + uz| >= 1
     float b = ux * uy * a;
     float e1x = 1.f + sg * ux * ux * a, e1y = sg * b, e1z = -sg * ux;
     float e2x = b, e2y = sg + uy * uy * a, e2z = -uy;

@@ -202,6 +202,7 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     P.km_r = (float)p.km_r;
     P.batch = 32;
     P.refill_min = 32;
+    P.aggregate = 0;
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {
         P.rk0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
@@ -221,11 +222,13 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     P.err = err;
 
     const int block = 8 * 32;
-    int per_sm = transport_max_blocks_per_sm(block, table_bytes, true, p.tally_mode);
+    int per_sm = transport_max_blocks_per_sm(block, table_bytes, false, p.tally_mode, false);
     if (per_sm < 1) return noalloc_fail(SDE_ECUDA, "sde_transport_noalloc: transport kernel cannot be resident");
-    NA_TRY(launch_transport(P, sms * per_sm, block, table_bytes, true, st));
+    NA_TRY(launch_transport(P, sms * per_sm, block, table_bytes, false, st));
 
     if (bal) {
+        NA_TRY(cudaMemsetAsync(counters + kCntDeposited, 0, sizeof(unsigned long long), st));
+        NA_TRY(launch_sum_u64(d_edep, (size_t)nx * ny * nz, counters + kCntDeposited, sms, st));
         unsigned long long c[kCntWords];
         unsigned int flag = 0;
         NA_TRY(cudaMemcpyAsync(c, counters, sizeof c, cudaMemcpyDeviceToHost, st));

@@ -211,9 +211,9 @@ __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int
     float w = rho * ph.w;
     float g;
     if (w >= 1.f)
-        g = (1.f + w) / w * __logf(1.f + w) - 1.f;
+        g = __fdividef(1.f + w, w) * __logf(1.f + w) - 1.f;
     else if (w >= 0.01f)
-        g = (1.f + w) / w * log1pf(w) - 1.f;
+        g = __fdividef(1.f + w, w) * log1pf(w) - 1.f;
     else
         g = w * (0.5f + w * (-1.f / 6.f + w * (1.f / 12.f)));
     float t = rho * ph.tg * g * P.mcs_on;
@@ -232,7 +232,12 @@ __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int
 }
 
 // Sample Y_0 of history h from its spot (binary search of the history prefix).
-__device__ __forceinline__ void init_history(const KParams& P, uint64_t h, float& E, float& px, float& py,
+#ifdef SDE_INIT_NOINLINE
+#define SDE_INIT_ATTR __noinline__
+#else
+#define SDE_INIT_ATTR __forceinline__
+#endif
+__device__ SDE_INIT_ATTR void init_history(const KParams& P, uint64_t h, float& E, float& px, float& py,
                                              float& pz, float& ux, float& uy, float& uz, float& tau) {
     int lo = 0, hi = P.n_spots;
     while (hi - lo > 1) {
@@ -284,9 +289,9 @@ __device__ __forceinline__ float vox_rho(uint32_t w) { return __uint_as_float(w 
 // Split dq along the chord (ax,ay,az) + t (dx,dy,dz), t in [0,1], over the
 // voxels it crosses, in proportion to the length inside each (Amanatides-Woo
 // traversal).  Pieces are cumulative roundings of t dq, so they sum to dq.
-__device__ void deposit_chord(const KParams& P, float ax, float ay, float az, float dx, float dy, float dz,
-                              unsigned long long dq, unsigned long long& a_dep,
-                              unsigned long long& a_esc) {
+// Returns the part that falls outside the grid.
+__device__ unsigned long long deposit_chord(const KParams& P, float ax, float ay, float az, float dx,
+                                            float dy, float dz, unsigned long long dq) {
     float g[3] = {ax * P.inv_hx, ay * P.inv_hy, az * P.inv_hz};
     float v[3] = {dx * P.inv_hx, dy * P.inv_hy, dz * P.inv_hz};
     int n[3] = {P.nx, P.ny, P.nz};
@@ -309,7 +314,7 @@ __device__ void deposit_chord(const KParams& P, float ax, float ay, float az, fl
         }
     }
     float fq = (float)dq;
-    unsigned long long done = 0;
+    unsigned long long done = 0, escaped = 0;
     for (int it = 0; it < 32 && done < dq; ++it) {
         float tn = fminf(fminf(tmax[0], tmax[1]), tmax[2]);
         bool last = tn >= 1.f || it == 31;
@@ -320,47 +325,52 @@ __device__ void deposit_chord(const KParams& P, float ax, float ay, float az, fl
         if (part) {
             bool in = (unsigned)i[0] < (unsigned)n[0] && (unsigned)i[1] < (unsigned)n[1] &&
                       (unsigned)i[2] < (unsigned)n[2];
-            if (in) {
+            if (in)
                 atomicAdd(&P.edep[i[0] + P.nx * (i[1] + P.ny * i[2])], part);
-                a_dep += part;
-            } else {
-                a_esc += part;
-            }
+            else
+                escaped += part;
         }
         if (last) break;
         int ax_ = (tmax[0] <= tmax[1] && tmax[0] <= tmax[2]) ? 0 : (tmax[1] <= tmax[2] ? 1 : 2);
         i[ax_] += st[ax_];
         tmax[ax_] += tdel[ax_];
     }
+    return escaped;
 }
 
 #ifndef SDE_MIN_BLOCKS
-#define SDE_MIN_BLOCKS 3
+#define SDE_MIN_BLOCKS 5
 #endif
 
-template <int TALLY, bool SMEM>
+// Rare events (start, escape, non-elastic removal, jumps) go to per-block
+// shared-memory counters; the per-step deposit needs no counter at all: the
+// deposited total is the sum of the tally, reduced when the balance is read.
+#define SDE_BLOCK_ADD(idx, v) atomicAdd(&s_cnt[idx], (unsigned long long)(v))
+
+template <int TALLY, bool SMEM, bool AGG>
 __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
     extern __shared__ float4 s_tab[];
+    __shared__ unsigned long long s_cnt[kCntWords];
+    if (threadIdx.x < kCntWords) s_cnt[threadIdx.x] = 0ull;
     const float4* tab = P.table;
     if (SMEM) {
         int rows = P.n_mats * P.N * kRowFloat4;
         for (int i = threadIdx.x; i < rows; i += blockDim.x) s_tab[i] = P.table[i];
-        __syncthreads();
         tab = s_tab;
     }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned long long total = P.prefix[P.n_spots];
     bool alive = false;
     float E = 0.f, px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 1.f, tau = 1.f;
-    unsigned long long h = 0, qprev = 0;
+    unsigned long long h = 0;
     uint32_t n = 0;
     // Software pipeline: the voxel word of R_n and the Philox block of step n are
     // fetched/computed during step n-1, so their latency overlaps the step's work.
     uint32_t vox = 0;
     int vcur = -1;
     uint4 x = make_uint4(0u, 0u, 0u, 0u);
-    unsigned long long a_inc = 0, a_dep = 0, a_esc = 0, a_rem = 0;
-    uint32_t a_hist = 0, a_steps = 0, a_jel = 0, a_jin = 0;
+    uint32_t a_steps = 0;
     unsigned long long b_next = 0, b_end = 0;
     bool drained = false;
 
@@ -386,9 +396,8 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
             if (((dead >> lane) & 1u) && rank < take) {
                 h = b_next + (unsigned long long)rank;
                 init_history(P, h, E, px, py, pz, ux, uy, uz, tau);
-                qprev = qfix(P, E);
-                a_inc += qprev;
-                a_hist += 1;
+                SDE_BLOCK_ADD(kCntIncident, qfix(P, E));
+                SDE_BLOCK_ADD(kCntHistories, 1);
                 n = 0;
                 alive = true;
                 vcur = voxel_index(P, px, py, pz);
@@ -401,14 +410,9 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
         if (!__any_sync(0xffffffffu, alive)) break;
         if (!alive) continue;
 
-        if (n >= (uint32_t)P.max_steps) {
-            atomicOr(P.err, kErrStepCap);
-            a_esc += qprev;
-            alive = false;
-            continue;
-        }
-        if (vcur < 0) {  // R_n outside the domain D
-            a_esc += qprev;
+        if (n >= (uint32_t)P.max_steps || vcur < 0) {  // step cap, or R_n outside the domain D
+            if (n >= (uint32_t)P.max_steps) atomicOr(P.err, kErrStepCap);
+            SDE_BLOCK_ADD(kCntEscaped, qfix(P, E));
             alive = false;
             continue;
         }
@@ -424,68 +428,75 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
         const uint32_t vox_next = vnext >= 0 ? __ldg(&P.vox[vnext]) : 0u;
         const uint4 xcur = x;
         x = philox(P, n + 1u, kTagStep, h);
+        const unsigned long long q0 = qfix(P, E);
         float E1;
         int jump = sde_step(P, tab, m, rho, xcur, E, ux, uy, uz, tau, h, n, E1);
         unsigned long long q1 = qfix(P, E1);
-        unsigned long long dq = qprev - q1;
+        unsigned long long dq = q0 - q1;
         if (TALLY == 0) {
             // deposit at the step midpoint (Sec. 2.2.2)
             int mv = voxel_index(P, fmaf(oux, P.half_step_mm, ox), fmaf(ouy, P.half_step_mm, oy),
                                  fmaf(ouz, P.half_step_mm, oz));
-            if (mv >= 0) {
-                if (dq) atomicAdd(&P.edep[mv], dq);
-                a_dep += dq;
-            } else {
-                a_esc += dq;
+            if (mv < 0) {
+                if (dq) SDE_BLOCK_ADD(kCntEscaped, dq);
+            } else if (AGG) {
+                // Lanes depositing into the same voxel add their parts first and one
+                // lane commits the sum.  dq < 2^40 (E <= 1000 MeV in units of at least
+                // 2^-30 MeV), so the sums of the 24-bit low parts and of the high parts
+                // of up to 32 lanes each fit 32 bits and the 64-bit sum is exact.
+                unsigned grp = __match_any_sync(__activemask(), mv);
+                unsigned lo = __reduce_add_sync(grp, (unsigned)(dq & 0xFFFFFFull));
+                unsigned hi = __reduce_add_sync(grp, (unsigned)(dq >> 24));
+                unsigned long long sum = ((unsigned long long)hi << 24) + lo;
+                if (lane == __ffs(grp) - 1 && sum) atomicAdd(&P.edep[mv], sum);
+            } else if (dq) {
+                atomicAdd(&P.edep[mv], dq);
             }
         } else if (dq) {
-            deposit_chord(P, ox, oy, oz, oux * P.step_mm, ouy * P.step_mm, ouz * P.step_mm, dq, a_dep, a_esc);
+            unsigned long long esc = deposit_chord(P, ox, oy, oz, oux * P.step_mm, ouy * P.step_mm,
+                                                   ouz * P.step_mm, dq);
+            if (esc) SDE_BLOCK_ADD(kCntEscaped, esc);
         }
-        if (jump == 2) {
-            unsigned long long q2 = qfix(P, E);
-            a_rem += q1 - q2;
-            q1 = q2;
-            a_jin += 1;
-        } else if (jump == 1) {
-            a_jel += 1;
+        if (jump) {
+            if (jump == 2) {
+                SDE_BLOCK_ADD(kCntRemoved, q1 - qfix(P, E));
+                SDE_BLOCK_ADD(kCntJumpInel, 1);
+            } else {
+                SDE_BLOCK_ADD(kCntJumpEl, 1);
+            }
         }
-        qprev = q1;
         n += 1;
         a_steps += 1;
         vcur = vnext;
         vox = vox_next;
         if (E < P.e_min) {  // absorbed; the rest is deposited where the proton is
-            if (vcur >= 0) {
-                if (qprev) atomicAdd(&P.edep[vcur], qprev);
-                a_dep += qprev;
-            } else {
-                a_esc += qprev;
+            unsigned long long qr = qfix(P, E);
+            if (qr) {
+                if (vcur >= 0)
+                    atomicAdd(&P.edep[vcur], qr);
+                else
+                    SDE_BLOCK_ADD(kCntEscaped, qr);
             }
             alive = false;
         }
     }
 
-    // warp totals, one atomic per counter per warp
-    for (int off = 16; off > 0; off >>= 1) {
-        a_inc += __shfl_down_sync(0xffffffffu, a_inc, off);
-        a_dep += __shfl_down_sync(0xffffffffu, a_dep, off);
-        a_esc += __shfl_down_sync(0xffffffffu, a_esc, off);
-        a_rem += __shfl_down_sync(0xffffffffu, a_rem, off);
-        a_hist += __shfl_down_sync(0xffffffffu, a_hist, off);
-        a_steps += __shfl_down_sync(0xffffffffu, a_steps, off);
-        a_jel += __shfl_down_sync(0xffffffffu, a_jel, off);
-        a_jin += __shfl_down_sync(0xffffffffu, a_jin, off);
-    }
-    if (lane == 0) {
-        atomicAdd(&P.counters[kCntIncident], a_inc);
-        atomicAdd(&P.counters[kCntDeposited], a_dep);
-        atomicAdd(&P.counters[kCntEscaped], a_esc);
-        atomicAdd(&P.counters[kCntRemoved], a_rem);
-        atomicAdd(&P.counters[kCntHistories], (unsigned long long)a_hist);
-        atomicAdd(&P.counters[kCntSteps], (unsigned long long)a_steps);
-        atomicAdd(&P.counters[kCntJumpEl], (unsigned long long)a_jel);
-        atomicAdd(&P.counters[kCntJumpInel], (unsigned long long)a_jin);
-    }
+    for (int off = 16; off > 0; off >>= 1) a_steps += __shfl_down_sync(0xffffffffu, a_steps, off);
+    if (lane == 0) SDE_BLOCK_ADD(kCntSteps, a_steps);
+    __syncthreads();
+    if (threadIdx.x < kCntWords && threadIdx.x != kCntCursor && threadIdx.x != kCntDeposited &&
+        s_cnt[threadIdx.x])
+        atomicAdd(&P.counters[threadIdx.x], s_cnt[threadIdx.x]);
+}
+#undef SDE_BLOCK_ADD
+
+// Sum of the tally (the deposited energy of the balance), added to *out.
+__global__ void k_sum_u64(const unsigned long long* __restrict__ v, size_t n, unsigned long long* out) {
+    unsigned long long acc = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc += v[i];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
 // Spot records -> device form and the inclusive prefix of history counts;
@@ -579,42 +590,57 @@ __global__ void k_convert(const unsigned long long* edep, const float* rho, size
 }
 
 // ---------------------------------------------------------------- launchers
-template <int TALLY, bool SMEM>
+template <int TALLY, bool SMEM, bool AGG>
 static cudaError_t allow_smem(size_t smem) {
     if (!SMEM) return cudaSuccess;
-    return cudaFuncSetAttribute(k_transport<TALLY, SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+#ifdef SDE_SMEM_CARVEOUT
+    e = cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             SDE_SMEM_CARVEOUT);
+#endif
+    return e;
 }
 
-template <int TALLY, bool SMEM>
+template <int TALLY, bool SMEM, bool AGG>
 static cudaError_t launch_t(const KParams& P, int grid, int block, size_t smem, cudaStream_t st) {
-    cudaError_t e = allow_smem<TALLY, SMEM>(smem);
+    cudaError_t e = allow_smem<TALLY, SMEM, AGG>(smem);
     if (e != cudaSuccess) return e;
-    k_transport<TALLY, SMEM><<<grid, block, SMEM ? smem : 0, st>>>(P);
+    k_transport<TALLY, SMEM, AGG><<<grid, block, SMEM ? smem : 0, st>>>(P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_table, bool use_smem,
-                             cudaStream_t st) {
-    if (P.tally_mode == 0)
-        return use_smem ? launch_t<0, true>(P, grid, block, smem_table, st)
-                        : launch_t<0, false>(P, grid, block, 0, st);
-    return use_smem ? launch_t<1, true>(P, grid, block, smem_table, st)
-                    : launch_t<1, false>(P, grid, block, 0, st);
-}
-
-template <int TALLY, bool SMEM>
-static int blocks_per_sm(int block, size_t smem) {
-    if (allow_smem<TALLY, SMEM>(smem) != cudaSuccess) return 0;
+template <int TALLY, bool SMEM, bool AGG>
+static int blocks_per_sm_t(int block, size_t smem) {
+    if (allow_smem<TALLY, SMEM, AGG>(smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<TALLY, SMEM>, block, SMEM ? smem : 0) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<TALLY, SMEM, AGG>, block,
+                                                      SMEM ? smem : 0) != cudaSuccess)
         return 0;
     return nb;
 }
 
-int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode) {
-    if (tally_mode == 0) return use_smem ? blocks_per_sm<0, true>(block, smem) : blocks_per_sm<0, false>(block, 0);
-    return use_smem ? blocks_per_sm<1, true>(block, smem) : blocks_per_sm<1, false>(block, 0);
+// Variant selection: tally mode (midpoint, chord), table placement, and warp
+// aggregation of the midpoint tally.
+cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_table, bool use_smem,
+                             cudaStream_t st) {
+    if (P.tally_mode == 1)
+        return use_smem ? launch_t<1, true, false>(P, grid, block, smem_table, st)
+                        : launch_t<1, false, false>(P, grid, block, 0, st);
+    if (P.aggregate)
+        return use_smem ? launch_t<0, true, true>(P, grid, block, smem_table, st)
+                        : launch_t<0, false, true>(P, grid, block, 0, st);
+    return use_smem ? launch_t<0, true, false>(P, grid, block, smem_table, st)
+                    : launch_t<0, false, false>(P, grid, block, 0, st);
+}
+
+int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode, bool aggregate) {
+    if (tally_mode == 1)
+        return use_smem ? blocks_per_sm_t<1, true, false>(block, smem) : blocks_per_sm_t<1, false, false>(block, 0);
+    if (aggregate)
+        return use_smem ? blocks_per_sm_t<0, true, true>(block, smem) : blocks_per_sm_t<0, false, true>(block, 0);
+    return use_smem ? blocks_per_sm_t<0, true, false>(block, smem) : blocks_per_sm_t<0, false, false>(block, 0);
 }
 
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,
@@ -628,6 +654,12 @@ cudaError_t launch_probe(const KParams& P, int m, float rho, float E0, uint64_t 
                          float* co, int* jo, float* uxo, float* uyo, cudaStream_t st) {
     int threads = 256, blocks = (n + threads - 1) / threads;
     k_probe<<<blocks, threads, 0, st>>>(P, m, rho, E0, h0, n, Eo, co, jo, uxo, uyo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_u64(const unsigned long long* v, size_t n, unsigned long long* out, int num_sms,
+                           cudaStream_t st) {
+    k_sum_u64<<<num_sms * 4, 256, 0, st>>>(v, n, out);
     return cudaGetLastError();
 }
 

@@ -111,8 +111,10 @@ def test_water100_common_random_numbers(sde_gpu, oracle_lib):
 def test_tally_is_independent_of_launch_shape(sde_gpu):
     wl = water100(30_000)
     outs = []
-    for tune in ({"warps_per_block": 8, "batch": 256}, {"warps_per_block": 2, "batch": 32},
-                 {"warps_per_block": 4, "batch": 1024, "blocks_per_sm": 1}):
+    for tune in ({"warps_per_block": 8, "batch": 256}, {"warps_per_block": 2, "batch": 32, "refill_min": 1},
+                 {"warps_per_block": 4, "batch": 1024, "blocks_per_sm": 1, "table_smem": 1},
+                 {"warps_per_block": 8, "batch": 64, "refill_min": 16, "table_smem": 2, "aggregate": 1},
+                 {"warps_per_block": 8, "aggregate": 2, "refill_min": 8}):
         with sde_gpu.SdeDose(wl, tuning=tune) as d:
             d.run(wl.spots, seed=11)
             outs.append(d.fetch()[1:])
