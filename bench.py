@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 # kinematic factors, Lynch-Dahl width, spherical Brownian rotation, exponential jump
 # clock, two voxel lookups, fixed-point conversion and one 64-bit atomic).  The
 # breakdown is listed with the roofline in the design notes.
-ALGO_OPS_PER_STEP = 220
+ALGO_OPS_PER_STEP = 200
 SMS = 152
 LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per clock each
 # DRAM traffic (read + write bytes) per transport launch from the ncu capture of the
@@ -179,6 +179,59 @@ def run_reference(args):
     return 0
 
 
+def plan_benchmark(torch, S, dev, total=100_000_000, per_spot_sample=200):
+    """The 2000-spot plan phantom (200x200x300 mm, 30 spheres) with 1e8 protons:
+    default launch shape, autotuned shape, graph launch, and one launch per spot
+    (timed on the first ``per_spot_sample`` spots and scaled to all 2000)."""
+    from sde_workloads import plan2000
+    wl = plan2000(total)
+    st = torch.cuda.Stream(device=dev)
+    d = S.SdeDose(wl, stream=st)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sp = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
+
+    def timed(fn, reps=3):
+        ts = []
+        for r in range(reps + 1):
+            with torch.cuda.stream(st):
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            d.reset()
+            a.record(st)
+            fn(r)
+            b.record(st)
+            st.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    out = {"workload": "plan2000: 2000 spots, E U(70,200) MeV, lognormal weights, 1e8 protons, "
+                       "200x200x300 mm at 1 mm, water + 30 spheres"}
+    out["one_launch_default_ms"] = timed(lambda r: d.run_device(sp.data_ptr(), len(wl.spots), seed=r))
+    out["autotuned"] = d.autotune(wl.spots, seed=5, max_histories=2_000_000)
+    out["one_launch_autotuned_ms"] = timed(lambda r: d.run_device(sp.data_ptr(), len(wl.spots), seed=r))
+    d.set_tuning(graph=2)
+    out["one_launch_graph_ms"] = timed(lambda r: d.run_device(sp.data_ptr(), len(wl.spots), seed=r))
+    d.set_tuning(graph=1)
+    n = per_spot_sample
+    rec = int(wl.spots.dtype.itemsize)
+
+    def per_spot(r):
+        for i in range(n):
+            d.run_device(sp.data_ptr() + i * rec, 1, seed=r * 10_000 + i)
+
+    t_sample = timed(per_spot, reps=1)
+    hist_sample = int(wl.spots["n_hist"][:n].sum())
+    out["per_spot_sample"] = {"spots": n, "histories": hist_sample, "ms": t_sample}
+    out["per_spot_all_2000_ms_estimated"] = t_sample * len(wl.spots) / n
+    out["histories_per_s_one_launch"] = wl.n_histories / (min(out["one_launch_default_ms"],
+                                                             out["one_launch_autotuned_ms"]) * 1e-3)
+    out["histories_per_s_per_spot"] = hist_sample / (t_sample * 1e-3)
+    d.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -189,6 +242,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-histories", type=int, default=20_000)
+    ap.add_argument("--plan", action="store_true",
+                    help="also time the 2000-spot plan (1e8 protons): one persistent launch, "
+                         "autotuned, graph-launched, and one launch per spot")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -306,6 +362,8 @@ def main():
         "clocks": clocks,
         "balance_exact": bal["incident"] == bal["deposited"] + bal["escaped"] + bal["removed"],
     }
+    if args.plan:
+        line["batched_plan"] = plan_benchmark(torch, S, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

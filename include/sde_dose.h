@@ -125,6 +125,8 @@ typedef struct {
     int aggregate;       /* midpoint tally: 1 one atomic per lane and step
                             (default); 2 lanes of a warp that hit the same
                             voxel sum their deposits first                  */
+    int graph;           /* 1: launch the kernels directly (default);
+                            2: launch them as one CUDA graph                */
 } sde_tuning;
 
 /* Fill p with the defaults listed above.  Returns SDE_OK or SDE_EINVAL (p NULL). */
@@ -152,6 +154,17 @@ int sde_dose_set_stream(sde_dose* d, void* cuda_stream);
 /* Set the transport launch shape (see sde_tuning). */
 int sde_dose_set_tuning(sde_dose* d, const sde_tuning* t);
 int sde_dose_get_tuning(const sde_dose* d, sde_tuning* t);
+
+/* Autotuner: run the plan spots[0..n_spots) (host array), scaled down to at
+ * most max_histories histories, under a fixed set of candidate launch shapes
+ * (warps per block, refill threshold, batch, table placement, tally
+ * aggregation, blocks per SM), keep the fastest (CUDA-event timing, best of
+ * two timed runs after a warm-up) as the handle's tuning and return it in
+ * best_out (may be NULL).  The results do not depend on the tuning.  The
+ * tuning runs go through the tally: the call ends with sde_dose_reset, so
+ * tune before accumulating.  Synchronous. */
+int sde_dose_autotune(sde_dose* d, const sde_spot* spots, int n_spots, uint64_t seed,
+                      uint64_t max_histories, sde_tuning* best_out);
 
 /* Transport the histories of spots[0..n_spots) (host array) with the given
  * seed and add their deposits to the tally (accumulates until reset).  History

@@ -26,7 +26,7 @@ MAX_ELEMENTS = 16
 
 EXPORTED = [
     "sde_default_params", "sde_last_error", "sde_dose_create", "sde_dose_set_stream",
-    "sde_dose_set_tuning", "sde_dose_get_tuning", "sde_dose_run", "sde_dose_run_device",
+    "sde_dose_set_tuning", "sde_dose_get_tuning", "sde_dose_autotune", "sde_dose_run", "sde_dose_run_device",
     "sde_dose_sync", "sde_dose_fetch", "sde_dose_fetch_device", "sde_dose_reset",
     "sde_dose_destroy", "sde_dose_info", "sde_dose_tables", "sde_dose_probe_steps",
     "sde_transport_noalloc",
@@ -72,7 +72,7 @@ class Balance(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int), ("warps_per_block", C.c_int), ("batch", C.c_int),
-                ("refill_min", C.c_int), ("table_smem", C.c_int), ("aggregate", C.c_int)]
+                ("refill_min", C.c_int), ("table_smem", C.c_int), ("aggregate", C.c_int), ("graph", C.c_int)]
 
 
 assert C.sizeof(Spot) == 88
@@ -95,6 +95,7 @@ def lib():
         L.sde_dose_set_stream.argtypes = [vp, vp]
         L.sde_dose_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.sde_dose_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.sde_dose_autotune.argtypes = [vp, C.POINTER(Spot), i, u64, u64, C.POINTER(Tuning)]
         L.sde_dose_run.argtypes = [vp, C.POINTER(Spot), i, u64]
         L.sde_dose_run_device.argtypes = [vp, vp, i, u64]
         L.sde_dose_sync.argtypes = [vp]
@@ -179,9 +180,17 @@ class SdeDose:
         _check(lib().sde_dose_set_stream(self.h, C.c_void_p(ptr)))
 
     def set_tuning(self, blocks_per_sm=0, warps_per_block=0, batch=0, refill_min=0, table_smem=0,
-                   aggregate=0):
-        t = Tuning(blocks_per_sm, warps_per_block, batch, refill_min, table_smem, aggregate)
+                   aggregate=0, graph=0):
+        t = Tuning(blocks_per_sm, warps_per_block, batch, refill_min, table_smem, aggregate, graph)
         _check(lib().sde_dose_set_tuning(self.h, C.byref(t)))
+
+    def autotune(self, spots, seed=0, max_histories=200_000):
+        """Pick the fastest launch shape for this plan (resets the tally)."""
+        a, ptr = spots_to_ctypes(spots)
+        t = Tuning()
+        _check(lib().sde_dose_autotune(self.h, ptr, len(a), C.c_uint64(seed), C.c_uint64(max_histories),
+                                       C.byref(t)))
+        return {n: getattr(t, n) for n, _ in Tuning._fields_}
 
     def get_tuning(self):
         t = Tuning()

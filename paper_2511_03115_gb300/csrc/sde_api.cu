@@ -68,6 +68,10 @@ struct sde_dose {
     cudaEvent_t stage_ev = nullptr;
     unsigned long long* h_counters = nullptr;  // kCntWords + 1 (error flag)
     size_t table_bytes = 0;
+    // graph launch: [spot prep, transport] captured on a private stream and
+    // updated in place when only kernel arguments change
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
 };
 
 extern "C" int sde_default_params(sde_params* p) {
@@ -116,6 +120,8 @@ static void free_all(sde_dose* d) {
                     d->d_err,   d->d_raw_spots, d->d_spots, d->d_prefix,      d->d_dose};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
+    if (d->capture_stream) cudaStreamDestroy(d->capture_stream);
     if (d->h_stage) cudaFreeHost(d->h_stage);
     if (d->h_counters) cudaFreeHost(d->h_counters);
     if (d->stage_ev) cudaEventDestroy(d->stage_ev);
@@ -180,6 +186,7 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     d->tune.refill_min = 32;
     d->tune.table_smem = 2;
     d->tune.aggregate = 1;
+    d->tune.graph = 1;
 
     auto fail = [&](int rc) {
         free_all(d);
@@ -268,10 +275,10 @@ extern "C" int sde_dose_set_tuning(sde_dose* d, const sde_tuning* t) {
     if (t->blocks_per_sm < 0 || t->blocks_per_sm > 8 || t->warps_per_block < 0 ||
         t->warps_per_block > kMaxWarpsPerBlock || t->batch < 0 || t->batch > 4096 || (t->batch % 32) != 0 ||
         t->refill_min < 0 || t->refill_min > 32 || t->table_smem < 0 || t->table_smem > 2 || t->aggregate < 0 ||
-        t->aggregate > 2)
+        t->aggregate > 2 || t->graph < 0 || t->graph > 2)
         return set_err(SDE_EINVAL,
                        "tuning out of range (blocks_per_sm 0..8, warps_per_block 0..%d, batch multiple of 32 <= 4096, "
-                       "refill_min 0..32, table_smem 0..2, aggregate 0..2)",
+                       "refill_min 0..32, table_smem 0..2, aggregate 0..2, graph 0..2)",
                        kMaxWarpsPerBlock);
     if (t->blocks_per_sm) d->tune.blocks_per_sm = t->blocks_per_sm;
     if (t->warps_per_block) d->tune.warps_per_block = t->warps_per_block;
@@ -279,6 +286,7 @@ extern "C" int sde_dose_set_tuning(sde_dose* d, const sde_tuning* t) {
     if (t->refill_min) d->tune.refill_min = t->refill_min;
     if (t->table_smem) d->tune.table_smem = t->table_smem;
     if (t->aggregate) d->tune.aggregate = t->aggregate;
+    if (t->graph) d->tune.graph = t->graph;
     return SDE_OK;
 }
 
@@ -357,8 +365,6 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
 }
 
 static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t seed) {
-    CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
-                         d->p.e_max_MeV, d->stream));
     KParams P = make_kparams(d, n, seed);
     int warps = d->tune.warps_per_block;
     int block = warps * 32;
@@ -368,7 +374,40 @@ static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t s
     if (per_sm < 1) return set_err(SDE_ECUDA, "transport kernel cannot be resident with %d warps per block", warps);
     if (d->tune.blocks_per_sm > 0) per_sm = std::min(per_sm, d->tune.blocks_per_sm);
     int grid = d->num_sms * per_sm;
-    CUDA_TRY(launch_transport(P, grid, block, d->table_bytes, smem, d->stream));
+    if (d->tune.graph != 2) {
+        CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
+                             d->p.e_max_MeV, d->stream));
+        CUDA_TRY(launch_transport(P, grid, block, d->table_bytes, smem, d->stream));
+        return SDE_OK;
+    }
+    // Graph launch: capture the two launches on the private stream, update the
+    // instantiated graph in place (only kernel arguments differ between runs of
+    // the same shape) or re-instantiate, then launch it on the handle's stream.
+    if (!d->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamBeginCapture(d->capture_stream, cudaStreamCaptureModeRelaxed));
+    cudaError_t e1 = launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
+                                 d->p.e_max_MeV, d->capture_stream);
+    cudaError_t e2 = e1 == cudaSuccess
+                         ? launch_transport(P, grid, block, d->table_bytes, smem, d->capture_stream)
+                         : e1;
+    cudaGraph_t g = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(d->capture_stream, &g);
+    if (e2 != cudaSuccess || e3 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return set_err(SDE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e2 != cudaSuccess ? e2 : e3));
+    }
+    if (d->graph_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(d->graph_exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(d->graph_exec);
+            d->graph_exec = nullptr;
+        }
+    }
+    cudaError_t e4 = d->graph_exec ? cudaSuccess : cudaGraphInstantiate(&d->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e4 != cudaSuccess) return set_err(SDE_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e4));
+    CUDA_TRY(cudaGraphLaunch(d->graph_exec, d->stream));
     return SDE_OK;
 }
 
@@ -395,7 +434,9 @@ extern "C" int sde_dose_run(sde_dose* d, const sde_spot* spots, int n_spots, uin
     // reuse the pinned staging buffer only after its previous copy finished
     CUDA_TRY(cudaEventSynchronize(d->stage_ev));
     if (n_spots > d->stage_cap) {
-        if (d->h_stage) cudaFreeHost(d->h_stage);
+        if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
+    if (d->capture_stream) cudaStreamDestroy(d->capture_stream);
+    if (d->h_stage) cudaFreeHost(d->h_stage);
         d->h_stage = nullptr;
         d->stage_cap = 0;
         CUDA_TRY(cudaMallocHost(&d->h_stage, (size_t)n_spots * sizeof(sde_spot)));
@@ -414,6 +455,75 @@ extern "C" int sde_dose_run_device(sde_dose* d, const sde_spot* d_spots, int n_s
     int rc = ensure_spot_capacity(d, n_spots);
     if (rc) return rc;
     return enqueue_transport(d, d_spots, n_spots, seed);
+}
+
+// Autotuner: times the transport on a subsample of the plan under each
+// candidate launch shape and keeps the fastest.  The tally does not depend on
+// the launch shape, so only time is compared.
+extern "C" int sde_dose_autotune(sde_dose* d, const sde_spot* spots, int n_spots, uint64_t seed,
+                                 uint64_t max_histories, sde_tuning* best_out) {
+    if (!d || !spots || n_spots < 1 || max_histories < 1) return set_err(SDE_EINVAL, "bad autotune arguments");
+    int rc = check_spots_host(d, spots, n_spots);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(d->device));
+    uint64_t total = 0;
+    for (int i = 0; i < n_spots; ++i) total += spots[i].n_hist;
+    if (total == 0) return set_err(SDE_EINVAL, "autotune needs at least one history");
+    double f = total > max_histories ? (double)max_histories / (double)total : 1.0;
+    sde_spot* sub = (sde_spot*)malloc((size_t)n_spots * sizeof(sde_spot));
+    if (!sub) return set_err(SDE_ENOMEM, "out of host memory");
+    for (int i = 0; i < n_spots; ++i) {
+        sub[i] = spots[i];
+        if (spots[i].n_hist) sub[i].n_hist = (uint64_t)ceil((double)spots[i].n_hist * f);
+    }
+    static const sde_tuning cands[] = {
+        {0, 8, 32, 32, 2, 1, 1}, {0, 8, 32, 16, 2, 1, 1}, {0, 4, 32, 32, 2, 1, 1}, {0, 8, 64, 32, 2, 1, 1},
+        {0, 8, 32, 32, 1, 1, 1}, {0, 8, 32, 16, 1, 1, 1}, {0, 8, 32, 32, 2, 2, 1}, {0, 8, 32, 8, 2, 1, 1},
+        {4, 8, 32, 32, 2, 1, 1}, {3, 8, 32, 32, 1, 1, 1}, {0, 8, 32, 32, 2, 1, 2},
+    };
+    const sde_tuning saved = d->tune;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int out = SDE_OK;
+    float best_ms = 1e30f;
+    sde_tuning best = saved;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        out = set_err(SDE_ECUDA, "cudaEventCreate failed");
+    } else {
+        for (const sde_tuning& c : cands) {
+            d->tune = c;
+            if (c.blocks_per_sm == 0) d->tune.blocks_per_sm = 0;
+            float t_best = 1e30f;
+            for (int rep = 0; rep < 3 && out == SDE_OK; ++rep) {
+                if (cudaEventRecord(a, d->stream) != cudaSuccess) out = set_err(SDE_ECUDA, "event record failed");
+                if (out == SDE_OK) out = sde_dose_run(d, sub, n_spots, seed + rep);
+                if (out == SDE_OK && cudaEventRecord(b, d->stream) != cudaSuccess)
+                    out = set_err(SDE_ECUDA, "event record failed");
+                float ms = 0.f;
+                if (out == SDE_OK && (cudaEventSynchronize(b) != cudaSuccess ||
+                                      cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+                    out = set_err(SDE_ECUDA, "event timing failed");
+                if (out == SDE_OK && rep > 0) t_best = std::min(t_best, ms);  // first run warms up
+            }
+            if (out != SDE_OK) break;
+            if (t_best < best_ms) {
+                best_ms = t_best;
+                best = c;
+            }
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    free(sub);
+    d->tune = out == SDE_OK ? best : saved;
+    int rc2 = sde_dose_reset(d);
+    if (out == SDE_OK && rc2 != SDE_OK) out = rc2;
+    if (out == SDE_OK) {
+        // the tuning runs may have raised the device flag on a bad spot: clear it
+        CUDA_TRY(cudaMemsetAsync(d->d_err, 0, sizeof(unsigned int), d->stream));
+        CUDA_TRY(cudaStreamSynchronize(d->stream));
+        if (best_out) *best_out = best;
+    }
+    return out;
 }
 
 static int read_counters(sde_dose* d, sde_balance* bal) {

@@ -280,3 +280,26 @@ def test_straight_track_tally_matches_the_oracle(sde_gpu, oracle_lib, mode):
     _, eo, bo = O.run_workload(wl, physics_mask=0, tally_mode=mode)
     assert bg["steps"] == bo["steps"] and balanced(bg)
     assert np.allclose(eg.astype(float), eo.astype(float), rtol=2e-5, atol=2e-5 * eo.max())
+
+
+def test_autotune_and_graph_launch_keep_the_tally(sde_gpu):
+    wl = water100(20_000)
+    with sde_gpu.SdeDose(wl) as d:
+        d.run(wl.spots, seed=11)
+        _, ref, rb = d.fetch(dose=False)
+        d.reset()
+        d.run(wl.spots, seed=12)
+        _, ref12, _ = d.fetch(dose=False)
+        best = d.autotune(wl.spots, seed=99, max_histories=8000)
+        assert best == d.get_tuning()
+        _, e0, b0 = d.fetch(dose=False)
+        assert e0.sum() == 0 and b0["histories"] == 0  # autotune leaves a clean tally
+        d.run(wl.spots, seed=11)
+        _, e1, b1 = d.fetch(dose=False)
+        assert np.array_equal(e1, ref) and b1 == rb
+        d.set_tuning(graph=2)
+        for seed, want in ((11, ref), (12, ref12), (11, ref)):
+            d.reset()
+            d.run(wl.spots, seed=seed)
+            _, e, _ = d.fetch(dose=False)
+            assert np.array_equal(e, want)
