@@ -40,7 +40,7 @@ SMS = 152
 LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per clock each
 # DRAM traffic (read + write bytes) per transport launch from the ncu capture of the
 # same launch configuration; None until captured for the current kernel.
-TRANSPORT_DRAM_BYTES = None
+TRANSPORT_DRAM_BYTES = 422_050_000  # 92.92 MB read + 329.13 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
 
 WORKLOAD_DESC = ("slab150: 150 MeV pencil beam (sigma_xy 3 mm), 1e6 protons per GPU, "
                  "60x60x200 mm at 0.5 mm (120x120x400 voxels), water/bone-like/lung-like/water slabs")

@@ -229,6 +229,45 @@ int sde_dose_probe_steps(sde_dose* d, int m, double rho, double E, uint64_t seed
                          int n, float* E_out, float* cos_out, int* jump_out, float* ux_out,
                          float* uy_out);
 
+/* ---- learned denoiser building blocks (tensor-core kernels) ----
+ * The denoiser is a 3D convolutional encoder-decoder that maps a low-history
+ * dose and the density map to a high-history dose (it has no counterpart in
+ * the paper; the plain high-history transport remains its reference).  Its
+ * kernels use the tcgen05 tensor core (BF16 operands, FP32 accumulation in
+ * tensor memory).  Completion waits are bounded; a wait that times out leaves
+ * the output unwritten and the call returns SDE_EDEVICE.  Synchronous. */
+
+/* D[M x N] = A[M x K] x B[N x K]^T.  A, B: device BF16, row-major, 16-byte
+ * aligned; D: device FP32, row-major.  N a multiple of 16 in [16, 256], K a
+ * multiple of 16.  stream: cudaStream_t or NULL. */
+int sde_gemm_bf16(const void* d_A, const void* d_B, float* d_D, int M, int N, int K, void* stream);
+
+/* 3x3x3 convolution, stride 1, zero padding 1, channels-last BF16:
+ * y[n][v][y_coffset + co] = (relu?) (bias[co] + sum_{tap,ci} x[n][v + off(tap)][ci] w[co][tap][ci]),
+ * v = (z*H + y)*W + x, tap = 9 kz + 3 ky + kx, off = (kz-1, ky-1, kx-1).  d_x [batch][D*H*W][Cin],
+ * d_w [Cout][27][Cin] BF16, d_bias [Cout] FP32 or NULL; y rows have y_cstride channels
+ * (BF16, or FP32 when y_fp32 != 0), written at channel offset y_coffset (so two
+ * producers can fill the halves of a concatenation).  Requires D*H*W a multiple of
+ * 128, Cin a multiple of 16 in [16, 192], Cout a multiple of 16 in [16, 256].  The
+ * data gradient of the convolution is this call on dy with the weights of
+ * sde_conv3d_flip_weights.  Asynchronous; sde_denoise_status reports a timed-out wait. */
+int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int W, int Cin, const void* d_w,
+                       const float* d_bias, int Cout, void* d_y, int y_cstride, int y_coffset, int y_fp32,
+                       int relu, void* stream);
+
+/* Weight gradient of sde_conv3d_forward: d_dw[co][tap][ci] += sum over voxels of
+ * dy[v][co] x[v + off(tap)][ci] (FP32 accumulation into d_dw; BF16 d_x, d_dy; Cout <= 128).
+ * Asynchronous. */
+int sde_conv3d_wgrad(const void* d_x, const void* d_dy, float* d_dw, int batch, int D, int H, int W, int Cin,
+                     int Cout, void* stream);
+
+/* d_wd[ci][26 - tap][co] = d_w[co][tap][ci] (BF16): weights of the data-gradient convolution. */
+int sde_conv3d_flip_weights(const void* d_w, void* d_wd, int Cin, int Cout, void* stream);
+
+/* Wait for the stream and report (and clear) a timed-out tensor-core wait of any
+ * denoiser kernel since the last call: SDE_EDEVICE, else SDE_OK. */
+int sde_denoise_status(void* stream);
+
 /* Transport without any memory allocation.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory -- code
  * running inside a framework that owns every device allocation through its own

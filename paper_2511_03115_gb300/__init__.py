@@ -29,7 +29,8 @@ EXPORTED = [
     "sde_dose_set_tuning", "sde_dose_get_tuning", "sde_dose_autotune", "sde_dose_run", "sde_dose_run_device",
     "sde_dose_sync", "sde_dose_fetch", "sde_dose_fetch_device", "sde_dose_reset",
     "sde_dose_destroy", "sde_dose_info", "sde_dose_tables", "sde_dose_probe_steps",
-    "sde_transport_noalloc",
+    "sde_transport_noalloc", "sde_gemm_bf16", "sde_conv3d_forward", "sde_conv3d_wgrad",
+    "sde_conv3d_flip_weights", "sde_denoise_status",
 ]
 
 
@@ -110,6 +111,11 @@ def lib():
         L.sde_dose_probe_steps.argtypes = [vp, i, d, d, u64, u64, i, vp, vp, vp, vp, vp]
         L.sde_transport_noalloc.argtypes = [i, i, i, C.POINTER(d), C.POINTER(d), vp, C.POINTER(Material), i,
                                             C.POINTER(Params), vp, i, u64, vp, C.POINTER(Balance), vp]
+        L.sde_gemm_bf16.argtypes = [vp, vp, vp, i, i, i, vp]
+        L.sde_conv3d_forward.argtypes = [vp, i, i, i, i, i, vp, vp, i, vp, i, i, i, i, vp]
+        L.sde_conv3d_wgrad.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp]
+        L.sde_conv3d_flip_weights.argtypes = [vp, vp, i, i, vp]
+        L.sde_denoise_status.argtypes = [vp]
         _lib = L
         return L
 
@@ -281,6 +287,56 @@ class SdeDose:
             self.close()
         except Exception:
             pass
+
+
+def gemm_bf16(A, B, D=None, stream=None):
+    """D = A @ B.T on the tensor core (torch CUDA tensors: A [M,K] and B [N,K] bfloat16,
+    D [M,N] float32)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if D is None:
+        D = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    st = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(lib().sde_gemm_bf16(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, st))
+    return D
+
+
+def _sp(stream):
+    return None if stream is None else C.c_void_p(stream.cuda_stream)
+
+
+def conv3d(x, w, bias=None, relu=False, y=None, y_coffset=0, fp32=False, stream=None):
+    """3x3x3 convolution: x [n, D, H, W, Cin] bf16, w [Cout, 27, Cin] bf16 -> y [n, D, H, W, C]."""
+    import torch
+    n, D, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    if y is None:
+        y = torch.empty(n, D, H, W, Cout, dtype=torch.float32 if fp32 else torch.bfloat16, device=x.device)
+    _check(lib().sde_conv3d_forward(x.data_ptr(), n, D, H, W, Cin, w.data_ptr(),
+                                    None if bias is None else bias.data_ptr(), Cout, y.data_ptr(),
+                                    y.shape[-1], y_coffset, int(fp32), int(relu), _sp(stream)))
+    return y
+
+
+def conv3d_wgrad(x, dy, dw, stream=None):
+    n, D, H, W, Cin = x.shape
+    _check(lib().sde_conv3d_wgrad(x.data_ptr(), dy.data_ptr(), dw.data_ptr(), n, D, H, W, Cin, dy.shape[-1],
+                                  _sp(stream)))
+    return dw
+
+
+def conv3d_flip_weights(w, wd=None, stream=None):
+    import torch
+    Cout, _, Cin = w.shape
+    if wd is None:
+        wd = torch.empty(Cin, 27, Cout, dtype=w.dtype, device=w.device)
+    _check(lib().sde_conv3d_flip_weights(w.data_ptr(), wd.data_ptr(), Cin, Cout, _sp(stream)))
+    return wd
+
+
+def denoise_status(stream=None):
+    _check(lib().sde_denoise_status(_sp(stream)))
 
 
 def run_workload(wl, seed=None, spots=None, **param_kw):

@@ -1,0 +1,535 @@
+// sde_denoise.cu -- tensor-core (tcgen05) kernels of the learned dose denoiser.
+//
+// The denoiser is a 3D convolutional encoder-decoder applied to a low-history dose
+// and the density map; its convolutions are implicit GEMMs on the 5th-generation
+// tensor core with BF16 operands in shared memory and FP32 accumulators in tensor
+// memory.  This file holds the GEMM building block and its C entry point.
+#include <cuda_bf16.h>
+#include <stdio.h>
+
+#include <mutex>
+
+#include "sde_dose.h"
+#include "sde_tables.h"
+#include "sde_umma.cuh"
+
+namespace sde {
+
+namespace {
+
+constexpr long long kWaitCycles = 1ll << 31;  // ~1 s at 2 GHz: a stuck wait sets the error flag
+
+// D[M x N] (FP32, row-major) = A[M x K] x B[N x K]^T with A, B row-major BF16 (both
+// K-major).  One CTA of 128 threads per 128-row tile of D; K is staged in chunks of
+// 64 through shared memory in the core-matrix layout; one thread issues the MMAs.
+__global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restrict__ A,
+                                                   const __nv_bfloat16* __restrict__ B, float* __restrict__ D,
+                                                   int M, int N, int K, unsigned int* status) {
+    constexpr int KC = 64;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + 128 * KC * 2;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 256 * KC * 2);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128;
+    const uint32_t ncols = N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
+    if (warp == 0) {
+        umma::tmem_alloc(slot, ncols);
+        umma::tmem_relinquish();
+    }
+    if (tid == 0) umma::mbar_init(mbar, 1);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tbase = *slot;
+    const uint32_t idesc = umma::idesc_bf16_f32(128, N);
+    bool ok = true;
+    int it = 0;
+    for (int k0 = 0; k0 < K; k0 += KC, ++it) {
+        const int kc = min(KC, K - k0);
+        const int q8 = kc >> 3;
+        for (int c = tid; c < 128 * q8; c += 128) {
+            int r = c / q8, q = c - r * q8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m0 + r < M) v = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + r) * K + k0 + q * 8);
+            *reinterpret_cast<uint4*>(sA + umma::core_offset(r, q * 8, kc)) = v;
+        }
+        for (int c = tid; c < N * q8; c += 128) {
+            int r = c / q8, q = c - r * q8;
+            uint4 v = *reinterpret_cast<const uint4*>(B + (size_t)r * K + k0 + q * 8);
+            *reinterpret_cast<uint4*>(sB + umma::core_offset(r, q * 8, kc)) = v;
+        }
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (tid == 0) {
+            for (int ks = 0; ks < (kc >> 4); ++ks) {
+                uint64_t ad = umma::smem_desc(umma::smem_addr(sA) + ks * 256, 128, 16 * kc);
+                uint64_t bd = umma::smem_desc(umma::smem_addr(sB) + ks * 256, 128, 16 * kc);
+                umma::mma_bf16(tbase, ad, bd, idesc, (k0 > 0 || ks > 0) ? 1u : 0u);
+            }
+            umma::mma_commit(mbar);
+        }
+        bool done = umma::mbar_wait(mbar, (uint32_t)(it & 1), kWaitCycles);
+        umma::fence_after_sync();
+        if (!__syncthreads_and(done ? 1 : 0)) {
+            ok = false;
+            break;
+        }
+    }
+    if (ok) {
+        for (int c = 0; c < N; c += 8) {
+            float v[8];
+            umma::tmem_ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            int row = m0 + 32 * warp + lane;
+            if (row < M)
+                for (int j = 0; j < 8; ++j) D[(size_t)row * N + c + j] = v[j];
+        }
+    } else if (tid == 0) {
+        atomicOr(status, 1u);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) umma::tmem_dealloc(tbase, ncols);
+}
+
+std::mutex g_status_mutex;
+unsigned int* g_status[64] = {};
+
+// A device status word per device (allocated on first use).
+cudaError_t status_word(unsigned int** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_status_mutex);
+    if (!g_status[dev]) {
+        e = cudaMalloc(&g_status[dev], sizeof(unsigned int));
+        if (e != cudaSuccess) return e;
+        e = cudaMemset(g_status[dev], 0, sizeof(unsigned int));
+        if (e != cudaSuccess) return e;
+    }
+    *out = g_status[dev];
+    return cudaSuccess;
+}
+
+int report(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SDE_OK;
+    char m[256];
+    snprintf(m, sizeof m, "%s: %s", what, cudaGetErrorString(e));
+    set_last_error(m);
+    return e == cudaErrorMemoryAllocation ? SDE_ENOMEM : SDE_ECUDA;
+}
+
+}  // namespace
+
+// Reads and clears the device status word; SDE_EDEVICE when a tensor-core wait timed out.
+int denoise_check_status(cudaStream_t st) {
+    unsigned int* d_status = nullptr;
+    int rc = report(status_word(&d_status), "status word");
+    if (rc) return rc;
+    unsigned int h = 0;
+    rc = report(cudaMemcpyAsync(&h, d_status, sizeof h, cudaMemcpyDeviceToHost, st), "status copy");
+    if (rc) return rc;
+    rc = report(cudaStreamSynchronize(st), "status sync");
+    if (rc) return rc;
+    if (h) {
+        cudaMemsetAsync(d_status, 0, sizeof h, st);
+        cudaStreamSynchronize(st);
+        set_last_error("a tensor-core completion wait timed out (result not written)");
+        return SDE_EDEVICE;
+    }
+    return SDE_OK;
+}
+
+}  // namespace sde
+
+using namespace sde;
+
+extern "C" int sde_gemm_bf16(const void* d_A, const void* d_B, float* d_D, int M, int N, int K, void* stream) {
+    if (!d_A || !d_B || !d_D || M < 1 || N < 16 || N > 256 || (N % 16) || K < 16 || (K % 16)) {
+        set_last_error("sde_gemm_bf16: need M >= 1, N a multiple of 16 in [16, 256], K a multiple of 16");
+        return SDE_EINVAL;
+    }
+    if (((uintptr_t)d_A | (uintptr_t)d_B) & 15) {
+        set_last_error("sde_gemm_bf16: A and B must be 16-byte aligned");
+        return SDE_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* d_status = nullptr;
+    int rc = report(status_word(&d_status), "status word");
+    if (rc) return rc;
+    const size_t smem = 128 * 64 * 2 + 256 * 64 * 2 + 64;
+    rc = report(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                "cudaFuncSetAttribute");
+    if (rc) return rc;
+    k_gemm_bf16<<<(M + 127) / 128, 128, smem, st>>>(static_cast<const __nv_bfloat16*>(d_A),
+                                                       static_cast<const __nv_bfloat16*>(d_B), d_D, M, N, K,
+                                                       d_status);
+    rc = report(cudaGetLastError(), "k_gemm_bf16 launch");
+    if (rc) return rc;
+    return denoise_check_status(st);
+}
+
+// ============================================================================
+// 3D convolution (3x3x3, stride 1, zero padding 1) as an implicit GEMM.
+// Activations are channels-last BF16: x[n][z][y][x][c].  Weights w[co][tap][ci]
+// (tap = 9 kz + 3 ky + kx).  GEMM: rows = 128 output voxels of one sample,
+// columns = output channels, K = 27 taps x Cin.
+// ============================================================================
+namespace sde {
+namespace {
+
+struct ConvArgs {
+    const __nv_bfloat16* x;
+    const __nv_bfloat16* w;
+    const float* bias;
+    void* y;
+    int D, H, W, Cin, Cout;
+    int nvox;  // D*H*W (a multiple of 128)
+    int y_cstride, y_coffset, y_fp32, relu;
+    unsigned int* status;
+};
+
+__global__ void __launch_bounds__(128) k_conv3d(ConvArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int Cin = a.Cin, Cout = a.Cout, q8 = Cin >> 3;
+    const int a_bytes = 128 * Cin * 2, b_bytes = Cout * Cin * 2;
+    unsigned char* sA[2] = {smem, smem + a_bytes + b_bytes};
+    unsigned char* sB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * (a_bytes + b_bytes));
+    uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const long long tile0 = (long long)blockIdx.x * 128;
+    const int n = (int)(tile0 / a.nvox);
+    const int v = (int)(tile0 - (long long)n * a.nvox) + tid;  // this thread's output voxel
+    const int HW = a.H * a.W;
+    const int z = v / HW, y = (v / a.W) % a.H, xq = v % a.W;
+    const __nv_bfloat16* xin = a.x + (size_t)n * a.nvox * Cin;
+    const uint32_t ncols = Cout <= 32 ? 32u : Cout <= 64 ? 64u : Cout <= 128 ? 128u : 256u;
+    if (warp == 0) {
+        umma::tmem_alloc(slot, ncols);
+        umma::tmem_relinquish();
+    }
+    if (tid == 0) {
+        umma::mbar_init(&mbar[0], 1);
+        umma::mbar_init(&mbar[1], 1);
+    }
+    auto load = [&](int tap, int s) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const int zz = z + dz, yy = y + dy, xx = xq + dx;
+        const bool in = (unsigned)zz < (unsigned)a.D && (unsigned)yy < (unsigned)a.H && (unsigned)xx < (unsigned)a.W;
+        const __nv_bfloat16* src = in ? xin + ((size_t)(zz * a.H + yy) * a.W + xx) * Cin : xin;
+        const uint32_t dst = umma::smem_addr(sA[s]) + (uint32_t)((tid >> 3) * q8) * 128u + (uint32_t)(tid & 7) * 16u;
+        for (int q = 0; q < q8; ++q) umma::cp_async16(dst + q * 128, src + q * 8, in ? 16u : 0u);
+        const uint32_t bdst = umma::smem_addr(sB[s]);
+        for (int c = tid; c < Cout * q8; c += 128) {
+            const int co = c / q8, q = c - co * q8;
+            umma::cp_async16(bdst + umma::core_offset(co, q * 8, Cin), a.w + ((size_t)co * 27 + tap) * Cin + q * 8, 16u);
+        }
+        umma::cp_async_commit();
+    };
+    load(0, 0);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tbase = *slot;
+    const uint32_t idesc = umma::idesc_bf16_f32(128, Cout);
+    uint32_t waits[2] = {0u, 0u};
+    bool ok = true;
+    for (int t = 0; t < 27; ++t) {
+        const int s = t & 1;
+        umma::cp_async_wait_all();
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (tid == 0) {
+            for (int ks = 0; ks < (Cin >> 4); ++ks) {
+                uint64_t ad = umma::smem_desc(umma::smem_addr(sA[s]) + ks * 256, 128, 16 * Cin);
+                uint64_t bd = umma::smem_desc(umma::smem_addr(sB[s]) + ks * 256, 128, 16 * Cin);
+                umma::mma_bf16(tbase, ad, bd, idesc, (t > 0 || ks > 0) ? 1u : 0u);
+            }
+            umma::mma_commit(&mbar[s]);
+        }
+        if (t + 1 < 27) {
+            const int s2 = (t + 1) & 1;
+            if (t >= 1) {  // the MMAs of tap t-1 read stage s2: wait before overwriting it
+                bool done = umma::mbar_wait(&mbar[s2], waits[s2] & 1u, kWaitCycles);
+                waits[s2] += 1;
+                if (!__syncthreads_and(done ? 1 : 0)) {
+                    ok = false;
+                    break;
+                }
+            }
+            load(t + 1, s2);
+        }
+    }
+    if (ok) {  // the last tap (26) used stage 0; its completion implies all earlier MMAs
+        bool done = umma::mbar_wait(&mbar[0], waits[0] & 1u, kWaitCycles);
+        ok = __syncthreads_and(done ? 1 : 0) != 0;
+    }
+    umma::fence_after_sync();
+    if (ok) {
+        const size_t vox = (size_t)n * a.nvox + (size_t)v;
+        for (int c = 0; c < Cout; c += 8) {
+            float r[8];
+            umma::tmem_ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, r);
+            for (int j = 0; j < 8; ++j) {
+                if (a.bias) r[j] += a.bias[c + j];
+                if (a.relu) r[j] = fmaxf(r[j], 0.f);
+            }
+            if (a.y_fp32) {
+                float* yo = static_cast<float*>(a.y) + vox * a.y_cstride + a.y_coffset + c;
+                reinterpret_cast<float4*>(yo)[0] = make_float4(r[0], r[1], r[2], r[3]);
+                reinterpret_cast<float4*>(yo)[1] = make_float4(r[4], r[5], r[6], r[7]);
+            } else {
+                __nv_bfloat162 p[4];
+                for (int j = 0; j < 4; ++j) p[j] = __floats2bfloat162_rn(r[2 * j], r[2 * j + 1]);
+                __nv_bfloat16* yo = static_cast<__nv_bfloat16*>(a.y) + vox * a.y_cstride + a.y_coffset + c;
+                *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<uint4*>(p);
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(a.status, 1u);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) umma::tmem_dealloc(tbase, ncols);
+}
+
+// Weight gradient: dw[co][tap][ci] += sum_v dy[v][co] x[v + off(tap)][ci].  One CTA per
+// (tap, voxel chunk); the GEMM has rows = co (padded to 128), columns = ci, K = voxels,
+// with both operands M/N-major (channels contiguous, as stored).
+struct WgradArgs {
+    const __nv_bfloat16* x;   // [n][V][Cin]
+    const __nv_bfloat16* dy;  // [n][V][Cout]
+    float* dw;                // [Cout][27][Cin], accumulated
+    int D, H, W, Cin, Cout, nvox, batch, chunk;
+    unsigned int* status;
+};
+
+__global__ void __launch_bounds__(128) k_conv3d_wgrad(WgradArgs a) {
+    constexpr int KV = 64;  // voxels per stage
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Cin = a.Cin, Cout = a.Cout;
+    const int a_bytes = KV * 128 * 2, b_bytes = KV * Cin * 2;
+    unsigned char* sA[2] = {smem, smem + a_bytes + b_bytes};
+    unsigned char* sB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * (a_bytes + b_bytes));
+    uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const int tap = blockIdx.y;
+    const int dz = tap / 9 - 1, dy_ = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const long long total = (long long)a.batch * a.nvox;
+    const long long c0 = (long long)blockIdx.x * a.chunk;
+    const long long c1 = min(c0 + a.chunk, total);
+    const int HW = a.H * a.W;
+    const uint32_t ncols = Cin <= 32 ? 32u : Cin <= 64 ? 64u : Cin <= 128 ? 128u : 256u;
+    if (warp == 0) {
+        umma::tmem_alloc(slot, ncols);
+        umma::tmem_relinquish();
+    }
+    if (tid == 0) {
+        umma::mbar_init(&mbar[0], 1);
+        umma::mbar_init(&mbar[1], 1);
+    }
+    // stage s <- voxels [g, g+KV): A rows are 16-byte groups of 8 co (m-group), one per
+    // (voxel, m-group); B the same for ci of the shifted voxel.  M/N-major core matrix:
+    // row = voxel % 8, the 16 bytes = 8 channels; [k-group][m-group] order.
+    auto load = [&](long long g, int s) {
+        const uint32_t adst = umma::smem_addr(sA[s]), bdst = umma::smem_addr(sB[s]);
+        for (int c = tid; c < KV * 16; c += 128) {  // 128 rows of A = 16 m-groups of co
+            const int kv = c >> 4, mg = c & 15;
+            const long long gv = g + kv;
+            const bool in = gv < c1 && mg * 8 < Cout;
+            const __nv_bfloat16* src = in ? a.dy + (size_t)gv * Cout + mg * 8 : a.dy;
+            umma::cp_async16(adst + (uint32_t)(((kv >> 3) * 16 + mg) * 128 + (kv & 7) * 16), src, in ? 16u : 0u);
+        }
+        const int ng8 = Cin >> 3;
+        for (int c = tid; c < KV * ng8; c += 128) {
+            const int kv = c / ng8, ng = c - kv * ng8;
+            const long long gv = g + kv;
+            bool in = gv < c1;
+            const __nv_bfloat16* src = a.x;
+            if (in) {
+                const int nn = (int)(gv / a.nvox), v = (int)(gv - (long long)nn * a.nvox);
+                const int zz = v / HW + dz, yy = (v / a.W) % a.H + dy_, xx = v % a.W + dx;
+                in = (unsigned)zz < (unsigned)a.D && (unsigned)yy < (unsigned)a.H && (unsigned)xx < (unsigned)a.W;
+                if (in) src = a.x + ((size_t)nn * a.nvox + (size_t)(zz * a.H + yy) * a.W + xx) * Cin + ng * 8;
+            }
+            umma::cp_async16(bdst + (uint32_t)(((kv >> 3) * ng8 + ng) * 128 + (kv & 7) * 16), src, in ? 16u : 0u);
+        }
+        umma::cp_async_commit();
+    };
+    load(c0, 0);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tbase = *slot;
+    const uint32_t idesc = umma::idesc_bf16_f32(128, Cin, 1, 1);
+    const int steps = (int)((c1 - c0 + KV - 1) / KV);
+    uint32_t waits[2] = {0u, 0u};
+    bool ok = true;
+    for (int t = 0; t < steps; ++t) {
+        const int s = t & 1;
+        umma::cp_async_wait_all();
+        umma::fence_async_smem();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (tid == 0) {
+            for (int ks = 0; ks < KV / 16; ++ks) {  // two k-groups of 8 voxels per instruction
+                uint64_t ad = umma::smem_desc(umma::smem_addr(sA[s]) + ks * 2 * 16 * 128, 16 * 128, 128);
+                uint64_t bd = umma::smem_desc(umma::smem_addr(sB[s]) + ks * 2 * (Cin >> 3) * 128, (Cin >> 3) * 128, 128);
+                umma::mma_bf16(tbase, ad, bd, idesc, (t > 0 || ks > 0) ? 1u : 0u);
+            }
+            umma::mma_commit(&mbar[s]);
+        }
+        if (t + 1 < steps) {
+            const int s2 = (t + 1) & 1;
+            if (t >= 1) {
+                bool done = umma::mbar_wait(&mbar[s2], waits[s2] & 1u, kWaitCycles);
+                waits[s2] += 1;
+                if (!__syncthreads_and(done ? 1 : 0)) {
+                    ok = false;
+                    break;
+                }
+            }
+            load(c0 + (long long)(t + 1) * KV, s2);
+        }
+    }
+    if (ok && steps > 0) {
+        const int sl = (steps - 1) & 1;
+        bool done = umma::mbar_wait(&mbar[sl], waits[sl] & 1u, kWaitCycles);
+        ok = __syncthreads_and(done ? 1 : 0) != 0;
+    }
+    umma::fence_after_sync();
+    if (ok && steps > 0) {
+        const int co = 32 * warp + lane;
+        for (int c = 0; c < Cin; c += 8) {
+            float r[8];
+            umma::tmem_ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, r);
+            if (co < Cout)
+                for (int j = 0; j < 8; ++j) atomicAdd(&a.dw[((size_t)co * 27 + tap) * Cin + c + j], r[j]);
+        }
+    } else if (!ok && tid == 0) {
+        atomicOr(a.status, 1u);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) umma::tmem_dealloc(tbase, ncols);
+}
+
+// wd[ci][26 - tap][co] = w[co][tap][ci]: the data gradient of a 3x3x3 convolution is
+// the convolution of dy with these weights.
+__global__ void k_flip_weights(const __nv_bfloat16* w, __nv_bfloat16* wd, int Cin, int Cout) {
+    const int n = Cout * 27 * Cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = i % Cin, tap = (i / Cin) % 27, co = i / (27 * Cin);
+        wd[((size_t)ci * 27 + (26 - tap)) * Cout + co] = w[i];
+    }
+}
+
+}  // namespace
+
+cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st) {
+    const size_t smem = 2 * ((size_t)128 * a.Cin * 2 + (size_t)a.Cout * a.Cin * 2) + 64;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)batch * a.nvox / 128;
+    k_conv3d<<<(unsigned)tiles, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad_launch(const WgradArgs& a, cudaStream_t st) {
+    const size_t smem = 2 * ((size_t)64 * 128 * 2 + (size_t)64 * a.Cin * 2) + 64;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)a.batch * a.nvox;
+    dim3 grid((unsigned)((total + a.chunk - 1) / a.chunk), 27);
+    k_conv3d_wgrad<<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sde
+
+static bool conv_shape_ok(int D, int H, int W, int Cin, int Cout, int batch) {
+    long long nvox = (long long)D * H * W;
+    return batch >= 1 && D >= 1 && H >= 1 && W >= 1 && nvox % 128 == 0 && nvox * batch < (1ll << 31) &&
+           Cin >= 16 && Cin <= 192 && Cin % 16 == 0 && Cout >= 16 && Cout <= 256 && Cout % 16 == 0;
+}
+
+extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int W, int Cin, const void* d_w,
+                                  const float* d_bias, int Cout, void* d_y, int y_cstride, int y_coffset,
+                                  int y_fp32, int relu, void* stream) {
+    if (!d_x || !d_w || !d_y || !conv_shape_ok(D, H, W, Cin, Cout, batch) || y_cstride < Cout + y_coffset ||
+        y_coffset < 0 || (y_coffset % 8) || (y_cstride % 8)) {
+        set_last_error("sde_conv3d_forward: need D*H*W a multiple of 128, Cin in 16..192 and Cout in 16..256 "
+                       "(multiples of 16), y_cstride >= Cout + y_coffset, both multiples of 8");
+        return SDE_EINVAL;
+    }
+    unsigned int* d_status = nullptr;
+    int rc = report(status_word(&d_status), "status word");
+    if (rc) return rc;
+    ConvArgs a;
+    a.x = static_cast<const __nv_bfloat16*>(d_x);
+    a.w = static_cast<const __nv_bfloat16*>(d_w);
+    a.bias = d_bias;
+    a.y = d_y;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.Cin = Cin;
+    a.Cout = Cout;
+    a.nvox = D * H * W;
+    a.y_cstride = y_cstride;
+    a.y_coffset = y_coffset;
+    a.y_fp32 = y_fp32;
+    a.relu = relu;
+    a.status = d_status;
+    return report(conv3d_launch(a, batch, (cudaStream_t)stream), "k_conv3d launch");
+}
+
+extern "C" int sde_conv3d_wgrad(const void* d_x, const void* d_dy, float* d_dw, int batch, int D, int H, int W,
+                                int Cin, int Cout, void* stream) {
+    if (!d_x || !d_dy || !d_dw || !conv_shape_ok(D, H, W, Cin, Cout, batch) || Cout > 128) {
+        set_last_error("sde_conv3d_wgrad: need D*H*W a multiple of 128, Cin in 16..192, Cout in 16..128 "
+                       "(multiples of 16)");
+        return SDE_EINVAL;
+    }
+    unsigned int* d_status = nullptr;
+    int rc = report(status_word(&d_status), "status word");
+    if (rc) return rc;
+    WgradArgs a;
+    a.x = static_cast<const __nv_bfloat16*>(d_x);
+    a.dy = static_cast<const __nv_bfloat16*>(d_dy);
+    a.dw = d_dw;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.Cin = Cin;
+    a.Cout = Cout;
+    a.nvox = D * H * W;
+    a.batch = batch;
+    a.chunk = 8192;
+    a.status = d_status;
+    return report(wgrad_launch(a, (cudaStream_t)stream), "k_conv3d_wgrad launch");
+}
+
+extern "C" int sde_conv3d_flip_weights(const void* d_w, void* d_wd, int Cin, int Cout, void* stream) {
+    if (!d_w || !d_wd || Cin < 1 || Cout < 1) {
+        set_last_error("sde_conv3d_flip_weights: bad arguments");
+        return SDE_EINVAL;
+    }
+    k_flip_weights<<<256, 256, 0, (cudaStream_t)stream>>>(static_cast<const __nv_bfloat16*>(d_w),
+                                                            static_cast<__nv_bfloat16*>(d_wd), Cin, Cout);
+    return report(cudaGetLastError(), "k_flip_weights launch");
+}
+
+extern "C" int sde_denoise_status(void* stream) { return denoise_check_status((cudaStream_t)stream); }

@@ -303,3 +303,19 @@ def test_autotune_and_graph_launch_keep_the_tally(sde_gpu):
             d.run(wl.spots, seed=seed)
             _, e, _ = d.fetch(dose=False)
             assert np.array_equal(e, want)
+
+
+def test_insert150_gamma_at_one_million_protons(sde_gpu, oracle_lib):
+    """configs[2]: 3D gamma (2 %/0.5 mm, local, 1 % threshold) of the GPU dose against the
+    oracle at 10^6 protons.  Both doses are noisy, so the pass rate is compared with the pass
+    rate of the oracle against itself (another seed): equal distributions give equal rates."""
+    wl = insert150(1_000_000)
+    dg, eg, bg = sde_gpu.run_workload(wl, seed=21)
+    do1, _, bo = O.run_workload(wl, seed=22)
+    do2, _, _ = O.run_workload(wl, seed=23)
+    assert balanced(bg) and balanced(bo)
+    g_go = A.gamma_pass_rate(do1, dg, wl.voxel_mm)
+    g_oo = A.gamma_pass_rate(do1, do2, wl.voxel_mm)
+    print({"gamma_gpu_vs_oracle": g_go, "gamma_oracle_vs_oracle": g_oo})
+    assert g_go > 0.9
+    assert abs(g_go - g_oo) < 0.01
