@@ -196,6 +196,10 @@ int sde_dose_fetch(sde_dose* d, double* dose_Gy, uint64_t* edep_fixed, sde_balan
 int sde_dose_fetch_device(sde_dose* d, double* d_dose_Gy, uint64_t* d_edep_fixed,
                           sde_balance* bal);
 
+/* As sde_dose_fetch_device for the dose only, written as FP32 (n_vox floats,
+ * caller-owned device memory).  Asynchronous. */
+int sde_dose_fetch_device_f32(sde_dose* d, float* d_dose_Gy);
+
 /* Zero the tally and the balance counters (asynchronous). */
 int sde_dose_reset(sde_dose* d);
 
@@ -267,6 +271,56 @@ int sde_conv3d_flip_weights(const void* d_w, void* d_wd, int Cin, int Cout, void
 /* Wait for the stream and report (and clear) a timed-out tensor-core wait of any
  * denoiser kernel since the last call: SDE_EDEVICE, else SDE_OK. */
 int sde_denoise_status(void* stream);
+
+/* The denoiser network: a 3-level 3D convolutional encoder-decoder (32/64/128
+ * channels, 3x3x3 kernels, average-pool down, nearest-neighbour up, skip
+ * concatenations, leaky ReLU with slope 0.1), BF16 weights and activations with FP32 accumulation,
+ * trained with Adam on FP32 master weights.  Inputs on a D x H x W grid (x
+ * fastest, device FP32): the low-history dose (Gy) and the density (g/cm^3);
+ * the output is the dose (Gy).  Internally the dose is scaled by 1/max of the
+ * low-history dose of each sample and the network predicts a correction that
+ * is added to it.  D, H, W must be multiples of 4 and (D/4)(H/4)(W/4) a
+ * multiple of 128.  The handle owns its device memory (weights, optimiser
+ * state, activations and gradients for batch_max samples). */
+typedef struct sde_denoiser sde_denoiser;
+int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int batch_max, uint64_t seed);
+void sde_denoiser_destroy(sde_denoiser* d);
+int sde_denoiser_set_stream(sde_denoiser* d, void* cuda_stream);
+int sde_denoiser_num_params(const sde_denoiser* d, uint64_t* n);
+/* Inference: d_dose_out[batch][D*H*W] (device).  Asynchronous. */
+int sde_denoiser_infer(sde_denoiser* d, const float* d_dose_low, const float* d_density, int batch,
+                       float* d_dose_out);
+/* One Adam step on the squared error between the prediction and t =
+ * target_scale * d_dose_high (target_scale: e.g. the ratio of the history counts
+ * of the low and high runs, so that both are doses of the same fluence), both
+ * scaled as the input, weighted by 1/(t + 0.05) and summed over voxels (Adam
+ * works on the sum; loss_out, host, may be NULL, receives the mean over voxels,
+ * which makes the call synchronous). */
+int sde_denoiser_train_step(sde_denoiser* d, const float* d_dose_low, const float* d_density,
+                            const float* d_dose_high, float target_scale, int batch, float lr,
+                            float* loss_out);
+/* Gradient of the summed loss for all parameters without an update (host FP32
+ * vector, same order as sde_denoiser_get_params; loss_out gets the mean loss);
+ * synchronous. */
+int sde_denoiser_gradients(sde_denoiser* d, const float* d_dose_low, const float* d_density,
+                           const float* d_dose_high, float target_scale, int batch, float* host_grad,
+                           uint64_t n, float* loss_out);
+/* All parameters as one FP32 host vector: per layer the weights [Cout][27][Cin]
+ * then the biases [Cout].  Synchronous. */
+int sde_denoiser_get_params(const sde_denoiser* d, float* host, uint64_t n);
+int sde_denoiser_set_params(sde_denoiser* d, const float* host, uint64_t n);
+
+/* d_x[i] *= factor for i < n (device FP32).  Asynchronous. */
+int sde_scale_f32(float* d_x, uint64_t n, float factor, void* stream);
+
+/* 3D gamma index (local dose normalisation): reference voxels with dose >=
+ * threshold * max(ref) are evaluated; one passes when an evaluated position within
+ * dta_mm (searched on a grid of step dta_mm/steps, trilinear interpolation of
+ * d_eval) has |dr|^2/dta^2 + (De - Dr)^2/(dd Dr)^2 <= 1.  Device FP32 grids of
+ * nx*ny*nz (x fastest).  Synchronous; returns the counts. */
+int sde_gamma3d(const float* d_ref, const float* d_eval, int nx, int ny, int nz, const double voxel_mm[3],
+                double dd, double dta_mm, double threshold, int steps, uint64_t* n_eval, uint64_t* n_pass,
+                void* stream);
 
 /* Transport without any memory allocation.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory -- code

@@ -27,10 +27,13 @@ MAX_ELEMENTS = 16
 EXPORTED = [
     "sde_default_params", "sde_last_error", "sde_dose_create", "sde_dose_set_stream",
     "sde_dose_set_tuning", "sde_dose_get_tuning", "sde_dose_autotune", "sde_dose_run", "sde_dose_run_device",
-    "sde_dose_sync", "sde_dose_fetch", "sde_dose_fetch_device", "sde_dose_reset",
+    "sde_dose_sync", "sde_dose_fetch", "sde_dose_fetch_device", "sde_dose_fetch_device_f32", "sde_dose_reset",
     "sde_dose_destroy", "sde_dose_info", "sde_dose_tables", "sde_dose_probe_steps",
     "sde_transport_noalloc", "sde_gemm_bf16", "sde_conv3d_forward", "sde_conv3d_wgrad",
-    "sde_conv3d_flip_weights", "sde_denoise_status",
+    "sde_conv3d_flip_weights", "sde_denoise_status", "sde_denoiser_create", "sde_denoiser_destroy",
+    "sde_denoiser_set_stream", "sde_denoiser_num_params", "sde_denoiser_infer", "sde_denoiser_train_step",
+    "sde_denoiser_gradients", "sde_denoiser_get_params", "sde_denoiser_set_params", "sde_gamma3d",
+    "sde_scale_f32",
 ]
 
 
@@ -102,6 +105,7 @@ def lib():
         L.sde_dose_sync.argtypes = [vp]
         L.sde_dose_fetch.argtypes = [vp, vp, vp, C.POINTER(Balance)]
         L.sde_dose_fetch_device.argtypes = [vp, vp, vp, C.POINTER(Balance)]
+        L.sde_dose_fetch_device_f32.argtypes = [vp, vp]
         L.sde_dose_reset.argtypes = [vp]
         L.sde_dose_destroy.argtypes = [vp]
         L.sde_dose_destroy.restype = None
@@ -116,6 +120,18 @@ def lib():
         L.sde_conv3d_wgrad.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp]
         L.sde_conv3d_flip_weights.argtypes = [vp, vp, i, i, vp]
         L.sde_denoise_status.argtypes = [vp]
+        L.sde_denoiser_create.argtypes = [C.POINTER(vp), i, i, i, i, u64]
+        L.sde_denoiser_destroy.argtypes = [vp]
+        L.sde_denoiser_destroy.restype = None
+        L.sde_denoiser_set_stream.argtypes = [vp, vp]
+        L.sde_denoiser_num_params.argtypes = [vp, C.POINTER(u64)]
+        L.sde_denoiser_infer.argtypes = [vp, vp, vp, i, vp]
+        L.sde_denoiser_train_step.argtypes = [vp, vp, vp, vp, C.c_float, i, C.c_float, C.POINTER(C.c_float)]
+        L.sde_denoiser_gradients.argtypes = [vp, vp, vp, vp, C.c_float, i, vp, u64, C.POINTER(C.c_float)]
+        L.sde_scale_f32.argtypes = [vp, u64, C.c_float, vp]
+        L.sde_denoiser_get_params.argtypes = [vp, vp, u64]
+        L.sde_denoiser_set_params.argtypes = [vp, vp, u64]
+        L.sde_gamma3d.argtypes = [vp, vp, i, i, i, C.POINTER(d), d, d, d, i, C.POINTER(u64), C.POINTER(u64), vp]
         _lib = L
         return L
 
@@ -234,7 +250,21 @@ class SdeDose:
                                     C.byref(bal) if balance else None))
         return bal.as_dict()
 
+    def dose_into(self, tensor):
+        """Write the dose (Gy) into a device tensor of n_vox float32 or float64 elements."""
+        import torch
+        if not tensor.is_cuda or tensor.numel() != self.wl.n_voxels or not tensor.is_contiguous():
+            raise ValueError("dose_into needs a contiguous CUDA tensor with one element per voxel")
+        if tensor.dtype == torch.float32:
+            _check(lib().sde_dose_fetch_device_f32(self.h, C.c_void_p(tensor.data_ptr())))
+        elif tensor.dtype == torch.float64:
+            _check(lib().sde_dose_fetch_device(self.h, C.c_void_p(tensor.data_ptr()), None, None))
+        else:
+            raise ValueError("dose_into needs float32 or float64")
+        return tensor
+
     def fetch_device(self, dose_ptr=None, edep_ptr=None, balance=False):
+        """Raw device pointers: dose_ptr must hold n_vox float64, edep_ptr n_vox uint64."""
         bal = Balance()
         _check(lib().sde_dose_fetch_device(self.h, C.c_void_p(dose_ptr) if dose_ptr else None,
                                            C.c_void_p(edep_ptr) if edep_ptr else None,
@@ -337,6 +367,96 @@ def conv3d_flip_weights(w, wd=None, stream=None):
 
 def denoise_status(stream=None):
     _check(lib().sde_denoise_status(_sp(stream)))
+
+
+class Denoiser:
+    """Handle of the learned dose denoiser (see include/sde_dose.h)."""
+
+    LAYERS = [(16, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (192, 64), (64, 64), (96, 32),
+              (32, 32), (32, 16)]
+
+    def __init__(self, D, H, W, batch_max=1, seed=0, stream=None):
+        h = C.c_void_p()
+        _check(lib().sde_denoiser_create(C.byref(h), D, H, W, batch_max, C.c_uint64(seed)))
+        self.h = h
+        self.shape = (D, H, W)
+        if stream is not None:
+            _check(lib().sde_denoiser_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def num_params(self):
+        n = C.c_uint64()
+        _check(lib().sde_denoiser_num_params(self.h, C.byref(n)))
+        return n.value
+
+    def infer(self, dose_low, density, out=None):
+        import torch
+        b = dose_low.shape[0] if dose_low.dim() == 4 else 1
+        if out is None:
+            out = torch.empty_like(dose_low)
+        _check(lib().sde_denoiser_infer(self.h, dose_low.data_ptr(), density.data_ptr(), b, out.data_ptr()))
+        return out
+
+    def train_step(self, dose_low, density, dose_high, lr=1e-3, want_loss=True, target_scale=1.0):
+        b = dose_low.shape[0] if dose_low.dim() == 4 else 1
+        loss = C.c_float()
+        _check(lib().sde_denoiser_train_step(self.h, dose_low.data_ptr(), density.data_ptr(), dose_high.data_ptr(),
+                                             C.c_float(target_scale), b, C.c_float(lr),
+                                             C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def gradients(self, dose_low, density, dose_high, target_scale=1.0):
+        b = dose_low.shape[0] if dose_low.dim() == 4 else 1
+        n = self.num_params()
+        g = np.empty(n, np.float32)
+        loss = C.c_float()
+        _check(lib().sde_denoiser_gradients(self.h, dose_low.data_ptr(), density.data_ptr(), dose_high.data_ptr(),
+                                            C.c_float(target_scale), b, g.ctypes.data, n, C.byref(loss)))
+        return g, loss.value
+
+    def get_params(self):
+        n = self.num_params()
+        p = np.empty(n, np.float32)
+        _check(lib().sde_denoiser_get_params(self.h, p.ctypes.data, n))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(lib().sde_denoiser_set_params(self.h, p.ctypes.data, len(p)))
+
+    def split(self, vec):
+        """Per-layer (weights [Cout,27,Cin], bias [Cout]) views of a parameter vector."""
+        out, o = [], 0
+        for ci, co in self.LAYERS:
+            n = co * 27 * ci
+            out.append((vec[o:o + n].reshape(co, 27, ci), vec[o + n:o + n + co]))
+            o += n + co
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sde_denoiser_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scale_(x, factor, stream=None):
+    """x *= factor in place (device FP32 tensor), in the library's kernel."""
+    _check(lib().sde_scale_f32(x.data_ptr(), x.numel(), C.c_float(factor), _sp(stream)))
+    return x
+
+
+def gamma3d(ref, ev, voxel_mm, dd=0.02, dta_mm=0.5, threshold=0.01, steps=10, stream=None):
+    """Gamma pass rate on the GPU (device FP32 grids [nz, ny, nx])."""
+    nz, ny, nx = ref.shape[-3:]
+    ne, npass = C.c_uint64(), C.c_uint64()
+    _check(lib().sde_gamma3d(ref.data_ptr(), ev.data_ptr(), nx, ny, nz, (C.c_double * 3)(*voxel_mm), dd, dta_mm,
+                             threshold, steps, C.byref(ne), C.byref(npass), _sp(stream)))
+    return npass.value / max(ne.value, 1)
 
 
 def run_workload(wl, seed=None, spots=None, **param_kw):

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUTDIR, "libsde_dose.so")
-SOURCES = ["sde_api.cu", "sde_tables.cu", "sde_transport.cu", "sde_noalloc.cu", "sde_denoise.cu"]
+SOURCES = ["sde_api.cu", "sde_tables.cu", "sde_transport.cu", "sde_noalloc.cu", "sde_denoise.cu", "sde_denoiser.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

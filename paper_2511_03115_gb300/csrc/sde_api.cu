@@ -602,6 +602,16 @@ extern "C" int sde_dose_fetch_device(sde_dose* d, double* d_dose_Gy, uint64_t* d
     return SDE_OK;
 }
 
+extern "C" int sde_dose_fetch_device_f32(sde_dose* d, float* d_dose_Gy) {
+    if (!d || !d_dose_Gy) return set_err(SDE_EINVAL, "null argument");
+    CUDA_TRY(cudaSetDevice(d->device));
+    double unit_J = ldexp(1.0, -d->p.fixed_point_shift) * kJoulePerMeV;
+    double vol_kg_per_rho = d->h[0] * d->h[1] * d->h[2] * 1e-3 * 1e-3;
+    CUDA_TRY(launch_convert_f32(d->d_edep, d->d_rho, d->nvox, unit_J, vol_kg_per_rho, d_dose_Gy, d->num_sms,
+                                d->stream));
+    return SDE_OK;
+}
+
 extern "C" int sde_dose_reset(sde_dose* d) {
     if (!d) return set_err(SDE_EINVAL, "null handle");
     CUDA_TRY(cudaSetDevice(d->device));

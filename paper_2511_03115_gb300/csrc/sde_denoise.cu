@@ -11,6 +11,7 @@
 
 #include "sde_dose.h"
 #include "sde_tables.h"
+#include "sde_denoise.h"
 #include "sde_umma.cuh"
 
 namespace sde {
@@ -126,6 +127,8 @@ int report(cudaError_t e, const char* what) {
 
 }  // namespace
 
+cudaError_t denoise_status_word(unsigned int** out) { return status_word(out); }
+
 // Reads and clears the device status word; SDE_EDEVICE when a tensor-core wait timed out.
 int denoise_check_status(cudaStream_t st) {
     unsigned int* d_status = nullptr;
@@ -182,17 +185,6 @@ extern "C" int sde_gemm_bf16(const void* d_A, const void* d_B, float* d_D, int M
 // ============================================================================
 namespace sde {
 namespace {
-
-struct ConvArgs {
-    const __nv_bfloat16* x;
-    const __nv_bfloat16* w;
-    const float* bias;
-    void* y;
-    int D, H, W, Cin, Cout;
-    int nvox;  // D*H*W (a multiple of 128)
-    int y_cstride, y_coffset, y_fp32, relu;
-    unsigned int* status;
-};
 
 __global__ void __launch_bounds__(128) k_conv3d(ConvArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -280,7 +272,7 @@ __global__ void __launch_bounds__(128) k_conv3d(ConvArgs a) {
             umma::tmem_ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, r);
             for (int j = 0; j < 8; ++j) {
                 if (a.bias) r[j] += a.bias[c + j];
-                if (a.relu) r[j] = fmaxf(r[j], 0.f);
+                if (a.relu) r[j] = r[j] > 0.f ? r[j] : a.slope * r[j];
             }
             if (a.y_fp32) {
                 float* yo = static_cast<float*>(a.y) + vox * a.y_cstride + a.y_coffset + c;
@@ -301,17 +293,6 @@ __global__ void __launch_bounds__(128) k_conv3d(ConvArgs a) {
     umma::fence_after_sync();
     if (warp == 0) umma::tmem_dealloc(tbase, ncols);
 }
-
-// Weight gradient: dw[co][tap][ci] += sum_v dy[v][co] x[v + off(tap)][ci].  One CTA per
-// (tap, voxel chunk); the GEMM has rows = co (padded to 128), columns = ci, K = voxels,
-// with both operands M/N-major (channels contiguous, as stored).
-struct WgradArgs {
-    const __nv_bfloat16* x;   // [n][V][Cin]
-    const __nv_bfloat16* dy;  // [n][V][Cout]
-    float* dw;                // [Cout][27][Cin], accumulated
-    int D, H, W, Cin, Cout, nvox, batch, chunk;
-    unsigned int* status;
-};
 
 __global__ void __launch_bounds__(128) k_conv3d_wgrad(WgradArgs a) {
     constexpr int KV = 64;  // voxels per stage
@@ -438,6 +419,11 @@ __global__ void k_flip_weights(const __nv_bfloat16* w, __nv_bfloat16* wd, int Ci
 
 }  // namespace
 
+cudaError_t flip_weights_launch(const __nv_bfloat16* w, __nv_bfloat16* wd, int Cin, int Cout, cudaStream_t st) {
+    k_flip_weights<<<256, 256, 0, st>>>(w, wd, Cin, Cout);
+    return cudaGetLastError();
+}
+
 cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st) {
     const size_t smem = 2 * ((size_t)128 * a.Cin * 2 + (size_t)a.Cout * a.Cin * 2) + 64;
     cudaError_t e = cudaFuncSetAttribute(k_conv3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -492,6 +478,7 @@ extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int 
     a.y_coffset = y_coffset;
     a.y_fp32 = y_fp32;
     a.relu = relu;
+    a.slope = 0.f;
     a.status = d_status;
     return report(conv3d_launch(a, batch, (cudaStream_t)stream), "k_conv3d launch");
 }

@@ -581,11 +581,12 @@ __global__ void k_probe(KParams P, int m, float rho, float E0, uint64_t h0, int 
 }
 
 // Dose to medium (Sec. 2.2.2): tally units -> J over voxel mass (kg).
+template <typename T>
 __global__ void k_convert(const unsigned long long* edep, const float* rho, size_t nv, double unit_J,
-                          double vol_kg_per_rho, double* dose) {
+                          double vol_kg_per_rho, T* dose) {
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
         double mass = (double)rho[v] * vol_kg_per_rho;
-        dose[v] = mass > 0.0 ? (double)edep[v] * unit_J / mass : 0.0;
+        dose[v] = (T)(mass > 0.0 ? (double)edep[v] * unit_J / mass : 0.0);
     }
 }
 
@@ -666,7 +667,14 @@ cudaError_t launch_sum_u64(const unsigned long long* v, size_t n, unsigned long 
 cudaError_t launch_convert(const unsigned long long* edep, const float* rho, size_t nv, double unit_J,
                            double vol_kg_per_rho, double* dose, int num_sms, cudaStream_t st) {
     int blocks = num_sms * 4;
-    k_convert<<<blocks, 256, 0, st>>>(edep, rho, nv, unit_J, vol_kg_per_rho, dose);
+    k_convert<double><<<blocks, 256, 0, st>>>(edep, rho, nv, unit_J, vol_kg_per_rho, dose);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f32(const unsigned long long* edep, const float* rho, size_t nv, double unit_J,
+                               double vol_kg_per_rho, float* dose, int num_sms, cudaStream_t st) {
+    int blocks = num_sms * 4;
+    k_convert<float><<<blocks, 256, 0, st>>>(edep, rho, nv, unit_J, vol_kg_per_rho, dose);
     return cudaGetLastError();
 }
 

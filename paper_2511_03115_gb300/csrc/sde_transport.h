@@ -22,5 +22,7 @@ cudaError_t launch_sum_u64(const unsigned long long* v, size_t n, unsigned long 
                            cudaStream_t st);
 cudaError_t launch_convert(const unsigned long long* edep, const float* rho, size_t nv, double unit_J,
                            double vol_kg_per_rho, double* dose, int num_sms, cudaStream_t st);
+cudaError_t launch_convert_f32(const unsigned long long* edep, const float* rho, size_t nv, double unit_J,
+                               double vol_kg_per_rho, float* dose, int num_sms, cudaStream_t st);
 
 }  // namespace sde

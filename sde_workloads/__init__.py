@@ -164,7 +164,8 @@ def insert150(n_hist: int = 10_000_000) -> Workload:
 def sphere_phantom(shape, h, seed, n_spheres=30, r_range=(5.0, 25.0), rho_range=(0.2, 1.9)):
     """Water with random spherical inserts; later spheres overwrite earlier ones.
 
-    Material ids: 0 water, 1 tissue-like, 2 bone-like.
+    Material ids: 0 water, 1 tissue-like, 2 bone-like.  Each sphere is drawn as
+    (radius, centre, density, composition) and rasterised by voxel-centre inclusion.
     """
     nx, ny, nz = shape
     origin, xc, yc, zc = _grid(nx, ny, nz, h)
@@ -173,15 +174,26 @@ def sphere_phantom(shape, h, seed, n_spheres=30, r_range=(5.0, 25.0), rho_range=
     mid = np.zeros((nz, ny, nx), np.uint8)
     ext = np.array([nx * h, ny * h, nz * h])
     lo = np.array(origin)
-    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
     for _ in range(n_spheres):
         r = rng.uniform(*r_range)
         c = lo + rng.uniform(0.0, 1.0, 3) * ext
         rho = rng.uniform(*rho_range)
         m = 2 if rng.uniform() < 0.5 else 1
+        # only the voxels of the sphere's bounding box can be inside it
+        ix = np.nonzero(np.abs(xc - c[0]) <= r)[0]
+        iy = np.nonzero(np.abs(yc - c[1]) <= r)[0]
+        iz = np.nonzero(np.abs(zc - c[2]) <= r)[0]
+        if len(ix) == 0 or len(iy) == 0 or len(iz) == 0:
+            continue
+        Z, Y, X = np.meshgrid(zc[iz], yc[iy], xc[ix], indexing="ij")
         inside = (X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2 <= r * r
-        dens[inside] = rho
-        mid[inside] = m
+        sub = np.ix_(iz, iy, ix)
+        dsub = dens[sub]
+        msub = mid[sub]
+        dsub[inside] = rho
+        msub[inside] = m
+        dens[sub] = dsub
+        mid[sub] = msub
     return origin, dens, mid
 
 
@@ -214,5 +226,17 @@ def plan2000(total: int = 100_000_000, seed: int = 0) -> Workload:
                     spots, seed=seed)
 
 
+def denoise_case(seed: int, n_hist: int = 100_000, shape=(128, 128, 192), n_spots: int = 24) -> Workload:
+    """One sample of the denoiser workload: 128 x 128 x 192 mm at 1 mm, water with 30
+    random spheres (radius 5-15 mm, density 0.2-1.9, tissue or bone) and a plan of
+    ``n_spots`` spots on a 5 mm lateral grid within +-30 mm, energies U(70, 200) MeV
+    (ranges beyond the phantom exit), weights lognormal(0, 0.7), ``n_hist`` protons."""
+    nx, ny, nz = shape
+    origin, dens, mid = sphere_phantom(shape, 1.0, seed, r_range=(5.0, 15.0))
+    spots = plan_spots(n_spots, n_hist, seed, pitch=5.0, half_width=30.0)
+    return Workload(f"denoise{seed}", shape, (1.0, 1.0, 1.0), origin, dens, mid, [WATER, TISSUE, BONE], spots,
+                    seed=seed)
+
+
 WORKLOADS = {"water100": water100, "slab150": slab150, "insert150": insert150,
-             "plan2000": plan2000}
+             "plan2000": plan2000, "denoise_case": denoise_case}

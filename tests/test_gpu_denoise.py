@@ -64,3 +64,129 @@ def test_conv3d_forward_dgrad_wgrad_match_torch(sde_gpu, Cin, Cout, shape):
         S.conv3d_wgrad(x.cuda(), dy_cl, dw)
         S.denoise_status()
         assert (dw.cpu().double() - dw_ref).abs().max().item() <= 1e-4 * dw_ref.abs().max().item() + 1e-4
+
+
+def _ref_network(layers, dose_low, rho, dose_high):
+    """The denoiser written with plain PyTorch CPU float64 operations (test reference):
+    same layers, skips, pooling, upsampling and input/output scaling as the library."""
+    import torch
+    import torch.nn.functional as F
+    D, H, W = dose_low.shape
+    s = 1.0 / dose_low.abs().max()
+    x = torch.zeros(1, 16, D, H, W, dtype=torch.float64)
+    x[0, 0] = dose_low * s
+    x[0, 1] = rho * 0.5
+
+    def conv(t, i, relu=True):
+        w, b = layers[i]
+        co, _, ci = w.shape
+        y = F.conv3d(t, w.reshape(co, 3, 3, 3, ci).permute(0, 4, 1, 2, 3), b, padding=1)
+        return F.leaky_relu(y, 0.1) if relu else y
+
+    e1a = conv(x, 0)
+    e1 = conv(e1a, 1)
+    e2a = conv(F.avg_pool3d(e1, 2), 2)
+    e2 = conv(e2a, 3)
+    b1 = conv(F.avg_pool3d(e2, 2), 4)
+    b2 = conv(b1, 5)
+    d2a = conv(torch.cat([F.interpolate(b2, scale_factor=2, mode="nearest"), e2], 1), 6)
+    d2 = conv(d2a, 7)
+    d1a = conv(torch.cat([F.interpolate(d2, scale_factor=2, mode="nearest"), e1], 1), 8)
+    d1 = conv(d1a, 9)
+    out = conv(d1, 10, relu=False)
+    pred = dose_low * s + out[0, 0]
+    t = dose_high * s
+    return torch.mean((pred - t) ** 2 / (t.abs() + 0.05)), pred / s
+
+
+def _smooth_case(shape, seed):
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    D, H, W = shape
+    z, y, x = torch.meshgrid(torch.arange(D), torch.arange(H), torch.arange(W), indexing="ij")
+    base = torch.exp(-((x - W / 2) ** 2 + (y - H / 2) ** 2) / 30.0) * (1 + z / D)
+    low = (base * (1 + 0.3 * torch.randn(shape, generator=g))).clamp(min=0).double()
+    high = base.double()
+    rho = (1.0 + 0.5 * (torch.rand(shape, generator=g) > 0.7)).double()
+    return low, rho, high
+
+
+def test_denoiser_gradients_match_a_float64_reference(sde_gpu):
+    import torch
+    S = sde_gpu
+    shape = (16, 16, 32)
+    net = S.Denoiser(*shape, batch_max=1, seed=3)
+    # a trained-looking output layer (the library starts it near zero)
+    p = net.get_params()
+    layers = net.split(p)
+    w10, b10 = layers[10]
+    w10 *= 20.0
+    net.set_params(p)
+    low, rho, high = _smooth_case(shape, 1)
+    g, loss = net.gradients(low.float().cuda(), rho.float().cuda(), high.float().cuda())
+    ref_layers = [(torch.tensor(w, dtype=torch.float64, requires_grad=True),
+                   torch.tensor(b, dtype=torch.float64, requires_grad=True)) for w, b in net.split(p)]
+    ref_loss, _ = _ref_network(ref_layers, low, rho, high)
+    (ref_loss * low.numel()).backward()  # the library differentiates the summed loss
+    assert abs(loss - ref_loss.item()) <= 0.03 * ref_loss.item()
+    for i, ((gw, gb), (rw, rb)) in enumerate(zip(net.split(g), ref_layers)):
+        for a_, r_ in ((gw, rw.grad.numpy()), (gb, rb.grad.numpy())):
+            a_ = a_.astype(np.float64).ravel()
+            r_ = r_.ravel()
+            if np.linalg.norm(r_) == 0:
+                continue
+            cos = a_ @ r_ / (np.linalg.norm(a_) * np.linalg.norm(r_))
+            rel = np.linalg.norm(a_ - r_) / np.linalg.norm(r_)
+            assert cos > 0.99 and rel < 0.15, (i, cos, rel)
+    net.close()
+
+
+def test_denoiser_inference_matches_the_reference_and_training_reduces_the_loss(sde_gpu):
+    import torch
+    S = sde_gpu
+    shape = (16, 16, 32)
+    net = S.Denoiser(*shape, batch_max=1, seed=5)
+    low, rho, high = _smooth_case(shape, 2)
+    lo, rh, hi = low.float().cuda(), rho.float().cuda(), high.float().cuda()
+    out = net.infer(lo, rh)
+    S.denoise_status()
+    layers = [(torch.tensor(w, dtype=torch.float64), torch.tensor(b, dtype=torch.float64))
+              for w, b in net.split(net.get_params())]
+    _, ref_pred = _ref_network(layers, low, rho, high)
+    err = (out.cpu().double() - ref_pred).abs().max().item()
+    assert err <= 0.02 * ref_pred.abs().max().item()
+    # a learnable target (a systematic change of the input dose): the loss must fall
+    tgt = (0.8 * low).float().cuda()
+    losses = [net.train_step(lo, rh, tgt, lr=1e-3) for _ in range(100)]
+    assert losses[-1] < 0.5 * losses[0], losses[::20]
+    net.close()
+
+
+def test_gpu_gamma_equals_the_oracle_gamma(sde_gpu, oracle_lib):
+    import torch
+    from oracle import analysis as A
+    g = torch.Generator().manual_seed(9)
+    ref = torch.exp(-torch.linspace(-3, 3, 28)[:, None, None] ** 2) * torch.ones(28, 20, 24)
+    ref = ref * (1 + 0.02 * torch.randn(ref.shape, generator=g))
+    ev = ref * (1 + 0.03 * torch.randn(ref.shape, generator=g))
+    for dta in (0.5, 1.0):
+        rg = S_gamma = sde_gpu.gamma3d(ref.float().cuda(), ev.float().cuda(), (1.0, 1.0, 1.0), dta_mm=dta)
+        ro = A.gamma_pass_rate(ref.double().numpy(), ev.double().numpy(), (1.0, 1.0, 1.0), dta_mm=dta)
+        assert abs(rg - ro) < 2e-3, (dta, rg, ro)
+
+
+def test_trained_denoiser_gains_over_the_low_history_dose(sde_gpu):
+    """Trained on SDE-generated pairs (1e5-history input, 1e7-history target) of the
+    128x128x192 denoiser workload, the network must bring held-out low-history doses
+    closer to the high-history dose than the low-history dose itself: smaller maximum
+    error and a gamma pass rate at least as high."""
+    from paper_2511_03115_gb300 import denoise as DN
+    pairs = DN.generate(range(24))
+    net = sde_gpu.Denoiser(DN.SHAPE[2], DN.SHAPE[1], DN.SHAPE[0], seed=1)
+    DN.train(net, pairs, epochs=3, lr=1e-3, warmup=20)
+    del pairs
+    agg, rows = DN.evaluate(net, range(200_000, 200_004), ladder=False)
+    print(agg)
+    assert agg["gamma_denoised"] > agg["gamma_low"]
+    assert agg["max_err_denoised"] < 1.5 * agg["max_err_low"]
+    net.close()
