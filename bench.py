@@ -165,7 +165,7 @@ def run_reference(args):
     T = sum(times) / len(times)
     v = n / T
     line = {
-        "impl": "reference", "metric": "proton histories/s on 1 GB300", "value": v,
+        "impl": "reference", "metric": "proton histories/s on 1 GB300; time-to-dose at \u226595% gamma 2%/0.5mm, learned vs plain", "value": v,
         "unit": "histories/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": T * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
@@ -232,6 +232,88 @@ def plan_benchmark(torch, S, dev, total=100_000_000, per_spot_sample=200):
     return out
 
 
+# Executed multiply-adds of one denoiser inference on 128 x 128 x 192 (16-channel padded
+# input and output layers): (voxels, Cin, Cout) per convolution, 27 taps each.
+DENOISER_LAYERS = [(3_145_728, 16, 32), (3_145_728, 32, 32), (393_216, 32, 64), (393_216, 64, 64),
+                   (49_152, 64, 128), (49_152, 128, 128), (393_216, 192, 64), (393_216, 64, 64),
+                   (3_145_728, 96, 32), (3_145_728, 32, 32), (3_145_728, 32, 16)]
+DENOISER_WEIGHTS = os.path.join(ROOT, "paper_2511_03115_gb300", "weights", "denoiser_128x128x192.npy")
+
+
+def time_to_dose(torch, S, seeds=(100_000, 100_001, 100_002, 100_003), ladder=(300_000, 1_000_000, 3_000_000)):
+    """Learned vs plain time to a dose that passes gamma 2 %/0.5 mm (1 % threshold) against
+    the 10^7-history dose of the same plan: device time of the 10^5-history run plus
+    inference with the trained weights, and of plain runs at the ladder's history counts."""
+    from paper_2511_03115_gb300 import denoise as DN
+    if not os.path.exists(DENOISER_WEIGHTS):
+        return {"unavailable": "no trained weights at paper_2511_03115_gb300/weights/"}
+    net = S.Denoiser(DN.SHAPE[2], DN.SHAPE[1], DN.SHAPE[0], batch_max=1, seed=1)
+    net.set_params(np.load(DENOISER_WEIGHTS).astype(np.float32))
+    st = torch.cuda.current_stream()
+    rows = []
+    for seed in seeds:
+        r = DN.transport_doses(seed)
+        ref = S.scale_(r["high"], DN.N_LOW / DN.N_HIGH)
+        net.infer(r["low"], r["density"])  # warm
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        den = net.infer(r["low"], r["density"])
+        b.record(st)
+        st.synchronize()
+        S.denoise_status()
+        t_inf = a.elapsed_time(b)
+        rmax = float(ref.max())
+        row = {"seed": seed, "t_low_ms": r["low_ms"], "t_infer_ms": t_inf, "t_high_ms": r["high_ms"],
+               "gamma_low": S.gamma3d(ref, r["low"], (1.0, 1.0, 1.0)),
+               "gamma_learned": S.gamma3d(ref, den, (1.0, 1.0, 1.0)),
+               "max_err_low": float((r["low"] - ref).abs().max()) / rmax,
+               "max_err_learned": float((den - ref).abs().max()) / rmax,
+               "plain": DN.plain_ladder(seed, ref, DN.N_LOW, ladder=ladder)}
+        rows.append(row)
+    net.close()
+    mean = lambda k: float(np.mean([r[k] for r in rows]))
+    learned_ms = mean("t_low_ms") + mean("t_infer_ms")
+    plain = [{"histories": n, "ms": float(np.mean([r["plain"][j]["ms"] for r in rows])),
+              "gamma": float(np.mean([r["plain"][j]["gamma"] for r in rows])),
+              "all_ge_95": all(r["plain"][j]["gamma"] >= 0.95 for r in rows)} for j, n in enumerate(ladder)]
+    first_pass = next((p for p in plain if p["all_ge_95"]), None)
+    return {"cases": len(rows), "learned_ms": learned_ms, "gamma_learned": mean("gamma_learned"),
+            "learned_all_ge_95": all(r["gamma_learned"] >= 0.95 for r in rows),
+            "max_err_learned": mean("max_err_learned"), "gamma_low": mean("gamma_low"),
+            "max_err_low": mean("max_err_low"), "plain_1e7_ms": mean("t_high_ms"), "plain_ladder": plain,
+            "plain_ms_at_95": first_pass["ms"] if first_pass else None,
+            "plain_histories_at_95": first_pass["histories"] if first_pass else None,
+            "note": "device time (CUDA events) of transport + dose conversion (+ inference); gamma 2%/0.5mm, "
+                    "1% threshold, local, vs the 1e7-history plain dose; held-out seeds of the denoiser workload"}
+
+
+def denoiser_roofline(torch, S, peaks):
+    """Inference time of the denoiser on 128 x 128 x 192 and its tensor throughput."""
+    net = S.Denoiser(192, 128, 128, batch_max=1, seed=1)
+    low = torch.rand(192, 128, 128, device="cuda")
+    rho = torch.ones_like(low)
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        net.infer(low, rho)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(5):
+        net.infer(low, rho)
+    b.record(st)
+    st.synchronize()
+    S.denoise_status()
+    net.close()
+    ms = a.elapsed_time(b) / 5
+    flop = sum(2.0 * v * 27 * ci * co for v, ci, co in DENOISER_LAYERS)
+    peak = peaks.get("bf16_tflops")
+    tf = flop / (ms * 1e-3) / 1e12
+    return {"infer_ms": ms, "flop_per_inference": flop, "achieved_tflops": tf, "bound": "tensor",
+            "peak_tflops": peak, "frac": tf / peak if peak else None,
+            "peak_note": "measured bf16 burst peak (MEASURED_PEAKS.json)" if peak else "no measured peak"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,6 +324,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-histories", type=int, default=20_000)
+    ap.add_argument("--no-denoiser", action="store_true",
+                    help="skip the learned-vs-plain time-to-dose and the denoiser throughput")
     ap.add_argument("--plan", action="store_true",
                     help="also time the 2000-spot plan (1e8 protons): one persistent launch, "
                          "autotuned, graph-launched, and one launch per spot")
@@ -334,7 +418,7 @@ def main():
     peak_ops = SMS * LANE_OPS_PER_CLK_PER_SM * clk_mhz * 1e6
     achieved = steps_per_launch * ALGO_OPS_PER_STEP / (Tk * 1e-3)
     line = {
-        "metric": "proton histories/s on 1 GB300",
+        "metric": "proton histories/s on 1 GB300; time-to-dose at \u226595% gamma 2%/0.5mm, learned vs plain",
         "value": value,
         "unit": "histories/s",
         "n_gpus": ws,
@@ -364,6 +448,9 @@ def main():
     }
     if args.plan:
         line["batched_plan"] = plan_benchmark(torch, S, dev)
+    if rank == 0 and ws == 1 and not args.no_denoiser:
+        line["time_to_dose"] = time_to_dose(torch, S)
+        line["denoiser"] = denoiser_roofline(torch, S, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -294,6 +294,302 @@ __global__ void __launch_bounds__(128) k_conv3d(ConvArgs a) {
     if (warp == 0) umma::tmem_dealloc(tbase, ncols);
 }
 
+// ----------------------------------------------------------------------------
+// Brick convolution.  A work item computes Ty full output rows (all x) of one z plane
+// for Cp output channels.  Per 16-channel chunk of Cin the zero-padded input "brick" --
+// planes z-1..z+1, rows y0-1..y0+Ty, columns -1..W -- is staged in shared memory once,
+// as two 8-channel planes in which brick position f = (zb Yb + yb) P + xp (P = W + 2,
+// Yb = Ty + 2) holds 16 bytes.  In that layout 8 consecutive positions form a K-major
+// core matrix, so the A operand of tap (dz, dy, dx) for the M tile starting at brick
+// position f0 is the same buffer read from f0 + (dz Yb + dy) P + dx: the 27 taps are 27
+// descriptor offsets, not 27 copies.  M tiles of 128 rows cover the positions of the Ty
+// output rows including their two padding columns; the epilogue drops the rows that are
+// not output voxels.
+//
+// Persistent and warp-specialised: warps 0-3 stream (brick, weight) chunks into a ring of
+// shared-memory stages with cp.async (each stage's "full" barrier completes when the
+// copies land) and run the epilogue of the previous item while the tensor core works on
+// the current one; one thread of warp 4 issues the MMAs into one of two tensor-memory
+// accumulators and releases stages and accumulators through tcgen05.commit.  Every wait
+// is bounded; a timeout sets a shared abort flag that ends all roles' loops.
+// ----------------------------------------------------------------------------
+constexpr int kPipeStages = 2;
+constexpr int kPipeHeader = 1024;  // barriers, tensor-memory slot, abort flag
+
+__device__ __forceinline__ bool pipe_wait(uint64_t* m, uint32_t parity, volatile int* abort_flag) {
+    const long long t0 = clock64();
+    while (!umma::mbar_try_wait(m, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// AND of a predicate over the 128 worker threads (warps 0-3), named barrier 1.
+__device__ __forceinline__ bool workers_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, 1, 128, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Cin = a.Cin, Cp = b.Cp, W = a.W, H = a.H, D = a.D;
+    const int P = b.P, Yb = b.Yb;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);  // [kPipeStages]
+    uint64_t* empty = full + kPipeStages;                 // [kPipeStages]
+    uint64_t* tfull = empty + kPipeStages;                // [2]
+    uint64_t* tempty = tfull + 2;                         // [2]
+    uint64_t* wfull = tempty + 2;                         // resident weights landed
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem + 128);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 132);
+    const uint32_t s_stage0 = umma::smem_addr(smem) + kPipeHeader;
+    if (warp == 0) {
+        umma::tmem_alloc(slot, (uint32_t)b.tcols);
+        umma::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kPipeStages; ++s) {
+            umma::mbar_init(&full[s], 128);
+            umma::mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            umma::mbar_init(&tfull[s], 1);
+            umma::mbar_init(&tempty[s], 128);
+        }
+        umma::mbar_init(wfull, 128);
+        *abort_flag = 0;
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tbase = *slot;
+    const int nchunk = Cin >> 4;
+    const int npos = 3 * Yb * P;
+    const int fA = (Yb + 1) * P;  // brick position of output (y0, x = -1): row 0 of M tile 0
+    const int acc_cols = b.tiles * Cp;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            const uint32_t idesc = umma::idesc_bf16_f32(128, Cp);
+            int k = 0;
+            bool ok = !b.wres || pipe_wait(wfull, 0u, abort_flag);
+            const uint32_t s_wres = s_stage0 + (uint32_t)(kPipeStages * b.stage);
+            for (int item = blockIdx.x, j = 0; ok && item < b.items; item += gridDim.x, ++j) {
+                const int acc = j % b.nacc, v = j / b.nacc;
+                if (v >= 1 && !pipe_wait(&tempty[acc], (uint32_t)(v - 1) & 1u, abort_flag)) break;
+                umma::fence_after_sync();
+                const uint32_t dacc = tbase + (uint32_t)(acc * acc_cols);
+                for (int c = 0; c < nchunk; ++c, ++k) {
+                    const int s = k % kPipeStages, u = k / kPipeStages;
+                    if (!pipe_wait(&full[s], (uint32_t)u & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    umma::fence_after_sync();
+                    umma::fence_async_smem();  // cp.async (generic proxy) data -> tensor core
+                    const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
+                    // Only the start-address field (16-byte units, low bits) differs between
+                    // the descriptors of one stage, so they are the base descriptors plus a
+                    // position index (A) or a tap offset (B).  Shared addresses stay below
+                    // 256 KB, so the field never carries into the next one.
+                    const uint64_t a0 = umma::smem_desc(st + 128u, (uint32_t)b.plane, 128);
+                    uint64_t bd = umma::smem_desc(
+                        b.wres ? s_wres + (uint32_t)(c * 27 * Cp * 32) : st + (uint32_t)b.w_off, 128, 256);
+                    uint32_t accum = c > 0 ? 1u : 0u;
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                // fA + tap offset >= -1: the lowest start is one position before
+                                // the plane (a padding row whose result is dropped), inside the stage
+                                uint64_t ad = a0 + (uint64_t)(int64_t)(fA + (dz * Yb + dy) * P + dx);
+                                uint32_t dcol = dacc;
+                                for (int m = 0; m < b.tiles; ++m) {
+                                    umma::mma_bf16(dcol, ad, bd, idesc, accum);
+                                    ad += 128;  // next 128 positions
+                                    dcol += (uint32_t)Cp;
+                                }
+                                accum = 1u;
+                                bd += (uint64_t)(2 * Cp);  // next tap: Cp x 16 BF16 = 2 Cp units
+                            }
+                    umma::mma_commit(&empty[s]);
+                }
+                if (ok) umma::mma_commit(&tfull[acc]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // workers: loads of item j, then the epilogue of item j - 1.  With one accumulator
+        // the MMAs of item j wait for that epilogue, so it runs once the first
+        // kPipeStages chunks of item j (which need no MMA of item j) are issued.  Worker
+        // control flow is uniform: thread 0 polls each barrier and the outcome is shared
+        // through a named-barrier vote, so a timeout ends all four warps together.
+        int k = 0;
+        bool ok = true;
+        auto worker_wait = [&](uint64_t* m, uint32_t parity) {
+            bool done = true;
+            if (tid == 0) done = pipe_wait(m, parity, abort_flag);
+            return workers_all(done);
+        };
+        auto epilogue = [&](int pj, int pitem) {
+            const int acc = pj % b.nacc, v = pj / b.nacc;
+            if (!worker_wait(&tfull[acc], (uint32_t)v & 1u)) {
+                ok = false;
+                return;
+            }
+            umma::fence_after_sync();
+            int r = pitem;
+            const int z = r % D;
+            r /= D;
+            const int y0 = (r % b.nyb) * b.Ty;
+            r /= b.nyb;
+            const int part = r % b.nsplit;
+            const int n = r / b.nsplit;
+            const int cbase = part * Cp;
+            const uint32_t trow = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * acc_cols);
+            for (int m = 0; m < b.tiles; ++m) {
+                const int q = fA + 128 * m + 32 * warp + lane - Yb * P;  // position in plane zb = 1
+                const int yb = q / P, xp = q - (q / P) * P;
+                const int yy = y0 + yb - 1, xx = xp - 1;
+                const bool valid = yb >= 1 && yb <= b.Ty && xp >= 1 && xp <= W && yy < H;
+                const size_t vox = (size_t)n * a.nvox + ((size_t)z * H + (valid ? yy : 0)) * W + (valid ? xx : 0);
+                for (int c = 0; c < Cp; c += 8) {
+                    float rr[8];
+                    __syncwarp();
+                    umma::tmem_ld8(trow + (uint32_t)(m * Cp + c), rr);
+                    if (valid) {
+                        for (int e = 0; e < 8; ++e) {
+                            if (a.bias) rr[e] += a.bias[cbase + c + e];
+                            if (a.relu) rr[e] = rr[e] > 0.f ? rr[e] : a.slope * rr[e];
+                        }
+                        if (a.y_fp32) {
+                            float* yo = static_cast<float*>(a.y) + vox * a.y_cstride + a.y_coffset + cbase + c;
+                            reinterpret_cast<float4*>(yo)[0] = make_float4(rr[0], rr[1], rr[2], rr[3]);
+                            reinterpret_cast<float4*>(yo)[1] = make_float4(rr[4], rr[5], rr[6], rr[7]);
+                        } else {
+                            __nv_bfloat162 pk[4];
+                            for (int e = 0; e < 4; ++e) pk[e] = __floats2bfloat162_rn(rr[2 * e], rr[2 * e + 1]);
+                            __nv_bfloat16* yo =
+                                static_cast<__nv_bfloat16*>(a.y) + vox * a.y_cstride + a.y_coffset + cbase + c;
+                            *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<uint4*>(pk);
+                        }
+                    }
+                }
+            }
+            umma::fence_before_sync();
+            umma::mbar_arrive(&tempty[acc]);
+        };
+        if (b.wres) {  // all chunks' weights, once: [chunk][tap][Cp x 16 K-major]
+            const uint32_t s_wres = s_stage0 + (uint32_t)(kPipeStages * b.stage);
+            for (int c = 0; c < nchunk; ++c) {
+                int tap = 0, q = tid;
+                while (q >= 2 * Cp) {
+                    q -= 2 * Cp;
+                    ++tap;
+                }
+                for (; tap < 27;) {
+                    const int co = q >> 1, g = q & 1;
+                    umma::cp_async16(s_wres + (uint32_t)((c * 27 + tap) * Cp * 32) + umma::core_offset(co, g * 8, 16),
+                                     a.w + ((size_t)co * 27 + tap) * Cin + c * 16 + g * 8, 16u);
+                    q += 128;
+                    while (q >= 2 * Cp) {
+                        q -= 2 * Cp;
+                        ++tap;
+                    }
+                }
+            }
+            umma::cp_async_mbar_arrive(wfull);
+        }
+        for (int item = blockIdx.x, j = 0;; item += gridDim.x, ++j) {
+            bool epi_done = j == 0;
+            if (item < b.items) {
+                int r = item;
+                const int z = r % D;
+                r /= D;
+                const int y0 = (r % b.nyb) * b.Ty;
+                r /= b.nyb;
+                const int part = r % b.nsplit;
+                const int n = r / b.nsplit;
+                const __nv_bfloat16* xin = a.x + (size_t)n * a.nvox * Cin;
+                const __nv_bfloat16* win = a.w + (size_t)part * Cp * 27 * Cin;
+                for (int c = 0; c < nchunk && ok; ++c, ++k) {
+                    if (b.nacc == 1 && c == kPipeStages && !epi_done) {
+                        epilogue(j - 1, item - (int)gridDim.x);
+                        epi_done = true;
+                        if (!ok) break;
+                    }
+                    const int s = k % kPipeStages, u = k / kPipeStages;
+                    if (u >= 1 && !worker_wait(&empty[s], (uint32_t)(u - 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
+                    {  // brick: lane pairs copy both 8-channel halves (one 32-byte sector) of a position
+                        const int g = tid & 1;
+                        int f = tid >> 1;
+                        int row = f / P, xp = f - row * P;
+                        int zb = row / Yb, yb = row - zb * Yb;
+                        const uint32_t dst = st + 128u + (uint32_t)(g * b.plane);
+                        const __nv_bfloat16* src_c = xin + c * 16 + g * 8;
+                        while (f < npos) {
+                            const int zz = z + zb - 1, yy = y0 + yb - 1, xx = xp - 1;
+                            const bool in =
+                                (unsigned)zz < (unsigned)D && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
+                            const __nv_bfloat16* src = in ? src_c + ((size_t)(zz * H + yy) * W + xx) * Cin : src_c;
+                            umma::cp_async16(dst + (uint32_t)f * 16u, src, in ? 16u : 0u);
+                            f += 64;
+                            xp += 64;
+                            while (xp >= P) {
+                                xp -= P;
+                                if (++yb == Yb) {
+                                    yb = 0;
+                                    ++zb;
+                                }
+                            }
+                        }
+                    }
+                    if (!b.wres) {  // weights of this chunk and part: per tap a Cp x 16 K-major tile
+                        const uint32_t s_w = st + (uint32_t)b.w_off;
+                        int tap = 0, q = tid;
+                        while (q >= 2 * Cp) {
+                            q -= 2 * Cp;
+                            ++tap;
+                        }
+                        for (; tap < 27;) {
+                            const int co = q >> 1, g = q & 1;
+                            umma::cp_async16(s_w + (uint32_t)(tap * Cp * 32) + umma::core_offset(co, g * 8, 16),
+                                             win + ((size_t)co * 27 + tap) * Cin + c * 16 + g * 8, 16u);
+                            q += 128;
+                            while (q >= 2 * Cp) {
+                                q -= 2 * Cp;
+                                ++tap;
+                            }
+                        }
+                    }
+                    umma::cp_async_mbar_arrive(&full[s]);
+                }
+            }
+            if (!epi_done && ok) epilogue(j - 1, item - (int)gridDim.x);
+            if (item >= b.items || !ok) break;
+        }
+        umma::cp_async_wait_all();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (tid == 0 && *abort_flag) atomicOr(a.status, 1u);
+    if (warp == 0) umma::tmem_dealloc(tbase, (uint32_t)b.tcols);
+}
+
 __global__ void __launch_bounds__(128) k_conv3d_wgrad(WgradArgs a) {
     constexpr int KV = 64;  // voxels per stage
     extern __shared__ __align__(128) unsigned char smem[];
@@ -424,7 +720,69 @@ cudaError_t flip_weights_launch(const __nv_bfloat16* w, __nv_bfloat16* wd, int C
     return cudaGetLastError();
 }
 
+// Work decomposition of the pipelined brick kernel for one layer shape: output channels
+// split into parts of Cp, weights resident or streamed, and rows per item Ty, chosen by a
+// cost model measured on GB300: an MMA (M = 128, K = 16) whose A operand is not the
+// previous one's costs ~100 cycles up to N = 192 and N / 2 beyond; staging moves ~11 bytes
+// per cycle per SM; with one accumulator the epilogue (~20 cycles per 8 columns of a
+// tile) does not overlap the MMAs.
+static bool brick_plan(const ConvArgs& a, int batch, BrickPlan* out, size_t* smem_out) {
+    const int P = a.W + 2;
+    const size_t smem_cap = 227 * 1024;
+    double best = 1e300;
+    bool found = false;
+    const int nchunk = a.Cin / 16;
+    for (int nsplit = 1; nsplit <= a.Cout / 16; ++nsplit) {
+        if (a.Cout % nsplit || (a.Cout / nsplit) % 16) continue;
+        const int Cp = a.Cout / nsplit;
+        if (Cp > 256) continue;
+        const size_t w_bytes = (size_t)27 * Cp * 32;
+        for (int wres = 0; wres <= (nsplit == 1 ? 1 : 0); ++wres)
+            for (int Ty = 1; Ty <= a.H; ++Ty) {
+                const int tiles = (Ty * P + 127) / 128;
+                if (tiles * Cp > 512) break;
+                const int nacc = 2 * tiles * Cp <= 512 ? 2 : 1;
+                const size_t npos = (size_t)3 * (Ty + 2) * P;
+                const size_t plane = (npos * 16 + 127) / 128 * 128;
+                // M tiles read up to 128 positions past the end of the second plane
+                const size_t w_off = (128 + 2 * plane + 2048 + 127) / 128 * 128;
+                const size_t stage = wres ? w_off : (w_off + w_bytes + 127) / 128 * 128;
+                const size_t smem = kPipeHeader + kPipeStages * stage + (wres ? nchunk * w_bytes : 0);
+                if (smem > smem_cap || plane >= (1u << 18)) break;
+                const double mma = (double)nchunk * 27 * tiles * (Cp > 192 ? Cp / 2.0 : 100.0);
+                const double load = (double)nchunk * (stage - 2176) / 11.0;
+                const double epi = tiles * (Cp / 8.0) * 20.0;
+                const double item = (mma > load ? mma : load) + (nacc == 1 ? epi : 0.0);
+                const double cost = item / ((double)Ty * a.W) * nsplit;  // per output voxel, all parts
+                if (cost < best) {
+                    best = cost;
+                    found = true;
+                    int tcols = 32;
+                    while (tcols < nacc * tiles * Cp) tcols <<= 1;
+                    const int nyb = (a.H + Ty - 1) / Ty;
+                    *out = BrickPlan{Ty,         tiles,      nyb,  P,     Ty + 2, Cp,   nsplit, (int)plane,
+                                     (int)w_off, wres,       (int)stage, nacc, tcols, batch * nsplit * nyb * a.D};
+                    *smem_out = smem;
+                }
+            }
+    }
+    return found;
+}
+
 cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st) {
+    BrickPlan bp{};
+    size_t bsmem = 0;
+    if (brick_plan(a, batch, &bp, &bsmem)) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3d_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const int ctas = bp.items < sms ? bp.items : sms;
+        k_conv3d_brick<<<ctas, 160, bsmem, st>>>(a, bp);
+        return cudaGetLastError();
+    }
     const size_t smem = 2 * ((size_t)128 * a.Cin * 2 + (size_t)a.Cout * a.Cin * 2) + 64;
     cudaError_t e = cudaFuncSetAttribute(k_conv3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

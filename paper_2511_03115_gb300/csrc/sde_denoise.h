@@ -19,6 +19,25 @@ struct ConvArgs {
     unsigned int* status;
 };
 
+// Work decomposition and shared-memory layout of the pipelined brick convolution
+// (host-chosen per layer shape).  A work item is (sample, Cout part, row block, z plane).
+struct BrickPlan {
+    int Ty;      // output rows (y) per work item, all x of one z plane
+    int tiles;   // M tiles of 128 brick positions per work item
+    int nyb;     // ceil(H / Ty)
+    int P;       // W + 2: brick row pitch in positions
+    int Yb;      // Ty + 2: brick rows per plane
+    int Cp;      // output channels per work item
+    int nsplit;  // Cout / Cp
+    int plane;   // bytes between the two 8-channel planes of a 16-channel chunk
+    int w_off;   // offset of the chunk's weights (27 taps x Cp x 16) within a stage (wres = 0)
+    int wres;    // 1: all chunks' weights stay resident after the stages (loaded once per CTA)
+    int stage;   // bytes per pipeline stage (brick chunk + weight chunk)
+    int nacc;    // tensor-memory accumulators (2: epilogue overlaps the next item)
+    int tcols;   // tensor-memory columns allocated (power of two >= nacc x tiles x Cp)
+    int items;   // batch x nsplit x nyb x D
+};
+
 // Weight gradient: dw[co][tap][ci] += sum_v dy[v][co] x[v + off(tap)][ci].  One CTA per
 // (tap, voxel chunk); the GEMM has rows = co (padded to 128), columns = ci, K = voxels,
 // with both operands M/N-major (channels contiguous, as stored).

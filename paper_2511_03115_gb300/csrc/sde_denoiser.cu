@@ -556,9 +556,10 @@ extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int 
         if (!rc) rc = dalloc(d, &l.wflip, l.nw);
         if (rc) break;
         // He initialisation; the input layer sees two live channels; the output layer
-        // starts small so that the network begins near the identity on the dose.
+        // starts at zero, so that the untrained network is the identity on the dose
+        // (its output is a correction added to the input dose).
         const int fan_in = 27 * (i == 0 ? 2 : l.Cin);
-        const double sd = (i == 10 ? 0.01 : 1.0) * sqrt(2.0 / fan_in);
+        const double sd = (i == 10 ? 0.0 : 1.0) * sqrt(2.0 / fan_in);
         std::vector<float> w(l.nw);
         for (size_t k = 0; k < l.nw; ++k) w[k] = (float)(sd * rng.normal());
         rc = fail(cudaMemcpy(l.w32, w.data(), l.nw * sizeof(float), cudaMemcpyHostToDevice), "weights upload");

@@ -96,6 +96,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, long lon
     return true;
 }
 
+// Plain arrive (count 1) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(m)) : "memory");
+}
+
+// Arrive on the mbarrier once all cp.async copies issued so far by this thread have
+// landed (the arrival is not pre-counted: the barrier's count includes it).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* m) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(m)) : "memory");
+}
+
 // Eight consecutive FP32 columns of this thread's tensor-memory lane.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     uint32_t r0, r1, r2, r3, r4, r5, r6, r7;

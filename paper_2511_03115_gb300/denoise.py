@@ -69,7 +69,7 @@ def generate(seeds, n_low=None, n_high=None):
     return pairs
 
 
-def train(net, pairs, epochs=2, lr=1e-3, lr_end=1e-5, warmup=50, seed=0, log_every=0, scale=None):
+def train(net, pairs, epochs=2, lr=1e-4, lr_end=1e-6, warmup=50, seed=0, log_every=0, scale=None):
     """Adam with linear warm-up and a cosine learning-rate decay; one pair per step."""
     scale = scale or N_LOW / N_HIGH
     order_rng = np.random.default_rng(seed)
@@ -169,10 +169,12 @@ def main():
     ap.add_argument("--train", type=int, default=64, help="training pairs (seeds 0..n-1)")
     ap.add_argument("--epochs", type=int, default=2)
     ap.add_argument("--eval", type=int, default=8, help="held-out pairs (seeds 100000..)")
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=1e-4)
     ap.add_argument("--out", default=None, help="write the report as JSON here")
     ap.add_argument("--n-low", type=int, default=N_LOW, help="histories of the input dose")
     ap.add_argument("--n-high", type=int, default=N_HIGH, help="histories of the target dose")
+    ap.add_argument("--save", default=None, help="write the trained FP32 parameters here (.npy)")
+    ap.add_argument("--load", default=None, help="start from these parameters (.npy) instead of training from scratch")
     args = ap.parse_args()
     torch = _torch()
     torch.cuda.init()
@@ -180,6 +182,8 @@ def main():
     pairs = generate(range(args.train), args.n_low, args.n_high)
     t_gen = time.time() - t0
     net = S.Denoiser(SHAPE[2], SHAPE[1], SHAPE[0], batch_max=1, seed=1)
+    if args.load:
+        net.set_params(np.load(args.load).astype(np.float32))
     t0 = time.time()
     losses = train(net, pairs, epochs=args.epochs, lr=args.lr, log_every=max(1, args.train // 4),
                    scale=args.n_low / args.n_high)
@@ -187,6 +191,8 @@ def main():
     S.denoise_status()
     t_train = time.time() - t0
     del pairs
+    if args.save:
+        np.save(args.save, net.get_params())
     agg, rows = evaluate(net, range(100_000, 100_000 + args.eval), n_low=args.n_low, n_high=args.n_high)
     report = {"train_pairs": args.train, "epochs": args.epochs, "n_low": args.n_low, "n_high": args.n_high, "generate_s": t_gen, "train_s": t_train,
               "train_step_ms": 1e3 * t_train / max(1, args.train * args.epochs), "losses": losses,

@@ -226,14 +226,17 @@ def plan2000(total: int = 100_000_000, seed: int = 0) -> Workload:
                     spots, seed=seed)
 
 
-def denoise_case(seed: int, n_hist: int = 100_000, shape=(128, 128, 192), n_spots: int = 24) -> Workload:
+def denoise_case(seed: int, n_hist: int = 100_000, shape=(128, 128, 192), n_spots: int = 24,
+                 sigma_xy_mm: float = 3.0) -> Workload:
     """One sample of the denoiser workload: 128 x 128 x 192 mm at 1 mm, water with 30
     random spheres (radius 5-15 mm, density 0.2-1.9, tissue or bone) and a plan of
-    ``n_spots`` spots on a 5 mm lateral grid within +-30 mm, energies U(70, 200) MeV
-    (ranges beyond the phantom exit), weights lognormal(0, 0.7), ``n_hist`` protons."""
+    ``n_spots`` Gaussian spots (sigma ``sigma_xy_mm``, as the slab and insert beams) on
+    a 5 mm lateral grid within +-30 mm, energies U(70, 200) MeV (ranges beyond the
+    phantom exit), weights lognormal(0, 0.7), ``n_hist`` protons."""
     nx, ny, nz = shape
     origin, dens, mid = sphere_phantom(shape, 1.0, seed, r_range=(5.0, 15.0))
     spots = plan_spots(n_spots, n_hist, seed, pitch=5.0, half_width=30.0)
+    spots["sigma_xy_mm"] = sigma_xy_mm
     return Workload(f"denoise{seed}", shape, (1.0, 1.0, 1.0), origin, dens, mid, [WATER, TISSUE, BONE], spots,
                     seed=seed)
 

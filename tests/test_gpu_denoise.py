@@ -28,7 +28,8 @@ def _torch_conv_ref(x, w, bias=None):
 
 
 @pytest.mark.parametrize("Cin,Cout,shape", [(16, 32, (4, 8, 8)), (32, 64, (3, 8, 16)), (96, 32, (2, 8, 8)),
-                                            (192, 64, (2, 4, 16)), (64, 128, (4, 4, 8))])
+                                            (192, 64, (2, 4, 16)), (64, 128, (4, 4, 8)),
+                                            (32, 32, (3, 5, 128)), (32, 96, (2, 9, 64)), (32, 16, (4, 7, 32))])
 def test_conv3d_forward_dgrad_wgrad_match_torch(sde_gpu, Cin, Cout, shape):
     import torch
     g = torch.Generator().manual_seed(Cin * 1000 + Cout)
@@ -116,11 +117,11 @@ def test_denoiser_gradients_match_a_float64_reference(sde_gpu):
     S = sde_gpu
     shape = (16, 16, 32)
     net = S.Denoiser(*shape, batch_max=1, seed=3)
-    # a trained-looking output layer (the library starts it near zero)
+    # a trained-looking output layer (the library starts it at zero)
     p = net.get_params()
     layers = net.split(p)
     w10, b10 = layers[10]
-    w10 *= 20.0
+    w10[:] = np.random.default_rng(5).normal(0.0, 0.2 * (2.0 / (27 * 32)) ** 0.5, w10.shape)
     net.set_params(p)
     low, rho, high = _smooth_case(shape, 1)
     g, loss = net.gradients(low.float().cuda(), rho.float().cuda(), high.float().cuda())
@@ -148,6 +149,11 @@ def test_denoiser_inference_matches_the_reference_and_training_reduces_the_loss(
     net = S.Denoiser(*shape, batch_max=1, seed=5)
     low, rho, high = _smooth_case(shape, 2)
     lo, rh, hi = low.float().cuda(), rho.float().cuda(), high.float().cuda()
+    assert torch.equal(net.infer(lo, rh), lo)  # the untrained network is the identity
+    p = net.get_params()
+    w10, _ = net.split(p)[10]
+    w10[:] = np.random.default_rng(6).normal(0.0, 0.2 * (2.0 / (27 * 32)) ** 0.5, w10.shape)
+    net.set_params(p)
     out = net.infer(lo, rh)
     S.denoise_status()
     layers = [(torch.tensor(w, dtype=torch.float64), torch.tensor(b, dtype=torch.float64))
@@ -178,15 +184,15 @@ def test_gpu_gamma_equals_the_oracle_gamma(sde_gpu, oracle_lib):
 def test_trained_denoiser_gains_over_the_low_history_dose(sde_gpu):
     """Trained on SDE-generated pairs (1e5-history input, 1e7-history target) of the
     128x128x192 denoiser workload, the network must bring held-out low-history doses
-    closer to the high-history dose than the low-history dose itself: smaller maximum
-    error and a gamma pass rate at least as high."""
+    closer to the high-history dose than the low-history dose itself: a higher gamma
+    pass rate (2 %/0.5 mm) and a smaller maximum error."""
     from paper_2511_03115_gb300 import denoise as DN
-    pairs = DN.generate(range(24))
+    pairs = DN.generate(range(32))
     net = sde_gpu.Denoiser(DN.SHAPE[2], DN.SHAPE[1], DN.SHAPE[0], seed=1)
-    DN.train(net, pairs, epochs=3, lr=1e-3, warmup=20)
+    DN.train(net, pairs, epochs=10, lr=1e-4, warmup=50)
     del pairs
     agg, rows = DN.evaluate(net, range(200_000, 200_004), ladder=False)
     print(agg)
-    assert agg["gamma_denoised"] > agg["gamma_low"]
-    assert agg["max_err_denoised"] < 1.5 * agg["max_err_low"]
+    assert agg["gamma_denoised"] > agg["gamma_low"] + 0.02
+    assert agg["max_err_denoised"] < agg["max_err_low"]
     net.close()
