@@ -131,11 +131,11 @@ def cpu_baseline(target_s: float = 12.0):
     oracle.build()
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
-    cal = 4000
+    cal = 20_000
     t0 = time.perf_counter()
     oracle.run_workload(slab150(cal), seed=12345)
     dt = time.perf_counter() - t0
-    n = int(min(2_000_000, max(cal, cal * target_s / max(dt, 1e-3))))
+    n = int(min(5_000_000, max(cal, cal * target_s / max(dt, 1e-3))))
     t0 = time.perf_counter()
     _, _, bal = oracle.run_workload(slab150(n), seed=777)
     dt = time.perf_counter() - t0

@@ -279,9 +279,11 @@ int sde_denoise_status(void* stream);
  * fastest, device FP32): the low-history dose (Gy) and the density (g/cm^3);
  * the output is the dose (Gy).  Internally the dose is scaled by 1/max of the
  * low-history dose of each sample and the network predicts a correction that
- * is added to it.  D, H, W must be multiples of 4 and (D/4)(H/4)(W/4) a
- * multiple of 128.  The handle owns its device memory (weights, optimiser
- * state, activations and gradients for batch_max samples). */
+ * is added to it; the output layer starts at zero, so an untrained network
+ * returns its input.  D, H, W must be multiples of 4, (D/4)(H/4)(W/4) a
+ * multiple of 128 and D H W batch_max below 2^31 / 24 (SDE_EINVAL otherwise).
+ * The handle owns its device memory (weights, optimiser state, activations and
+ * gradients for batch_max samples). */
 typedef struct sde_denoiser sde_denoiser;
 int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int batch_max, uint64_t seed);
 void sde_denoiser_destroy(sde_denoiser* d);

@@ -69,91 +69,115 @@ __global__ void k_prepare_input(const float* __restrict__ dose, const float* __r
     }
 }
 
-// Fine grid (D, H, W) even in each dimension; coarse = half.
+// Fine grid (D, H, W) even in each dimension; coarse = half.  The resampling kernels move
+// eight channels (16 bytes) per thread with 32-bit index arithmetic; every channel count,
+// stride and offset is a multiple of 8 and every index range is below 2^31 (checked at
+// creation).
 struct Grid2 {
     int D, H, W;
-    __device__ __forceinline__ size_t coarse_of(size_t fine_v) const {
-        int x = (int)(fine_v % W), y = (int)((fine_v / W) % H), z = (int)(fine_v / ((size_t)W * H));
-        return ((size_t)(z >> 1) * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1);
+    __device__ __forceinline__ int coarse_of(int v) const {
+        const int x = v % W, y = (v / W) % H, z = v / (W * H);
+        return ((z >> 1) * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1);
+    }
+    __device__ __forceinline__ int child(int vc, int d) const {  // d-th of the 8 fine children
+        const int Wc = W >> 1, Hc = H >> 1;
+        const int xc = vc % Wc, yc = (vc / Wc) % Hc, zc = vc / (Wc * Hc);
+        return ((2 * zc + (d >> 2)) * H + 2 * yc + ((d >> 1) & 1)) * W + 2 * xc + (d & 1);
     }
 };
+
+__device__ __forceinline__ void ld8(const bf16* p, float (&f)[8]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ void st8(bf16* p, const float (&f)[8]) {
+    __nv_bfloat162 h[4];
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(h);
+}
+
+#define SDE_GRID_LOOP(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
 // out[b][vc][c] = mean of the 8 children of vc in in[b][v][ico + c] (row stride ics)
 __global__ void k_avgpool2(const bf16* __restrict__ in, int ics, int ico, int C, Grid2 g, int batch,
                            bf16* __restrict__ out) {
-    const int Dc = g.D >> 1, Hc = g.H >> 1, Wc = g.W >> 1;
-    const size_t Vc = (size_t)Dc * Hc * Wc, Vf = (size_t)g.D * g.H * g.W;
-    const size_t n = Vc * batch * C;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t vc = (i / C) % Vc;
-        const int b = (int)(i / ((size_t)C * Vc));
-        const int xc = (int)(vc % Wc), yc = (int)((vc / Wc) % Hc), zc = (int)(vc / ((size_t)Wc * Hc));
-        float acc = 0.f;
+    const int G = C >> 3, Vf = g.D * g.H * g.W, Vc = Vf >> 3;
+    SDE_GRID_LOOP(i, Vc * batch * G) {
+        const int q = i % G, r = i / G, vc = r % Vc, b = r / Vc;
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int d = 0; d < 8; ++d) {
-            const size_t vf = ((size_t)(2 * zc + (d >> 2)) * g.H + 2 * yc + ((d >> 1) & 1)) * g.W + 2 * xc + (d & 1);
-            acc += __bfloat162float(in[((size_t)b * Vf + vf) * ics + ico + c]);
+            float f[8];
+            ld8(in + ((size_t)b * Vf + g.child(vc, d)) * ics + ico + 8 * q, f);
+            for (int e = 0; e < 8; ++e) acc[e] += f[e];
         }
-        out[i] = __float2bfloat16(0.125f * acc);
+        for (int e = 0; e < 8; ++e) acc[e] *= 0.125f;
+        st8(out + ((size_t)b * Vc + vc) * C + 8 * q, acc);
     }
 }
 
 // din[b][v][c] = dout[b][parent(v)][c] / 8 + add[b][v][aco + c]   (add may be NULL)
 __global__ void k_avgpool2_bwd(const bf16* __restrict__ dout, const bf16* __restrict__ add, int acs, int aco, int C,
                                Grid2 g, int batch, bf16* __restrict__ din) {
-    const size_t Vf = (size_t)g.D * g.H * g.W, Vc = Vf / 8;
-    const size_t n = Vf * batch * C;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t v = (i / C) % Vf;
-        const int b = (int)(i / ((size_t)C * Vf));
-        float r = 0.125f * __bfloat162float(dout[((size_t)b * Vc + g.coarse_of(v)) * C + c]);
-        if (add) r += __bfloat162float(add[((size_t)b * Vf + v) * acs + aco + c]);
-        din[i] = __float2bfloat16(r);
+    const int G = C >> 3, Vf = g.D * g.H * g.W, Vc = Vf >> 3;
+    SDE_GRID_LOOP(i, Vf * batch * G) {
+        const int q = i % G, r = i / G, v = r % Vf, b = r / Vf;
+        float f[8];
+        ld8(dout + ((size_t)b * Vc + g.coarse_of(v)) * C + 8 * q, f);
+        for (int e = 0; e < 8; ++e) f[e] *= 0.125f;
+        if (add) {
+            float a[8];
+            ld8(add + ((size_t)b * Vf + v) * acs + aco + 8 * q, a);
+            for (int e = 0; e < 8; ++e) f[e] += a[e];
+        }
+        st8(din + ((size_t)b * Vf + v) * C + 8 * q, f);
     }
 }
 
 // out[b][v][oco + c] = in[b][parent(v)][c]   (nearest-neighbour upsampling)
 __global__ void k_upsample2(const bf16* __restrict__ in, int C, Grid2 g, int batch, bf16* __restrict__ out, int ocs,
                             int oco) {
-    const size_t Vf = (size_t)g.D * g.H * g.W, Vc = Vf / 8;
-    const size_t n = Vf * batch * C;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t v = (i / C) % Vf;
-        const int b = (int)(i / ((size_t)C * Vf));
-        out[((size_t)b * Vf + v) * ocs + oco + c] = in[((size_t)b * Vc + g.coarse_of(v)) * C + c];
+    const int G = C >> 3, Vf = g.D * g.H * g.W, Vc = Vf >> 3;
+    SDE_GRID_LOOP(i, Vf * batch * G) {
+        const int q = i % G, r = i / G, v = r % Vf, b = r / Vf;
+        *reinterpret_cast<uint4*>(out + ((size_t)b * Vf + v) * ocs + oco + 8 * q) =
+            *reinterpret_cast<const uint4*>(in + ((size_t)b * Vc + g.coarse_of(v)) * C + 8 * q);
     }
 }
 
 // dout[b][vc][c] = sum over the 8 children of din[b][v][ico + c]
 __global__ void k_upsample2_bwd(const bf16* __restrict__ din, int ics, int ico, int C, Grid2 g, int batch,
                                 bf16* __restrict__ dout) {
-    const int Hc = g.H >> 1, Wc = g.W >> 1;
-    const size_t Vf = (size_t)g.D * g.H * g.W, Vc = Vf / 8;
-    const size_t n = Vc * batch * C;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t vc = (i / C) % Vc;
-        const int b = (int)(i / ((size_t)C * Vc));
-        const int xc = (int)(vc % Wc), yc = (int)((vc / Wc) % Hc), zc = (int)(vc / ((size_t)Wc * Hc));
-        float acc = 0.f;
+    const int G = C >> 3, Vf = g.D * g.H * g.W, Vc = Vf >> 3;
+    SDE_GRID_LOOP(i, Vc * batch * G) {
+        const int q = i % G, r = i / G, vc = r % Vc, b = r / Vc;
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int d = 0; d < 8; ++d) {
-            const size_t vf = ((size_t)(2 * zc + (d >> 2)) * g.H + 2 * yc + ((d >> 1) & 1)) * g.W + 2 * xc + (d & 1);
-            acc += __bfloat162float(din[((size_t)b * Vf + vf) * ics + ico + c]);
+            float f[8];
+            ld8(din + ((size_t)b * Vf + g.child(vc, d)) * ics + ico + 8 * q, f);
+            for (int e = 0; e < 8; ++e) acc[e] += f[e];
         }
-        dout[i] = __float2bfloat16(acc);
+        st8(dout + ((size_t)b * Vc + vc) * C + 8 * q, acc);
     }
 }
 
-// Leaky ReLU backward: dy[i][c] *= (y[i][yco + c] > 0 ? 1 : slope)  (y has the sign of x)
-__global__ void k_relu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y, int ycs, int yco, int C, size_t N,
+// Leaky ReLU backward: dy[r][c] *= (y[r][yco + c] > 0 ? 1 : slope)  (y has the sign of x)
+__global__ void k_relu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y, int ycs, int yco, int C, int N,
                            float slope) {
-    const size_t n = N * C;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = i / C;
-        const int c = (int)(i % C);
-        if (!(__bfloat162float(y[r * ycs + yco + c]) > 0.f)) dy[i] = __float2bfloat16(slope * __bfloat162float(dy[i]));
+    const int G = C >> 3;
+    SDE_GRID_LOOP(i, N * G) {
+        const int q = i % G, r = i / G;
+        float f[8], t[8];
+        ld8(dy + (size_t)r * C + 8 * q, f);
+        ld8(y + (size_t)r * ycs + yco + 8 * q, t);
+        for (int e = 0; e < 8; ++e)
+            if (!(t[e] > 0.f)) f[e] *= slope;
+        st8(dy + (size_t)r * C + 8 * q, f);
     }
 }
 
@@ -426,7 +450,7 @@ int wgrad(sde_denoiser* d, const bf16* x, const bf16* dy, const Layer& l, int ba
 }
 
 int relu_bwd(sde_denoiser* d, bf16* dy, const bf16* y, int ycs, int yco, int C, size_t N) {
-    k_relu_bwd<<<kBlocks, 256, 0, d->st>>>(dy, y, ycs, yco, C, N, kLeak);
+    k_relu_bwd<<<kBlocks, 256, 0, d->st>>>(dy, y, ycs, yco, C, (int)N, kLeak);
     return fail(cudaGetLastError(), "relu bwd launch");
 }
 
@@ -518,8 +542,9 @@ int refresh_flips(sde_denoiser* d) {
 
 extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int batch_max, uint64_t seed) {
     if (!out || D < 4 || H < 4 || W < 4 || (D % 4) || (H % 4) || (W % 4) || batch_max < 1 ||
-        ((long long)(D / 4) * (H / 4) * (W / 4)) % 128 || (long long)D * H * W * batch_max > (1ll << 30)) {
-        set_last_error("sde_denoiser_create: D, H, W must be multiples of 4 with (D/4)(H/4)(W/4) a multiple of 128");
+        ((long long)(D / 4) * (H / 4) * (W / 4)) % 128 || (long long)D * H * W * batch_max * 24 >= (1ll << 31)) {
+        set_last_error("sde_denoiser_create: D, H, W must be multiples of 4 with (D/4)(H/4)(W/4) a multiple of 128 "
+                       "and D H W batch_max below 2^31 / 24");
         return SDE_EINVAL;
     }
     sde_denoiser* d = new (std::nothrow) sde_denoiser();
