@@ -8,9 +8,10 @@ lateral sigma 3 mm, 10^6 protons, 60 x 60 x 200 mm at 0.5 mm voxels (water / bon
 lung-like / water).  Its inputs (29 MB phantom + 46 MB tally) fit in L2, so L2 is flushed
 (256 MB write) before every timed step, outside the timed events.
 
-Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank transports its own
-10^6 histories with its own seeds (weak scaling, no collective on the data path) and the
-step time is the maximum over ranks.
+Prints one JSON line (rank 0).  Under torchrun (N > 1) the ranks split one plan of N x 10^6
+histories by global history id (each rank its own 10^6, weak scaling, no collective in
+the timed steps) and the step time is the maximum over ranks; after timing, one exact
+integer all-reduce of the tallies gives the combined dose, and its time is reported.
 
 ``--impl reference`` times the FP64 CPU oracle instead (on the host cores, rank 0 only).
 """
@@ -343,16 +344,17 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = slab150(args.histories)
+    wl = slab150(args.histories * ws)  # one plan; this rank runs its shard of the history ids
+    first, count = S.history_shard(wl.n_histories, rank, ws)
     stream = torch.cuda.Stream(device=dev)
     d = S.SdeDose(wl, stream=stream)
     spots_dev = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    seed_base = 1_000_003 * (rank + 1)
+    seed_base = 1_000_003
 
     def step(k):
         d.reset()
-        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + k)
+        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + k, first=first, count=count)
 
     for w in range(args.warmup):
         step(10_000 + w)
@@ -374,7 +376,7 @@ def main():
         s.record(stream)
         d.reset()
         m.record(stream)
-        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + k)
+        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + k, first=first, count=count)
         e.record(stream)
         evs.append((s, m, e))
     stream.synchronize()
@@ -391,7 +393,7 @@ def main():
         t = torch.tensor([T, Tk], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         T, Tk = float(t[0]), float(t[1])
-    hist_per_step = wl.n_histories * ws
+    hist_per_step = wl.n_histories  # all ranks' shards
     value = hist_per_step / (T * 1e-3)
     steps_per_launch = bal["steps"]
 
@@ -402,7 +404,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d.reset()
-        d.run(wl.spots, seed=seed_base + 50_000 + k)
+        d.run(wl.spots, seed=seed_base + 50_000 + k, first=first, count=count)
         d.fetch_into(dose_ptr=host_dose.data_ptr())
         t1 = time.perf_counter()
         if k > 0:
@@ -412,6 +414,26 @@ def main():
         t = torch.tensor([e2e_T], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_T = float(t[0])
+
+    combine = None
+    if ws > 1:  # the one exchange step of the split: an exact integer sum of the tallies
+        d.reset()
+        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + 90_000, first=first, count=count)
+        tally = torch.empty(wl.n_voxels, dtype=torch.int64, device=dev)
+        rb = d.fetch_device(edep_ptr=tally.data_ptr(), balance=True)
+        bt = torch.tensor([rb[k] for k in ("incident", "deposited", "escaped", "removed", "histories")],
+                          dtype=torch.int64, device=dev)
+        torch.cuda.synchronize()
+        dist.barrier()
+        c0 = time.perf_counter()
+        dist.all_reduce(tally, op=dist.ReduceOp.SUM)
+        torch.cuda.synchronize()
+        c1 = time.perf_counter()
+        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
+        inc, dep, esc, rem, nh = [int(v) for v in bt.tolist()]
+        combine = {"allreduce_ms": (c1 - c0) * 1e3, "bytes": wl.n_voxels * 8, "histories": nh,
+                   "balance_exact": inc == dep + esc + rem and nh == wl.n_histories,
+                   "tally_sum_equals_deposited": int(tally.sum()) == dep}
 
     peaks = _peaks()
     clk_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -431,6 +453,7 @@ def main():
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "histories_per_step": hist_per_step,
+                   "split": f"history ids {first}..{first + count - 1} of {wl.n_histories} on rank {rank}",
                    "euler_steps_per_launch": steps_per_launch, "parallelism": f"replicas x{ws}",
                    "l2": "flushed (256 MB write) before every timed step", "tally": "int64 fixed point 2^-24 MeV",
                    "tuning": d.get_tuning()},
@@ -445,6 +468,7 @@ def main():
                      "peak_note": f"{SMS} SMs x {LANE_OPS_PER_CLK_PER_SM} lane-ops/clk x {clk_mhz:.0f} MHz (max SM clock)"},
         "clocks": clocks,
         "balance_exact": bal["incident"] == bal["deposited"] + bal["escaped"] + bal["removed"],
+        "combine": combine,
     }
     if args.plan:
         line["batched_plan"] = plan_benchmark(torch, S, dev)

@@ -174,11 +174,26 @@ int sde_dose_autotune(sde_dose* d, const sde_spot* spots, int n_spots, uint64_t 
  * Errors: SDE_EINVAL (bad spot, energy above e_max/1.05), SDE_ECUDA. */
 int sde_dose_run(sde_dose* d, const sde_spot* spots, int n_spots, uint64_t seed);
 
+/* As sde_dose_run for the histories with global ids in [first_history,
+ * first_history + n_histories) of the plan only (ids beyond the plan's total
+ * are ignored).  Because every history's random stream is keyed by its global
+ * id, disjoint ranges run with one seed -- on one handle, or on several GPUs
+ * whose integer tallies are then summed -- give exactly the tally and balance
+ * of the whole run: the multi-GPU split of a plan (the paper has no
+ * counterpart; its histories are independent, Sec. 2.2.3).  Errors as
+ * sde_dose_run. */
+int sde_dose_run_range(sde_dose* d, const sde_spot* spots, int n_spots, uint64_t seed, uint64_t first_history,
+                       uint64_t n_histories);
+
 /* As sde_dose_run, with spots already in device memory (d_spots, device
  * pointer to n_spots sde_spot records, caller-owned, must stay valid until
  * the work completes).  Fully asynchronous: invalid spots are reported as
  * SDE_EDEVICE by the next sync/fetch and their histories are not run. */
 int sde_dose_run_device(sde_dose* d, const sde_spot* d_spots, int n_spots, uint64_t seed);
+
+/* sde_dose_run_range with device-resident spots (as sde_dose_run_device). */
+int sde_dose_run_device_range(sde_dose* d, const sde_spot* d_spots, int n_spots, uint64_t seed,
+                              uint64_t first_history, uint64_t n_histories);
 
 /* Wait for the handle's work; SDE_EDEVICE if the device flagged an error
  * (the flag is cleared by the call). */

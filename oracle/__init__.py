@@ -93,6 +93,7 @@ def lib():
             L.oracle_create.argtypes = [C.POINTER(dp), i, i, i, C.POINTER(d), C.POINTER(d), dp, dp,
                                         C.POINTER(Material), i, C.POINTER(Params)]
             L.oracle_run.argtypes = [dp, C.POINTER(Spot), i, u64]
+            L.oracle_run_range.argtypes = [dp, C.POINTER(Spot), i, u64, u64, u64]
             L.oracle_fetch.argtypes = [dp, dp, dp, C.POINTER(Balance)]
             L.oracle_reset.argtypes = [dp]
             L.oracle_destroy.argtypes = [dp]
@@ -183,11 +184,17 @@ class OracleDose:
                                C.byref(self.params)))
         self.h = h
 
-    def run(self, spots=None, seed=None):
+    def run(self, spots=None, seed=None, first=None, count=None):
+        """Transport the plan (or, with first/count, the histories with global ids in
+        [first, first + count))."""
         spots = self.wl.spots if spots is None else spots
         seed = self.wl.seed if seed is None else seed
         arr = _spots(spots)
-        _check(lib().oracle_run(self.h, arr, len(spots), C.c_uint64(seed)))
+        if first is None and count is None:
+            _check(lib().oracle_run(self.h, arr, len(spots), C.c_uint64(seed)))
+        else:
+            _check(lib().oracle_run_range(self.h, arr, len(spots), C.c_uint64(seed), C.c_uint64(first or 0),
+                                          C.c_uint64(2**64 - 1 if count is None else count)))
 
     def fetch(self):
         nx, ny, nz = self.shape

@@ -848,6 +848,11 @@ static void* run_job(void* arg) {
 }
 
 int oracle_run(oracle_dose* d, const oracle_spot* spots, int n_spots, uint64_t seed) {
+    return oracle_run_range(d, spots, n_spots, seed, 0, UINT64_MAX);
+}
+
+int oracle_run_range(oracle_dose* d, const oracle_spot* spots, int n_spots, uint64_t seed, uint64_t first,
+                     uint64_t count) {
     if (!d || !spots || n_spots <= 0) return fail(ORACLE_EINVAL, "bad run arguments");
     uint64_t* prefix = (uint64_t*)malloc(((size_t)n_spots + 1) * sizeof(uint64_t));
     if (!prefix) return fail(ORACLE_ENOMEM, "out of memory");
@@ -862,7 +867,10 @@ int oracle_run(oracle_dose* d, const oracle_spot* spots, int n_spots, uint64_t s
         }
         prefix[s + 1] = prefix[s] + sp->n_hist;
     }
-    uint64_t total = prefix[n_spots];
+    /* the window [h0, h1) of global history ids */
+    const uint64_t h0 = first < prefix[n_spots] ? first : prefix[n_spots];
+    const uint64_t h1 = count < prefix[n_spots] - h0 ? h0 + count : prefix[n_spots];
+    uint64_t total = h1 - h0;
     int T = g_threads;
     if (T <= 0) {
         const char* env = getenv("ORACLE_THREADS");
@@ -887,8 +895,8 @@ int oracle_run(oracle_dose* d, const oracle_spot* spots, int n_spots, uint64_t s
         jobs[t].prefix = prefix;
         jobs[t].n_spots = n_spots;
         jobs[t].seed = seed;
-        jobs[t].h_begin = total * (uint64_t)t / (uint64_t)T;
-        jobs[t].h_end = total * (uint64_t)(t + 1) / (uint64_t)T;
+        jobs[t].h_begin = h0 + total * (uint64_t)t / (uint64_t)T;
+        jobs[t].h_end = h0 + total * (uint64_t)(t + 1) / (uint64_t)T;
         jobs[t].acc.edep = (uint64_t*)calloc(nv, sizeof(uint64_t));
         if (!jobs[t].acc.edep) rc = fail(ORACLE_ENOMEM, "out of memory");
     }

@@ -112,6 +112,11 @@ int oracle_create(oracle_dose** out, int nx, int ny, int nz, const double voxel_
                   const uint8_t* material_id, const oracle_material* mats, int n_mats,
                   const oracle_params* p);
 int oracle_run(oracle_dose* d, const oracle_spot* spots, int n_spots, uint64_t seed);
+/* As oracle_run for the histories with global ids in [first, first + count) of the plan
+ * only (ids run over the spots in order); disjoint ranges with one seed add up to the
+ * whole run exactly. */
+int oracle_run_range(oracle_dose* d, const oracle_spot* spots, int n_spots, uint64_t seed, uint64_t first,
+                     uint64_t count);
 int oracle_fetch(oracle_dose* d, double* dose_Gy, uint64_t* edep_fixed, oracle_balance* bal);
 int oracle_reset(oracle_dose* d);
 void oracle_destroy(oracle_dose* d);

@@ -26,7 +26,8 @@ MAX_ELEMENTS = 16
 
 EXPORTED = [
     "sde_default_params", "sde_last_error", "sde_dose_create", "sde_dose_set_stream",
-    "sde_dose_set_tuning", "sde_dose_get_tuning", "sde_dose_autotune", "sde_dose_run", "sde_dose_run_device",
+    "sde_dose_set_tuning", "sde_dose_get_tuning", "sde_dose_autotune", "sde_dose_run", "sde_dose_run_range",
+    "sde_dose_run_device", "sde_dose_run_device_range",
     "sde_dose_sync", "sde_dose_fetch", "sde_dose_fetch_device", "sde_dose_fetch_device_f32", "sde_dose_reset",
     "sde_dose_destroy", "sde_dose_info", "sde_dose_tables", "sde_dose_probe_steps",
     "sde_transport_noalloc", "sde_gemm_bf16", "sde_conv3d_forward", "sde_conv3d_wgrad",
@@ -35,6 +36,16 @@ EXPORTED = [
     "sde_denoiser_gradients", "sde_denoiser_get_params", "sde_denoiser_set_params", "sde_gamma3d",
     "sde_scale_f32",
 ]
+
+
+def history_shard(total: int, rank: int, world: int):
+    """(first, count) of the contiguous block of global history ids that rank ``rank`` of
+    ``world`` transports when one plan of ``total`` histories is split across GPUs: the
+    blocks are disjoint, cover [0, total) and differ in size by at most one."""
+    if world < 1 or not 0 <= rank < world or total < 0:
+        raise ValueError("need 0 <= rank < world and total >= 0")
+    first = total * rank // world
+    return first, total * (rank + 1) // world - first
 
 
 class SdeError(RuntimeError):
@@ -101,7 +112,9 @@ def lib():
         L.sde_dose_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
         L.sde_dose_autotune.argtypes = [vp, C.POINTER(Spot), i, u64, u64, C.POINTER(Tuning)]
         L.sde_dose_run.argtypes = [vp, C.POINTER(Spot), i, u64]
+        L.sde_dose_run_range.argtypes = [vp, C.POINTER(Spot), i, u64, u64, u64]
         L.sde_dose_run_device.argtypes = [vp, vp, i, u64]
+        L.sde_dose_run_device_range.argtypes = [vp, vp, i, u64, u64, u64]
         L.sde_dose_sync.argtypes = [vp]
         L.sde_dose_fetch.argtypes = [vp, vp, vp, C.POINTER(Balance)]
         L.sde_dose_fetch_device.argtypes = [vp, vp, vp, C.POINTER(Balance)]
@@ -220,12 +233,23 @@ class SdeDose:
         return {n: getattr(t, n) for n, _ in Tuning._fields_}
 
     # -- work
-    def run(self, spots, seed=0):
+    def run(self, spots, seed=0, first=None, count=None):
+        """Transport the plan, or with first/count the histories with global ids in
+        [first, first + count) (one shard of it)."""
         a, ptr = spots_to_ctypes(spots)
-        _check(lib().sde_dose_run(self.h, ptr, len(a), C.c_uint64(seed)))
+        if first is None and count is None:
+            _check(lib().sde_dose_run(self.h, ptr, len(a), C.c_uint64(seed)))
+        else:
+            _check(lib().sde_dose_run_range(self.h, ptr, len(a), C.c_uint64(seed), C.c_uint64(first or 0),
+                                            C.c_uint64(2**64 - 1 if count is None else count)))
 
-    def run_device(self, d_spots_ptr: int, n_spots: int, seed=0):
-        _check(lib().sde_dose_run_device(self.h, C.c_void_p(d_spots_ptr), int(n_spots), C.c_uint64(seed)))
+    def run_device(self, d_spots_ptr: int, n_spots: int, seed=0, first=None, count=None):
+        if first is None and count is None:
+            _check(lib().sde_dose_run_device(self.h, C.c_void_p(d_spots_ptr), int(n_spots), C.c_uint64(seed)))
+        else:
+            _check(lib().sde_dose_run_device_range(self.h, C.c_void_p(d_spots_ptr), int(n_spots), C.c_uint64(seed),
+                                                   C.c_uint64(first or 0),
+                                                   C.c_uint64(2**64 - 1 if count is None else count)))
 
     def sync(self):
         _check(lib().sde_dose_sync(self.h))

@@ -358,14 +358,18 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
     P.mats = d->d_mj;
     P.spots = d->d_spots;
     P.prefix = d->d_prefix;
+    P.h_end = ~0ull;
     P.n_spots = n_spots;
     P.counters = d->d_counters;
     P.err = d->d_err;
     return P;
 }
 
-static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t seed) {
+// Histories with global ids in [h_begin, h_end) of the plan are transported.
+static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t seed, uint64_t h_begin = 0,
+                             uint64_t h_end = ~0ull) {
     KParams P = make_kparams(d, n, seed);
+    P.h_end = h_end;
     int warps = d->tune.warps_per_block;
     int block = warps * 32;
     bool smem = d->tune.table_smem == 1 && d->table_bytes <= 96 * 1024;
@@ -376,7 +380,7 @@ static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t s
     int grid = d->num_sms * per_sm;
     if (d->tune.graph != 2) {
         CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
-                             d->p.e_max_MeV, d->stream));
+                             d->p.e_max_MeV, d->stream, h_begin));
         CUDA_TRY(launch_transport(P, grid, block, d->table_bytes, smem, d->stream));
         return SDE_OK;
     }
@@ -386,7 +390,7 @@ static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t s
     if (!d->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamBeginCapture(d->capture_stream, cudaStreamCaptureModeRelaxed));
     cudaError_t e1 = launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
-                                 d->p.e_max_MeV, d->capture_stream);
+                                 d->p.e_max_MeV, d->capture_stream, h_begin);
     cudaError_t e2 = e1 == cudaSuccess
                          ? launch_transport(P, grid, block, d->table_bytes, smem, d->capture_stream)
                          : e1;
@@ -424,7 +428,24 @@ static int check_spots_host(const sde_dose* d, const sde_spot* spots, int n) {
     return SDE_OK;
 }
 
+static int stage_spots(sde_dose* d, const sde_spot* spots, int n_spots);
+
 extern "C" int sde_dose_run(sde_dose* d, const sde_spot* spots, int n_spots, uint64_t seed) {
+    int rc = stage_spots(d, spots, n_spots);
+    return rc ? rc : enqueue_transport(d, d->d_raw_spots, n_spots, seed);
+}
+
+extern "C" int sde_dose_run_range(sde_dose* d, const sde_spot* spots, int n_spots, uint64_t seed,
+                                  uint64_t first_history, uint64_t n_histories) {
+    int rc = stage_spots(d, spots, n_spots);
+    if (rc) return rc;
+    const uint64_t end = n_histories > ~0ull - first_history ? ~0ull : first_history + n_histories;
+    return enqueue_transport(d, d->d_raw_spots, n_spots, seed, first_history, end);
+}
+
+// Validates host spots and copies them (through the pinned staging buffer) to the
+// device on the handle's stream.
+static int stage_spots(sde_dose* d, const sde_spot* spots, int n_spots) {
     if (!d || !spots || n_spots < 1) return set_err(SDE_EINVAL, "bad run arguments");
     int rc = check_spots_host(d, spots, n_spots);
     if (rc) return rc;
@@ -434,9 +455,7 @@ extern "C" int sde_dose_run(sde_dose* d, const sde_spot* spots, int n_spots, uin
     // reuse the pinned staging buffer only after its previous copy finished
     CUDA_TRY(cudaEventSynchronize(d->stage_ev));
     if (n_spots > d->stage_cap) {
-        if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
-    if (d->capture_stream) cudaStreamDestroy(d->capture_stream);
-    if (d->h_stage) cudaFreeHost(d->h_stage);
+        if (d->h_stage) cudaFreeHost(d->h_stage);
         d->h_stage = nullptr;
         d->stage_cap = 0;
         CUDA_TRY(cudaMallocHost(&d->h_stage, (size_t)n_spots * sizeof(sde_spot)));
@@ -446,15 +465,21 @@ extern "C" int sde_dose_run(sde_dose* d, const sde_spot* spots, int n_spots, uin
     CUDA_TRY(cudaMemcpyAsync(d->d_raw_spots, d->h_stage, (size_t)n_spots * sizeof(sde_spot),
                              cudaMemcpyHostToDevice, d->stream));
     CUDA_TRY(cudaEventRecord(d->stage_ev, d->stream));
-    return enqueue_transport(d, d->d_raw_spots, n_spots, seed);
+    return SDE_OK;
 }
 
 extern "C" int sde_dose_run_device(sde_dose* d, const sde_spot* d_spots, int n_spots, uint64_t seed) {
+    return sde_dose_run_device_range(d, d_spots, n_spots, seed, 0, ~0ull);
+}
+
+extern "C" int sde_dose_run_device_range(sde_dose* d, const sde_spot* d_spots, int n_spots, uint64_t seed,
+                                         uint64_t first_history, uint64_t n_histories) {
     if (!d || !d_spots || n_spots < 1) return set_err(SDE_EINVAL, "bad run arguments");
     CUDA_TRY(cudaSetDevice(d->device));
     int rc = ensure_spot_capacity(d, n_spots);
     if (rc) return rc;
-    return enqueue_transport(d, d_spots, n_spots, seed);
+    const uint64_t end = n_histories > ~0ull - first_history ? ~0ull : first_history + n_histories;
+    return enqueue_transport(d, d_spots, n_spots, seed, first_history, end);
 }
 
 // Autotuner: times the transport on a subsample of the plan under each

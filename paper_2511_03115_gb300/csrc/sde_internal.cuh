@@ -84,6 +84,7 @@ struct KParams {
     const MatJump* __restrict__ mats;
     const SpotDev* __restrict__ spots;
     const unsigned long long* __restrict__ prefix;  // [n_spots+1]
+    unsigned long long h_end;  // histories with global id >= h_end are not run (range runs)
     int n_spots;
     unsigned long long* counters;  // kCntWords
     unsigned int* err;

@@ -217,6 +217,7 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     P.mats = d_mj;
     P.spots = spots;
     P.prefix = prefix;
+    P.h_end = ~0ull;
     P.n_spots = n_spots;
     P.counters = counters;
     P.err = err;

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const unsigned long long total = P.prefix[P.n_spots];
+    const unsigned long long total = P.prefix[P.n_spots] < P.h_end ? P.prefix[P.n_spots] : P.h_end;
     bool alive = false;
     float E = 0.f, px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 1.f, tau = 1.f;
     unsigned long long h = 0;
@@ -500,12 +500,12 @@ __global__ void k_sum_u64(const unsigned long long* __restrict__ v, size_t n, un
 }
 
 // Spot records -> device form and the inclusive prefix of history counts;
-// resets the work-queue cursor.  One block.
+// sets the work-queue cursor to the first history id of the run.  One block.
 __global__ void __launch_bounds__(1024) k_prep_spots(const sde_spot* raw, int n, SpotDev* out,
                                                      unsigned long long* prefix,
                                                      unsigned long long* counters, unsigned int* err,
                                                      double ox, double oy, double oz, double e_min,
-                                                     double e_lim) {
+                                                     double e_lim, unsigned long long h_begin) {
     __shared__ unsigned long long scan[1024];
     unsigned long long carry = 0;
     for (int base = 0; base < n; base += blockDim.x) {
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(1024) k_prep_spots(const sde_spot* raw, int n,
     }
     if (threadIdx.x == 0) {
         prefix[0] = 0;
-        counters[kCntCursor] = 0;
+        counters[kCntCursor] = h_begin;
     }
 }
 
@@ -646,8 +646,9 @@ int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally
 
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,
                         unsigned long long* counters, unsigned int* err, const double o[3], double e_min,
-                        double e_lim, cudaStream_t st) {
-    k_prep_spots<<<1, 1024, 0, st>>>(raw, n, out, prefix, counters, err, o[0], o[1], o[2], e_min, e_lim);
+                        double e_lim, cudaStream_t st, unsigned long long h_begin) {
+    k_prep_spots<<<1, 1024, 0, st>>>(raw, n, out, prefix, counters, err, o[0], o[1], o[2], e_min, e_lim,
+                                     h_begin);
     return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_
 int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode, bool aggregate);
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,
                         unsigned long long* counters, unsigned int* err, const double o[3], double e_min,
-                        double e_lim, cudaStream_t st);
+                        double e_lim, cudaStream_t st, unsigned long long h_begin = 0);
 cudaError_t launch_probe(const KParams& P, int m, float rho, float E0, uint64_t h0, int n, float* Eo,
                          float* co, int* jo, float* uxo, float* uyo, cudaStream_t st);
 cudaError_t launch_sum_u64(const unsigned long long* v, size_t n, unsigned long long* out, int num_sms,

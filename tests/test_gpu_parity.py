@@ -305,6 +305,34 @@ def test_autotune_and_graph_launch_keep_the_tally(sde_gpu):
             assert np.array_equal(e, want)
 
 
+@pytest.mark.parametrize("graph", [0, 2])
+def test_history_ranges_add_up_to_the_whole_run(sde_gpu, graph):
+    """The multi-GPU split of a plan: shards of its global history ids (run here one after
+    the other on one handle, which accumulates) give the whole run's integer tally and
+    balance bit for bit, in plain and graph launch mode; a range past the plan runs
+    nothing and an over-long range is clipped."""
+    from sde_workloads import plan_spots
+    spots = plan_spots(6, 30_000, seed=4, e_range=(70.0, 110.0), pitch=5.0, half_width=10.0)
+    wl = water100(30_000)
+    with sde_gpu.SdeDose(wl) as d:
+        if graph:
+            d.set_tuning(graph=graph)
+        d.run(spots, seed=5)
+        _, ref, rb = d.fetch(dose=False)
+        d.reset()
+        total = int(spots["n_hist"].sum())
+        for r in range(3):
+            first, count = sde_gpu.history_shard(total, r, 3)
+            d.run(spots, seed=5, first=first, count=count)
+        d.run(spots, seed=5, first=total, count=100)
+        _, e, b = d.fetch(dose=False)
+        assert np.array_equal(e, ref) and b == rb
+        d.reset()
+        d.run(spots, seed=5, first=total - 10, count=10**12)
+        _, e, b = d.fetch(dose=False)
+        assert b["histories"] == 10 and b["incident"] == b["deposited"] + b["escaped"] + b["removed"]
+
+
 def test_insert150_gamma_at_one_million_protons(sde_gpu, oracle_lib):
     """configs[2]: 3D gamma (2 %/0.5 mm, local, 1 % threshold) of the GPU dose against the
     oracle at 10^6 protons.  Both doses are noisy, so the pass rate is compared with the pass
