@@ -59,7 +59,7 @@ class Params(C.Structure):
                 ("e_min_MeV", C.c_double), ("K", C.c_double), ("inel_u_lo", C.c_double),
                 ("inel_u_hi", C.c_double), ("km_r", C.c_double), ("tally_mode", C.c_int),
                 ("fixed_point_shift", C.c_int), ("jump_clock", C.c_int), ("max_steps", C.c_int),
-                ("physics_mask", C.c_int)]
+                ("physics_mask", C.c_int), ("theta_cut_sigmas", C.c_double)]
 
 
 class Balance(C.Structure):
@@ -77,7 +77,7 @@ MAX_EL = 16
 class PhysicsOut(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("beta2", "gamma", "p_MeV", "I_eV", "s1", "s2sq", "chi_c2",
                                           "chi_a2", "w", "sigma_msc", "t_sbm", "sig_e",
-                                          "sig_ne")] + [
+                                          "sig_ne", "theta_cut")] + [
         ("n_el", C.c_int), ("sig_e_el", C.c_double * MAX_EL), ("sig_ne_el", C.c_double * MAX_EL)]
 
 

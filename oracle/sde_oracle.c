@@ -357,9 +357,22 @@ static void physics_eval(const or_mat* m, double rho, const oracle_params* p, do
         o->t_sbm = sig2 * p->step_cm / z;
     }
 
+    /* Cut-off between the diffusion and the jumps (Sec. 2.1.3): the paper fixes it at
+     * 0.02 rad for its simulations but defines it as 2.5 sigma(E); with
+     * theta_cut_sigmas = k > 0 it is k sigma(E) at this energy and density.  Reading:
+     * clamped to [1e-4, 1] rad (sigma grows without bound near the end of the range,
+     * and vanishes in vacuum). */
+    double theta_c = p->theta_cut_rad;
+    if (p->theta_cut_sigmas > 0.0) {
+        theta_c = p->theta_cut_sigmas * o->sigma_msc;
+        if (theta_c < 1e-4) theta_c = 1e-4;
+        if (theta_c > 1.0) theta_c = 1.0;
+    }
+    o->theta_cut = theta_c;
+
     /* Eq. large_elastic_cm (non-H, Rutherford part) and
      * Eq. large_elastic_cm_hydrogen (Mott part): rate per cm. */
-    double mu_c = cos(p->theta_cut_rad);
+    double mu_c = cos(theta_c);
     double mu_lo = -cos(p->backscatter_rad); /* -1 + delta, delta = 1 + cos(pi - theta_b) */
     for (int i = 0; i < m->n; ++i) {
         double n_i = OR_NA * m->w[i] * rho / m->A[i]; /* atoms per cm^3 */
@@ -471,6 +484,7 @@ void oracle_default_params(oracle_params* p) {
     p->jump_clock = 0;
     p->max_steps = 100000;
     p->physics_mask = ORACLE_PHYS_ALL;
+    p->theta_cut_sigmas = 0.0;
 }
 
 static int check_params(const oracle_params* p) {
@@ -480,7 +494,8 @@ static int check_params(const oracle_params* p) {
         !(p->K > 0.0) || !(p->inel_u_lo >= 0.0 && p->inel_u_hi <= 1.0 && p->inel_u_lo <= p->inel_u_hi) ||
         !(p->km_r >= 0.0 && p->km_r < 1.0) || (p->tally_mode != 0 && p->tally_mode != 1) ||
         p->fixed_point_shift < 0 || p->fixed_point_shift > 30 || p->max_steps <= 0 ||
-        (p->jump_clock != 0 && p->jump_clock != 1) || p->physics_mask < 0 || p->physics_mask > 15)
+        (p->jump_clock != 0 && p->jump_clock != 1) || p->physics_mask < 0 || p->physics_mask > 15 ||
+        !(p->theta_cut_sigmas >= 0.0 && p->theta_cut_sigmas <= 100.0))
         return fail(ORACLE_EINVAL, "invalid parameters");
     return ORACLE_OK;
 }
@@ -741,7 +756,7 @@ static void sde_step(const or_mat* m, double rho, const oracle_params* p, uint64
         int el = pick < m->n ? pick : pick - m->n;
         double m2 = target_mass(m->Z[el], m->A[el]);
         if (pick < m->n) {
-            double mu_c = cos(p->theta_cut_rad);
+            double mu_c = cos(ph.theta_cut);
             double mu;
             if (m->Z[el] == 1) {
                 double eta, k;

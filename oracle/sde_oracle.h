@@ -75,6 +75,9 @@ typedef struct {
     int jump_clock;          /* 0: one Bernoulli draw per step (paper); 1: exponential clock */
     int max_steps;           /* step cap per history */
     int physics_mask;        /* ORACLE_PHYS_* */
+    double theta_cut_sigmas; /* 0: fixed theta_cut_rad; k > 0: energy-dependent cut-off
+                                theta_c = k sigma(E) (Sec. 2.1.3, k = 2.5), clamped to
+                                [1e-4, 1] rad */
 } oracle_params;
 
 typedef struct {
@@ -96,6 +99,7 @@ typedef struct {
     double t_sbm;         /* m^2 Delta = sigma^2 Delta / z            */
     double sig_e;         /* total large-angle elastic rate, 1/cm     */
     double sig_ne;        /* total non-elastic rate, 1/cm             */
+    double theta_cut;     /* large-angle cut-off used, CM, rad        */
     int n_el;
     double sig_e_el[ORACLE_MAX_EL];
     double sig_ne_el[ORACLE_MAX_EL];

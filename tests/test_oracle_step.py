@@ -133,3 +133,58 @@ def test_survival_against_nonelastic_removal(oracle_lib):
     _, _, b = O.run_workload(wl, physics_mask=O.PHYS_INELASTIC, inel_u_lo=1.0, inel_u_hi=1.0)
     frac = b["jumps_inelastic"] / n
     assert abs(frac - p) < 3.5 * math.sqrt(p * (1 - p) / n), (frac, p)
+
+
+OXYGEN = {"name": "oxygen", "elements": [(8, 1.0)], "I_eV": 0.0}
+
+
+@pytest.mark.parametrize("mat,rho", [(WATER, 1.0), (BONE, 1.85), (WATER, 0.26)])
+@pytest.mark.parametrize("E", [1.0, 10.0, 100.0])
+def test_energy_dependent_cut_off_is_the_fixed_law_at_that_angle(oracle_lib, mat, rho, E):
+    """Sec. 2.1.3 cut-off 2.5 sigma(E): the rates with theta_cut_sigmas = 2.5 equal those of
+    the fixed-cut law evaluated at the angle the mode chose, element by element."""
+    a = O.physics(mat, rho, E, theta_cut_sigmas=2.5)
+    b = O.physics(mat, rho, E, theta_cut_rad=a.theta_cut)
+    assert 1e-4 <= a.theta_cut <= 1.0
+    assert a.sig_e == b.sig_e and a.sig_ne == b.sig_ne
+    assert list(a.sig_e_el) == list(b.sig_e_el)
+
+
+def test_cut_off_scales_with_sigma_and_rutherford_rate_with_its_inverse_square(oracle_lib):
+    """Doubling k doubles theta_c; the Rutherford rate of a hydrogen-free material,
+    proportional to 1/(1 - cos theta_c) - 1/2 ~ 2/theta_c^2, falls by a factor of 4."""
+    a = O.physics(OXYGEN, 1.0, 100.0, theta_cut_sigmas=2.5)
+    b = O.physics(OXYGEN, 1.0, 100.0, theta_cut_sigmas=5.0)
+    assert b.theta_cut == pytest.approx(2.0 * a.theta_cut, rel=1e-14)
+    assert a.sig_e / b.sig_e == pytest.approx(4.0, rel=2e-5)
+    # the cut-off falls with energy (sigma ~ 1/(p beta)) and widens in denser media
+    assert O.physics(WATER, 1.0, 150.0, theta_cut_sigmas=2.5).theta_cut < a.theta_cut * 1.2
+    assert O.physics(WATER, 1.0, 30.0, theta_cut_sigmas=2.5).theta_cut > \
+        O.physics(WATER, 1.0, 100.0, theta_cut_sigmas=2.5).theta_cut
+    assert O.physics(BONE, 1.85, 100.0, theta_cut_sigmas=2.5).theta_cut > \
+        O.physics(BONE, 1.0, 100.0, theta_cut_sigmas=2.5).theta_cut
+
+
+def test_cut_off_clamps(oracle_lib):
+    assert O.physics(WATER, 1.0, 0.06, theta_cut_sigmas=2.5).theta_cut == 1.0
+    vac = O.physics(WATER, 0.0, 50.0, theta_cut_sigmas=2.5)
+    assert vac.theta_cut == 1e-4 and vac.sig_e == 0.0 and vac.sig_ne == 0.0
+
+
+def test_jumps_with_the_energy_dependent_cut_off(oracle_lib):
+    """Single steps at 100 MeV with only large-angle elastic and non-elastic events:
+    the jump probability is 1 - exp(-Delta sigma) at the mode's rates, and elastic
+    deflections on oxygen start at the cut-off (the lab angle of a small CM angle is
+    about A/(A+1) = 0.94 of it; the fixed cut-off would put them near 0.019 rad)."""
+    mask = O.PHYS_ELASTIC | O.PHYS_INELASTIC
+    for mat in (BONE, OXYGEN):
+        ph = O.physics(mat, 1.0, 100.0, physics_mask=mask, theta_cut_sigmas=2.5)
+        p = -math.expm1(-0.05 * (ph.sig_e + ph.sig_ne))
+        out = O.single_step(mat, 1.0, 100.0, N, seed=9, physics_mask=mask, jump_clock=1, theta_cut_sigmas=2.5)
+        frac = np.mean(out["jump"] > 0)
+        assert abs(frac - p) < 3.5 * math.sqrt(p * (1 - p) / N)
+        if mat is OXYGEN:
+            el = out["jump"] == 1
+            assert el.sum() > 100
+            smallest = np.arccos(out["cos"][el].max())
+            assert 0.9 * ph.theta_cut <= smallest <= ph.theta_cut
