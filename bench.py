@@ -325,6 +325,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-histories", type=int, default=20_000)
+    ap.add_argument("--theta-cut-sigmas", type=float, default=0.0,
+                    help="energy-dependent elastic cut-off theta_c = k sigma(E) (0: the paper's fixed 0.02 rad)")
     ap.add_argument("--no-denoiser", action="store_true",
                     help="skip the learned-vs-plain time-to-dose and the denoiser throughput")
     ap.add_argument("--plan", action="store_true",
@@ -347,7 +349,7 @@ def main():
     wl = slab150(args.histories * ws)  # one plan; this rank runs its shard of the history ids
     first, count = S.history_shard(wl.n_histories, rank, ws)
     stream = torch.cuda.Stream(device=dev)
-    d = S.SdeDose(wl, stream=stream)
+    d = S.SdeDose(wl, stream=stream, theta_cut_sigmas=args.theta_cut_sigmas)
     spots_dev = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     seed_base = 1_000_003
@@ -456,6 +458,8 @@ def main():
                    "split": f"history ids {first}..{first + count - 1} of {wl.n_histories} on rank {rank}",
                    "euler_steps_per_launch": steps_per_launch, "parallelism": f"replicas x{ws}",
                    "l2": "flushed (256 MB write) before every timed step", "tally": "int64 fixed point 2^-24 MeV",
+                   "elastic_cut_off": (f"theta_c = {args.theta_cut_sigmas} sigma(E)" if args.theta_cut_sigmas > 0
+                                       else "fixed 0.02 rad"),
                    "tuning": d.get_tuning()},
         "e2e": {"value": hist_per_step / e2e_T, "unit": "histories/s",
                 "h2d_bytes_per_step": int(wl.spots.nbytes),

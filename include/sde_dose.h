@@ -100,6 +100,11 @@ typedef struct {
     int max_steps;          /* step cap per history; exceeding it is SDE_EDEVICE    */
     int physics_mask;       /* SDE_PHYS_* (SDE_PHYS_ALL)                            */
     int table_points;       /* points of the ln-E table grid, 64..4096 (256)        */
+    double theta_cut_sigmas;/* 0: fixed theta_cut_rad (the paper's runs); k in (0, 100]: the
+                               energy-dependent cut-off theta_c = k sigma(E) of Sec. 2.1.3
+                               (k = 2.5), sigma the Lynch-Dahl width over z at the step's
+                               energy and density, clamped to [1e-4, 1] rad; it sets the
+                               large-angle elastic rates and the jump's CM angle range   */
 } sde_params;
 
 /* Energy balance in tally units: incident == deposited + escaped + removed

@@ -55,6 +55,7 @@ struct sde_dose {
     float* d_jrates = nullptr;
     double* d_csda = nullptr;
     float4* d_table = nullptr;
+    float4* d_cut = nullptr;  // [n_mats][N][2] Coulomb coefficients of the variable cut-off
     unsigned long long* d_counters = nullptr;
     unsigned int* d_err = nullptr;
     sde_spot* d_raw_spots = nullptr;
@@ -91,6 +92,7 @@ extern "C" int sde_default_params(sde_params* p) {
     p->fixed_point_shift = 24;
     p->max_steps = 100000;
     p->physics_mask = SDE_PHYS_ALL;
+    p->theta_cut_sigmas = 0.0;
     p->table_points = 256;
     return SDE_OK;
 }
@@ -110,14 +112,16 @@ static int check_params(const sde_params& p) {
               p.e_max_MeV > 2.0 * p.e_min_MeV && p.e_max_MeV <= 1000.0 &&
               (p.tally_mode == 0 || p.tally_mode == 1) && p.fixed_point_shift >= 0 &&
               p.fixed_point_shift <= 30 && p.max_steps > 0 && p.physics_mask >= 0 &&
-              p.physics_mask <= SDE_PHYS_ALL && p.table_points >= 64 && p.table_points <= 4096;
+              p.physics_mask <= SDE_PHYS_ALL && p.table_points >= 64 && p.table_points <= 4096 &&
+              p.theta_cut_sigmas >= 0.0 && p.theta_cut_sigmas <= 100.0;
     return ok ? SDE_OK : set_err(SDE_EINVAL, "invalid sde_params");
 }
 
 static void free_all(sde_dose* d) {
     void* ptrs[] = {d->d_rho,   d->d_vox,      d->d_edep,   d->d_mats,        d->d_mj,
                     d->d_raw,   d->d_jrates,   d->d_csda,   d->d_table,       d->d_counters,
-                    d->d_err,   d->d_raw_spots, d->d_spots, d->d_prefix,      d->d_dose};
+                    d->d_err,   d->d_raw_spots, d->d_spots, d->d_prefix,      d->d_dose,
+                    d->d_cut};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
@@ -214,6 +218,7 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     TRY(cudaMalloc(&d->d_csda, (size_t)n_mats * N * sizeof(double)));
     d->table_bytes = (size_t)n_mats * N * kRowFloat4 * sizeof(float4);
     TRY(cudaMalloc(&d->d_table, d->table_bytes));
+    TRY(cudaMalloc(&d->d_cut, (size_t)n_mats * N * 2 * sizeof(float4)));
     TRY(cudaMalloc(&d->d_counters, kCntWords * sizeof(unsigned long long)));
     TRY(cudaMalloc(&d->d_err, sizeof(unsigned int)));
     TRY(cudaMallocHost(&d->h_counters, (kCntWords + 1) * sizeof(unsigned long long)));
@@ -257,6 +262,7 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     tb.d_jrates = d->d_jrates;
     tb.d_csda = d->d_csda;
     tb.d_table = d->d_table;
+    tb.d_cut = d->d_cut;
     TRY(build_tables(tb, nullptr));
     TRY(cudaDeviceSynchronize());
 #undef TRY
@@ -355,6 +361,11 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
     P.edep = d->d_edep;
     P.table = d->d_table;
     P.jrates = d->d_jrates;
+    P.cut = d->d_cut;
+    // theta_c^2 = k^2 sigma^2 = k^2 (z / Delta) t, t the step's Brownian time
+    P.cut_k2 = d->p.theta_cut_sigmas > 0.0
+                   ? (float)(d->p.theta_cut_sigmas * d->p.theta_cut_sigmas * d->p.msc_z_cm / d->p.step_cm)
+                   : 0.f;
     P.mats = d->d_mj;
     P.spots = d->d_spots;
     P.prefix = d->d_prefix;
@@ -373,8 +384,10 @@ static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t s
     int warps = d->tune.warps_per_block;
     int block = warps * 32;
     bool smem = d->tune.table_smem == 1 && d->table_bytes <= 96 * 1024;
+    const bool cut = P.cut_k2 > 0.f;  // own kernels: no shared-memory tables or tally aggregation
+    if (cut) smem = false;
     int per_sm = transport_max_blocks_per_sm(block, smem ? d->table_bytes : 0, smem, d->p.tally_mode,
-                                             d->tune.aggregate == 2);
+                                             d->tune.aggregate == 2, cut);
     if (per_sm < 1) return set_err(SDE_ECUDA, "transport kernel cannot be resident with %d warps per block", warps);
     if (d->tune.blocks_per_sm > 0) per_sm = std::min(per_sm, d->tune.blocks_per_sm);
     int grid = d->num_sms * per_sm;

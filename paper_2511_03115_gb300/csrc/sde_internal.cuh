@@ -81,6 +81,8 @@ struct KParams {
     unsigned long long* __restrict__ edep;
     const float4* __restrict__ table;  // [n_mats][N][kRowFloat4]
     const float* __restrict__ jrates;  // [n_mats][N][2*SDE_MAX_ELEMENTS] per unit density
+    const float4* __restrict__ cut;    // [n_mats][N][2] Coulomb coefficients (variable cut-off)
+    float cut_k2;                      // k^2 z / Delta, or 0: fixed cut-off s_cut
     const MatJump* __restrict__ mats;
     const SpotDev* __restrict__ spots;
     const unsigned long long* __restrict__ prefix;  // [n_spots+1]

@@ -128,6 +128,7 @@ struct TableArgs {
     float* jrates;  // [n_mats][N][2*SDE_MAX_ELEMENTS]: sigma_e E^2 / rho, then sigma_ne / rho
     double* csda;   // [n_mats][N]
     float4* table;  // [n_mats][N][kRowFloat4]
+    float4* cut;    // [n_mats][N][2] or null
 };
 
 __device__ double stopping_per_rho(const MatHost& m, double K, double E) {
@@ -254,6 +255,47 @@ __global__ void k_build_hot(TableArgs a) {
     row[2] = make_float4((float)v0[4], (float)(v1[4] - v0[4]), (float)v0[5], (float)v0[6]);
 }
 
+// Coefficients of the large-angle elastic rate with a variable cut-off, per unit density,
+// times E^2 Delta (flat in E like fe): the Rutherford sum over elements other than
+// hydrogen, R = sum n_i 2 pi (eta_i/k_i)^2, multiplies 1/(1 - mu_c) - 1/2; hydrogen's
+// Hc = n_H 2 pi (eta/k)^2 multiplies the Mott primitive at mu_c, minus Hlo = Hc G(mu_lo)
+// at the backscatter limit.  Row 0 {R, dR, Hc, dHc}, row 1 {Hlo, dHlo, 0, 0}.
+__device__ void cut_values(const TableArgs& a, int mi, int kk, double v[3]) {
+    const MatHost& m = a.mats[mi];
+    double E = exp(a.lnEmin + kk * a.dlnE);
+    double vnr = sqrt(2.0 * E / kProtonMass);
+    v[0] = v[1] = v[2] = 0.0;
+    if (!(a.mask & SDE_PHYS_ELASTIC)) return;
+    for (int i = 0; i < m.n_el; ++i) {
+        double m2 = m.Z[i] == 1 ? kProtonMass : m.A[i] * kAtomicMassUnit;
+        double mu_red = kProtonMass * m2 / (kProtonMass + m2);
+        double eta = m.Z[i] * kFineStructure / vnr;
+        double kwave = mu_red * vnr / kHbarcMeVfm;
+        double coef = kAvogadro * m.w[i] / m.A[i] * 2.0 * kPi * (eta / kwave) * (eta / kwave) * 1e-26 * E * E * a.step;
+        if (m.Z[i] == 1) {
+            v[1] += coef;
+            v[2] += coef * mott_primitive(-a.cos_back, eta);
+        } else {
+            v[0] += coef;
+        }
+    }
+}
+
+__global__ void k_build_cut(TableArgs a) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.N * a.n_mats) return;
+    int mi = idx / a.N, kk = idx % a.N;
+    double v0[3], v1[3];
+    cut_values(a, mi, kk, v0);
+    if (kk + 1 < a.N)
+        cut_values(a, mi, kk + 1, v1);
+    else
+        for (int i = 0; i < 3; ++i) v1[i] = v0[i];
+    float4* row = a.cut + ((size_t)mi * a.N + kk) * 2;
+    row[0] = make_float4((float)v0[0], (float)(v1[0] - v0[0]), (float)v0[1], (float)(v1[1] - v0[1]));
+    row[1] = make_float4((float)v0[2], (float)(v1[2] - v0[2]), 0.f, 0.f);
+}
+
 // CSDA range at unit density: one block per material; thread j integrates
 // [E_j, E_j+1] by 8-point Gauss-Legendre in ln E, then a serial prefix sum.
 __global__ void k_csda(TableArgs a) {
@@ -300,11 +342,13 @@ cudaError_t build_tables(const TableBuild& tb, cudaStream_t st) {
     a.jrates = tb.d_jrates;
     a.csda = tb.d_csda;
     a.table = tb.d_table;
+    a.cut = tb.d_cut;
     int total = tb.N * tb.n_mats;
     int threads = 128, blocks = (total + threads - 1) / threads;
     k_build_raw<<<blocks, threads, 0, st>>>(a);
     k_build_hot<<<blocks, threads, 0, st>>>(a);
     k_csda<<<tb.n_mats, 256, 0, st>>>(a);
+    if (a.cut) k_build_cut<<<blocks, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

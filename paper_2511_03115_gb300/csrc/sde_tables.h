@@ -30,6 +30,7 @@ struct TableBuild {
     float* d_jrates;
     double* d_csda;
     float4* d_table;
+    float4* d_cut = nullptr;  // optional [n_mats][N][2]: Coulomb coefficients (variable cut-off)
 };
 
 cudaError_t build_tables(const TableBuild& tb, cudaStream_t st);

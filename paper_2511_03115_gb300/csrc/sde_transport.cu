@@ -20,9 +20,11 @@ namespace sde {
 
 // Per-unit-density step quantities at one energy (see the hot-row layout in
 // sde_internal.cuh): c = varsigma_1 Delta, s = sqrt(varsigma_2^2 Delta),
-// w = Lynch-Dahl w, tg = t / g(w) (Brownian time over g), sj = jump rate x Delta.
+// w = Lynch-Dahl w, tg = t / g(w) (Brownian time over g), sj = jump rate x Delta,
+// sn = its non-elastic part; k, f = table interval and fraction.
 struct Phys {
-    float c, s, w, tg, sj;
+    float c, s, w, tg, sj, sn, f;
+    int k;
 };
 
 __device__ __forceinline__ void grid_pos(const KParams& P, float E, int& k, float& f) {
@@ -48,8 +50,41 @@ __device__ __forceinline__ Phys lookup(const float4* tab, const KParams& P, int 
     ph.s = fmaf(a.w, f, a.z);
     ph.w = c.z * fmaf(b.y, f, b.x) * ib2;
     ph.tg = c.w * ib2 * rp2;
-    ph.sj = fmaf(fmaf(b.w, f, b.z), rE * rE, fmaf(c.y, f, c.x));
+    ph.sn = fmaf(c.y, f, c.x);
+    ph.sj = fmaf(fmaf(b.w, f, b.z), rE * rE, ph.sn);
+    ph.k = k;
+    ph.f = f;
     return ph;
+}
+
+// Primitive of the hydrogen (Mott) Coulomb law in the forward variable s = 1 - mu:
+// G = 2 mu/(1-mu^2) - sin(eta ln((1+mu)/(1-mu)))/(2 eta).
+__device__ __forceinline__ float mott_prim(float s, float eta) {
+    float L = __logf((2.f - s) / s);
+    return __fdividef(2.f * (1.f - s), s * (2.f - s)) - __fdividef(__sinf(eta * L), 2.f * eta);
+}
+
+// 1 - cos(theta_c) of the variable cut-off theta_c^2 = th2 (clamped to [1e-4, 1] rad as the
+// oracle does); a series below theta_c^2 = 0.01, where 1 - cosf would lose digits.
+__device__ __forceinline__ float cut_s(float th2) {
+    th2 = fminf(fmaxf(th2, 1e-8f), 1.f);
+    if (th2 < 0.01f) return 0.5f * th2 * (1.f - th2 * (1.f / 12.f) * (1.f - th2 * (1.f / 30.f)));
+    return 1.f - cosf(sqrtf(th2));
+}
+
+// Large-angle elastic rate x Delta per unit density at cut-off s_c (Sec. 2.1.3, Eq.
+// large_elastic_cm and its hydrogen form): R (1/s_c - 1/2) + Hc G(s_c) - Hc G(mu_lo),
+// from the coefficient rows (times E^2).
+__device__ __forceinline__ float cut_rate(const KParams& P, int m, const Phys& ph, float E, float s_c) {
+    const float4* r = P.cut + ((size_t)m * P.N + ph.k) * 2;
+    float4 a = __ldg(r), b = __ldg(r + 1);
+    float R = fmaf(a.y, ph.f, a.x), Hc = fmaf(a.w, ph.f, a.z), Hlo = fmaf(b.y, ph.f, b.x);
+    float rate = R * (__fdividef(1.f, s_c) - 0.5f) - Hlo;
+    if (Hc > 0.f) {
+        float eta = (float)kFineStructure * rsqrtf(2.f * E / (float)kProtonMass);
+        rate = fmaf(Hc, mott_prim(s_c, eta), rate);
+    }
+    return rate * __fdividef(1.f, E * E);
 }
 
 // ------------------------------------------------------------ jump samplers
@@ -126,9 +161,12 @@ __device__ void cm_to_lab(float E, float Eout, bool elastic, float m2, float cc,
 
 // A large-angle event of Eq. Npi at pre-step energy E: pick channel and element
 // by rate, sample the CM angle, convert to the lab, rotate; non-elastic events
-// scale the post-loss energy E1 by (1-u).  Refreshes the exponential clock.
+// scale the post-loss energy E1 by (1-u).  Refreshes the exponential clock.  CUT:
+// the energy-dependent cut-off s_c = 1 - cos(theta_c) of this step (compiled
+// separately so that the fixed-cut-off kernel carries none of it).
+template <bool CUT>
 __device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1, float& ux, float& uy,
-                                    float& uz, float& tau, uint64_t h, uint32_t n) {
+                                    float& uz, float& tau, uint64_t h, uint32_t n, float s_c) {
     uint4 J = philox(P, n, kTagJumpA, h);
     const MatJump& mj = P.mats[m];
     int k;
@@ -137,9 +175,19 @@ __device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1,
     const float* r0 = P.jrates + ((size_t)m * P.N + k) * (2 * SDE_MAX_ELEMENTS);
     const float* r1 = r0 + 2 * SDE_MAX_ELEMENTS;
     const float rE2 = __fdividef(1.f, E * E);  // elastic rates are stored times E^2
+    const float eta_h = (float)kFineStructure * rsqrtf(2.f * E / (float)kProtonMass);
+    // The stored elastic rates are those of the fixed cut-off s_cut; with the variable
+    // cut-off s_c they scale by the ratio of the angular factors (Rutherford: 1/s - 1/2,
+    // hydrogen: G(s) - G(mu_lo)).
+    float scale_R = rE2, scale_H = rE2;
+    if (CUT) {
+        scale_R *= (__fdividef(1.f, s_c) - 0.5f) / P.ruth_span;
+        float glo = -mott_prim(P.s_back, eta_h);
+        scale_H *= (mott_prim(s_c, eta_h) - glo) / (mott_prim(P.s_cut, eta_h) - glo);
+    }
     float total = 0.f;
     for (int i = 0; i < mj.n_el; ++i) {
-        total += fmaf(r1[i] - r0[i], f, r0[i]) * rE2;
+        total += fmaf(r1[i] - r0[i], f, r0[i]) * (mj.Z[i] == 1 ? scale_H : scale_R);
         total += fmaf(r1[SDE_MAX_ELEMENTS + i] - r0[SDE_MAX_ELEMENTS + i], f, r0[SDE_MAX_ELEMENTS + i]);
     }
     float target = u01(J.x) * total, acc = 0.f;
@@ -147,7 +195,7 @@ __device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1,
     for (int ch = 0; ch < 2 && pick < 0; ++ch)
         for (int i = 0; i < mj.n_el; ++i) {
             int o = ch * SDE_MAX_ELEMENTS + i;
-            float rate = fmaf(r1[o] - r0[o], f, r0[o]) * (ch == 0 ? rE2 : 1.f);
+            float rate = fmaf(r1[o] - r0[o], f, r0[o]) * (ch == 0 ? (mj.Z[i] == 1 ? scale_H : scale_R) : 1.f);
             if (rate <= 0.f) continue;
             last = o;
             acc += rate;
@@ -164,10 +212,10 @@ __device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1,
     float cc, sc, cl, sl;
     if (elastic) {
         if (mj.Z[el] == 1) {
-            float eta = (float)kFineStructure * rsqrtf(2.f * E / (float)kProtonMass);
-            mott_sample(u01(J.y), eta, P.s_cut, P.s_back, cc, sc);
+            mott_sample(u01(J.y), eta_h, CUT ? s_c : P.s_cut, P.s_back, cc, sc);
         } else {
-            float s = 1.f / (0.5f + u01(J.y) * P.ruth_span);
+            float span = CUT ? __fdividef(1.f, s_c) - 0.5f : P.ruth_span;
+            float s = 1.f / (0.5f + u01(J.y) * span);
             cc = 1.f - s;
             sc = sqrtf(s * (2.f - s));
         }
@@ -195,6 +243,7 @@ __device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1,
 // exponential: tau ~ Exp(1) is spent at rate sigma per unit path; crossing zero
 // within a step is the step's jump, which has probability 1 - exp(-Delta sigma)
 // as in the paper.  Switched-off terms are multiplied by zero (no branches).
+template <bool CUT>
 __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int m, float rho, uint4 x,
                                         float& E, float& ux, float& uy, float& uz, float& tau, uint64_t h,
                                         uint32_t n, float& E1_out) {
@@ -216,7 +265,8 @@ __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int
         g = __fdividef(1.f + w, w) * log1pf(w) - 1.f;
     else
         g = w * (0.5f + w * (-1.f / 6.f + w * (1.f / 12.f)));
-    float t = rho * ph.tg * g * P.mcs_on;
+    const float t_raw = rho * ph.tg * g;  // sigma^2 Delta / z, whether or not scattering is on
+    float t = t_raw * P.mcs_on;
     float th2 = -2.f * t * __logf(u01(x.z));
     float ct, st;
     cos_sin_from_sq(th2, ct, st);
@@ -225,8 +275,13 @@ __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int
     rotate(ux, uy, uz, ct, st, cp, sp);
     E1_out = E1;
     int jump = 0;
-    tau -= rho * ph.sj;
-    if (tau <= 0.f) jump = do_jump(P, m, E, E1, ux, uy, uz, tau, h, n);
+    float sj = ph.sj, s_c = P.s_cut;
+    if (CUT) {  // variable cut-off theta_c = k sigma(E): theta_c^2 = k^2 (z/Delta) t
+        s_c = cut_s(P.cut_k2 * t_raw);
+        sj = cut_rate(P, m, ph, E, s_c) + ph.sn;
+    }
+    tau -= rho * sj;
+    if (tau <= 0.f) jump = do_jump<CUT>(P, m, E, E1, ux, uy, uz, tau, h, n, s_c);
     E = E1;
     return jump;
 }
@@ -347,7 +402,7 @@ __device__ unsigned long long deposit_chord(const KParams& P, float ax, float ay
 // deposited total is the sum of the tally, reduced when the balance is read.
 #define SDE_BLOCK_ADD(idx, v) atomicAdd(&s_cnt[idx], (unsigned long long)(v))
 
-template <int TALLY, bool SMEM, bool AGG>
+template <int TALLY, bool SMEM, bool AGG, bool CUT>
 __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
     extern __shared__ float4 s_tab[];
     __shared__ unsigned long long s_cnt[kCntWords];
@@ -430,7 +485,7 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
         x = philox(P, n + 1u, kTagStep, h);
         const unsigned long long q0 = qfix(P, E);
         float E1;
-        int jump = sde_step(P, tab, m, rho, xcur, E, ux, uy, uz, tau, h, n, E1);
+        int jump = sde_step<CUT>(P, tab, m, rho, xcur, E, ux, uy, uz, tau, h, n, E1);
         unsigned long long q1 = qfix(P, E1);
         unsigned long long dq = q0 - q1;
         if (TALLY == 0) {
@@ -572,7 +627,9 @@ __global__ void k_probe(KParams P, int m, float rho, float E0, uint64_t h0, int 
     uint4 B = philox(P, 0u, kTagSrcB, h);
     float tau = -__logf(u01(B.z));
     float E = E0, ux = 0.f, uy = 0.f, uz = 1.f, E1;
-    int j = sde_step(P, P.table, m, rho, philox(P, 0u, kTagStep, h), E, ux, uy, uz, tau, h, 0u, E1);
+    int j = P.cut_k2 > 0.f
+                ? sde_step<true>(P, P.table, m, rho, philox(P, 0u, kTagStep, h), E, ux, uy, uz, tau, h, 0u, E1)
+                : sde_step<false>(P, P.table, m, rho, philox(P, 0u, kTagStep, h), E, ux, uy, uz, tau, h, 0u, E1);
     Eo[i] = E;
     co[i] = uz;
     jo[i] = j;
@@ -591,57 +648,68 @@ __global__ void k_convert(const unsigned long long* edep, const float* rho, size
 }
 
 // ---------------------------------------------------------------- launchers
-template <int TALLY, bool SMEM, bool AGG>
+template <int TALLY, bool SMEM, bool AGG, bool CUT>
 static cudaError_t allow_smem(size_t smem) {
     if (!SMEM) return cudaSuccess;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG, CUT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
 #ifdef SDE_SMEM_CARVEOUT
-    e = cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG, CUT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              SDE_SMEM_CARVEOUT);
 #endif
     return e;
 }
 
-template <int TALLY, bool SMEM, bool AGG>
+template <int TALLY, bool SMEM, bool AGG, bool CUT>
 static cudaError_t launch_t(const KParams& P, int grid, int block, size_t smem, cudaStream_t st) {
-    cudaError_t e = allow_smem<TALLY, SMEM, AGG>(smem);
+    cudaError_t e = allow_smem<TALLY, SMEM, AGG, CUT>(smem);
     if (e != cudaSuccess) return e;
-    k_transport<TALLY, SMEM, AGG><<<grid, block, SMEM ? smem : 0, st>>>(P);
+    k_transport<TALLY, SMEM, AGG, CUT><<<grid, block, SMEM ? smem : 0, st>>>(P);
     return cudaGetLastError();
 }
 
-template <int TALLY, bool SMEM, bool AGG>
+template <int TALLY, bool SMEM, bool AGG, bool CUT>
 static int blocks_per_sm_t(int block, size_t smem) {
-    if (allow_smem<TALLY, SMEM, AGG>(smem) != cudaSuccess) return 0;
+    if (allow_smem<TALLY, SMEM, AGG, CUT>(smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<TALLY, SMEM, AGG>, block,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<TALLY, SMEM, AGG, CUT>, block,
                                                       SMEM ? smem : 0) != cudaSuccess)
         return 0;
     return nb;
 }
 
 // Variant selection: tally mode (midpoint, chord), table placement, and warp
-// aggregation of the midpoint tally.
+// aggregation of the tally; the energy-dependent cut-off has its own kernels (midpoint
+// or chord tally, tables through L1, per-lane atomics) so that the fixed-cut-off ones
+// carry none of its arithmetic.
 cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_table, bool use_smem,
                              cudaStream_t st) {
+    if (P.cut_k2 > 0.f)
+        return P.tally_mode == 1 ? launch_t<1, false, false, true>(P, grid, block, 0, st)
+                                 : launch_t<0, false, false, true>(P, grid, block, 0, st);
     if (P.tally_mode == 1)
-        return use_smem ? launch_t<1, true, false>(P, grid, block, smem_table, st)
-                        : launch_t<1, false, false>(P, grid, block, 0, st);
+        return use_smem ? launch_t<1, true, false, false>(P, grid, block, smem_table, st)
+                        : launch_t<1, false, false, false>(P, grid, block, 0, st);
     if (P.aggregate)
-        return use_smem ? launch_t<0, true, true>(P, grid, block, smem_table, st)
-                        : launch_t<0, false, true>(P, grid, block, 0, st);
-    return use_smem ? launch_t<0, true, false>(P, grid, block, smem_table, st)
-                    : launch_t<0, false, false>(P, grid, block, 0, st);
+        return use_smem ? launch_t<0, true, true, false>(P, grid, block, smem_table, st)
+                        : launch_t<0, false, true, false>(P, grid, block, 0, st);
+    return use_smem ? launch_t<0, true, false, false>(P, grid, block, smem_table, st)
+                    : launch_t<0, false, false, false>(P, grid, block, 0, st);
 }
 
-int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode, bool aggregate) {
+int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode, bool aggregate, bool cut) {
+    if (cut)
+        return tally_mode == 1 ? blocks_per_sm_t<1, false, false, true>(block, 0)
+                               : blocks_per_sm_t<0, false, false, true>(block, 0);
     if (tally_mode == 1)
-        return use_smem ? blocks_per_sm_t<1, true, false>(block, smem) : blocks_per_sm_t<1, false, false>(block, 0);
+        return use_smem ? blocks_per_sm_t<1, true, false, false>(block, smem)
+                        : blocks_per_sm_t<1, false, false, false>(block, 0);
     if (aggregate)
-        return use_smem ? blocks_per_sm_t<0, true, true>(block, smem) : blocks_per_sm_t<0, false, true>(block, 0);
-    return use_smem ? blocks_per_sm_t<0, true, false>(block, smem) : blocks_per_sm_t<0, false, false>(block, 0);
+        return use_smem ? blocks_per_sm_t<0, true, true, false>(block, smem)
+                        : blocks_per_sm_t<0, false, true, false>(block, 0);
+    return use_smem ? blocks_per_sm_t<0, true, false, false>(block, smem)
+                    : blocks_per_sm_t<0, false, false, false>(block, 0);
 }
 
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,

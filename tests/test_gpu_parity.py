@@ -95,12 +95,14 @@ def test_water100_at_its_stated_size(sde_gpu, oracle_lib):
     assert abs(b1["incident"] - bo["incident"]) / bo["incident"] < 1e-9 + 1e-6
 
 
-def test_water100_common_random_numbers(sde_gpu, oracle_lib):
+@pytest.mark.parametrize("cut_k", [0.0, 2.5])
+def test_water100_common_random_numbers(sde_gpu, oracle_lib, cut_k):
     """With the oracle on the exponential jump clock both sides draw identical numbers for
-    every history; the tallies then agree far more tightly than independent runs."""
+    every history; the tallies then agree far more tightly than independent runs.  Also
+    with the energy-dependent cut-off theta_c = 2.5 sigma(E) (Sec. 2.1.3)."""
     wl = water100(20_000)
-    _, eg, bg = sde_gpu.run_workload(wl, seed=3)
-    _, eo, bo = O.run_workload(wl, seed=3, jump_clock=1)
+    _, eg, bg = sde_gpu.run_workload(wl, seed=3, theta_cut_sigmas=cut_k)
+    _, eo, bo = O.run_workload(wl, seed=3, jump_clock=1, theta_cut_sigmas=cut_k)
     ig, io = A.idd(eg.astype(float)), A.idd(eo.astype(float))
     assert np.max(np.abs(ig - io)) / io.max() < 0.01
     assert abs(bg["jumps_inelastic"] - bo["jumps_inelastic"]) <= 0.01 * bo["jumps_inelastic"] + 5

@@ -42,15 +42,16 @@ def test_tables_equal_the_oracle_at_grid_points(sde_gpu, oracle_lib, mat_index):
             assert t["csda"][k] == pytest.approx(O.csda_range(mat, 1.0, E), rel=1e-8)
 
 
-def test_probe_step_follows_the_oracle_on_common_random_numbers(sde_gpu, oracle_lib):
+@pytest.mark.parametrize("cut_k", [0.0, 2.5])
+def test_probe_step_follows_the_oracle_on_common_random_numbers(sde_gpu, oracle_lib, cut_k):
     """Same (seed, history, step) keys, same draw layout, exponential clock in both: the
     GPU step (FP32 tables) and the oracle step (FP64 formulas) give nearly the same
-    sample, history by history."""
+    sample, history by history -- with the fixed cut-off and with theta_c = 2.5 sigma(E)."""
     n = 100_000
-    with sde_gpu.SdeDose(_tiny([WATER])) as d:
+    with sde_gpu.SdeDose(_tiny([WATER]), theta_cut_sigmas=cut_k) as d:
         for E in (150.0, 12.0):
             g = d.probe_steps(0, 1.0, E, n, seed=42, h0=1000)
-            o = O.single_step(WATER, 1.0, E, n, seed=42, h0=1000, jump_clock=1)
+            o = O.single_step(WATER, 1.0, E, n, seed=42, h0=1000, jump_clock=1, theta_cut_sigmas=cut_k)
             same_jump = g["jump"] == o["jump"]
             assert same_jump.mean() > 0.999
             nj = same_jump & (o["jump"] == 0)

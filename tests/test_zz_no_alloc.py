@@ -23,11 +23,11 @@ def _packed_voxels(wl):
     return ((bits + np.uint32(8)) & np.uint32(0xFFFFFFF0)) | mid
 
 
-def _call(S, wl, vox, spots, out, seed, bal=None, n_spots=None, mats=None):
+def _call(S, wl, vox, spots, out, seed, bal=None, n_spots=None, mats=None, **param_kw):
     L = S.lib()
     nx, ny, nz = wl.shape
     m = S._Materials(wl.materials if mats is None else mats)
-    p = S.default_params()
+    p = S.default_params(**param_kw)
     return L.sde_transport_noalloc(nx, ny, nz, (C.c_double * 3)(*wl.voxel_mm), (C.c_double * 3)(*wl.origin_mm),
                                    vox.data_ptr(), m.arr, len(m._keep), C.byref(p), spots.data_ptr(),
                                    len(wl.spots) if n_spots is None else n_spots, C.c_uint64(seed),
@@ -66,4 +66,6 @@ def test_noalloc_rejects_inputs_beyond_its_scratch_limits(sde_gpu):
     assert rc == S.SDE_EINVAL and "4096" in S.lib().sde_last_error().decode()
     rc = _call(S, wl, vox, spots, out, 0, n_spots=1, mats=[wl.materials[0]] * 5)
     assert rc == S.SDE_EINVAL and "n_mats" in S.lib().sde_last_error().decode()
+    rc = _call(S, wl, vox, spots, out, 0, n_spots=1, theta_cut_sigmas=2.5)  # needs a handle's tables
+    assert rc == S.SDE_EINVAL and "cut-off" in S.lib().sde_last_error().decode()
     assert int(out.abs().sum()) == 0
