@@ -43,6 +43,8 @@ LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per cl
 # same launch configuration; None until captured for the current kernel.
 TRANSPORT_DRAM_BYTES = 422_050_000  # 92.92 MB read + 329.13 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
 
+CT_DESC = ("ct_sobp: thorax-like synthetic CT 120x120x240 mm at 1 mm (air, lung, adipose, soft tissue, "
+           "cortical bone from HU), 16-layer spread-out Bragg peak 90-140 mm, 256 spots, 1e6 protons per GPU")
 WORKLOAD_DESC = ("slab150: 150 MeV pencil beam (sigma_xy 3 mm), 1e6 protons per GPU, "
                  "60x60x200 mm at 0.5 mm (120x120x400 voxels), water/bone-like/lung-like/water slabs")
 
@@ -325,6 +327,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-histories", type=int, default=20_000)
+    ap.add_argument("--workload", default="slab150", choices=["slab150", "ct_sobp"],
+                    help="slab150 (default) or ct_sobp: thorax-like synthetic CT with a 16-layer spread-out Bragg peak")
     ap.add_argument("--theta-cut-sigmas", type=float, default=0.0,
                     help="energy-dependent elastic cut-off theta_c = k sigma(E) (0: the paper's fixed 0.02 rad)")
     ap.add_argument("--no-denoiser", action="store_true",
@@ -338,7 +342,7 @@ def main():
 
     import torch
     import paper_2511_03115_gb300 as S
-    from sde_workloads import slab150
+    from sde_workloads import ct_sobp, slab150
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -346,7 +350,8 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = slab150(args.histories * ws)  # one plan; this rank runs its shard of the history ids
+    # one plan; this rank runs its shard of the history ids
+    wl = (ct_sobp if args.workload == "ct_sobp" else slab150)(args.histories * ws)
     first, count = S.history_shard(wl.n_histories, rank, ws)
     stream = torch.cuda.Stream(device=dev)
     d = S.SdeDose(wl, stream=stream, theta_cut_sigmas=args.theta_cut_sigmas)
@@ -454,7 +459,8 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "histories_per_step": hist_per_step,
+        "config": {"workload": WORKLOAD_DESC if args.workload == "slab150" else CT_DESC,
+                   "histories_per_step": hist_per_step,
                    "split": f"history ids {first}..{first + count - 1} of {wl.n_histories} on rank {rank}",
                    "euler_steps_per_launch": steps_per_launch, "parallelism": f"replicas x{ws}",
                    "l2": "flushed (256 MB write) before every timed step", "tally": "int64 fixed point 2^-24 MeV",

@@ -23,8 +23,14 @@ Workloads (all synthetic, generated from a seed; no dataset is involved):
   remainder, total 10^8), 200 x 200 x 300 mm at 1 mm, water with 30 random
   spheres (radius U(5,25) mm, density U(0.2,1.9) g/cm^3, tissue or bone).
 
+* ``ct_sobp``    - thorax-like synthetic CT, 120 x 120 x 240 mm at 1 mm (HU -> density by
+  a piecewise-linear calibration, HU bins -> air / lung / adipose / soft tissue /
+  cortical bone), spread-out Bragg peak of 16 layers (ranges 90-140 mm in water).
+* ``sobp_water`` - the same spread-out Bragg peak in water.
+
 The paper's own test geometries (Sec. 2.2.2: 20 cm water cube, slab and
-insert phantoms with 1 mm voxels) inform these shapes.
+insert phantoms with 1 mm voxels) inform these shapes; its conclusion names patient
+CT geometries and spread-out Bragg peaks as the next validation step.
 """
 from __future__ import annotations
 
@@ -241,5 +247,132 @@ def denoise_case(seed: int, n_hist: int = 100_000, shape=(128, 128, 192), n_spot
                     seed=seed)
 
 
+# ---------------------------------------------------------------------------
+# CT-like phantoms and spread-out Bragg peaks (synthetic; no patient data).
+# Tissue compositions: ICRU Report 44 mass fractions, restricted to elements above
+# 0.1 % (each side renormalises); air: dry air at sea level.
+AIR = {"name": "air", "elements": [(6, 0.000124), (7, 0.755268), (8, 0.231781), (18, 0.012827)],
+       "I_eV": 85.7}
+LUNG = {"name": "lung", "elements": [(1, 0.103), (6, 0.105), (7, 0.031), (8, 0.749), (11, 0.002), (15, 0.002),
+                                     (16, 0.003), (17, 0.003), (19, 0.002)], "I_eV": 0.0}
+ADIPOSE = {"name": "adipose", "elements": [(1, 0.114), (6, 0.598), (7, 0.007), (8, 0.278), (11, 0.001),
+                                           (16, 0.001), (17, 0.001)], "I_eV": 0.0}
+SOFT = {"name": "soft tissue", "elements": [(1, 0.102), (6, 0.143), (7, 0.034), (8, 0.708), (11, 0.002),
+                                            (15, 0.003), (16, 0.003), (17, 0.002), (19, 0.003)], "I_eV": 0.0}
+CORTICAL = {"name": "cortical bone", "elements": [(1, 0.034), (6, 0.155), (7, 0.042), (8, 0.435), (11, 0.001),
+                                                  (12, 0.002), (15, 0.103), (16, 0.003), (20, 0.225)], "I_eV": 0.0}
+CT_MATERIALS = [AIR, LUNG, ADIPOSE, SOFT, CORTICAL]
+# upper HU bound of each material bin (air < -900 <= lung < -200 <= adipose < -30 <= soft < 150 <= bone)
+CT_HU_BINS = (-900.0, -200.0, -30.0, 150.0)
+
+
+def hu_to_density(hu):
+    """Piecewise-linear CT calibration (g/cm^3): 1 + HU/1000 below water (air at -1000,
+    floored at 0.0012) and 1 + 0.00058 HU above it (cortical bone ~1.9 at 1500 HU)."""
+    hu = np.asarray(hu, dtype=np.float64)
+    rho = np.where(hu <= 0.0, 1.0 + hu / 1000.0, 1.0 + 0.00058 * hu)
+    return np.maximum(rho, 0.0012).astype(np.float32)
+
+
+def hu_to_material(hu):
+    """Material id by HU bin (index into CT_MATERIALS)."""
+    return np.searchsorted(np.asarray(CT_HU_BINS), np.asarray(hu, dtype=np.float64), side="right").astype(np.uint8)
+
+
+def thorax_hu(shape=(120, 120, 240), h=1.0, seed=0):
+    """A thorax-like HU volume (nz, ny, nx), beam axis along +z: an elliptic body (adipose
+    shell 6 mm, soft tissue), two lungs with an airway between them, a rib layer in
+    front of the lungs, a spine behind the mediastinum, air outside and in front of the
+    skin; HU noise sigma 12 (seeded)."""
+    nx, ny, nz = shape
+    _, xc, yc, zc = _grid(nx, ny, nz, h)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xC7]))
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    hu = np.full((nz, ny, nx), -1000.0)
+    zb0, zb1 = 8.0, nz * h - 8.0                      # body extent along the beam
+    rx, ry = 0.47 * nx * h, 0.45 * ny * h             # body ellipse (x-y)
+    body = ((X / rx) ** 2 + (Y / ry) ** 2 <= 1.0) & (Z >= zb0) & (Z < zb1)
+    hu[body] = 40.0
+    skin = body & (((X / (rx - 6)) ** 2 + (Y / (ry - 6)) ** 2 > 1.0) | (Z < zb0 + 6) | (Z >= zb1 - 6))
+    hu[skin] = -90.0
+    ribs = body & (Z >= zb0 + 14) & (Z < zb0 + 22) & (np.abs(np.sin(Y / 6.0)) > 0.3)
+    hu[ribs] = 800.0
+    for sx in (-1.0, 1.0):                             # lungs
+        lung = body & (((X - sx * 0.22 * nx * h) / (0.18 * nx * h)) ** 2 + (Y / (0.33 * ny * h)) ** 2 +
+                       ((Z - 0.45 * nz * h) / (0.25 * nz * h)) ** 2 <= 1.0)
+        hu[lung] = -780.0
+    airway = body & (X ** 2 + (Y - 0.05 * ny * h) ** 2 <= 7.0 ** 2) & (Z >= 0.3 * nz * h) & (Z < 0.6 * nz * h)
+    hu[airway] = -980.0
+    spine = body & (X ** 2 + ((Y + 0.0 * ny * h) ** 2) <= 14.0 ** 2) & (Z >= 0.7 * nz * h) & (Z < 0.85 * nz * h)
+    hu[spine] = 1100.0
+    tumour = body & ((X - 0.2 * nx * h) ** 2 + Y ** 2 + (Z - 0.42 * nz * h) ** 2 <= 12.0 ** 2)
+    hu[tumour] = 45.0
+    hu[body] += rng.normal(0.0, 12.0, int(body.sum()))
+    return hu
+
+
+def bragg_kleeman_energy(range_mm, alpha=0.0022, p=1.77):
+    """Energy (MeV) whose CSDA range in water is range_mm by the Bragg-Kleeman rule
+    R = alpha E^p (R in cm)."""
+    return (np.asarray(range_mm, dtype=np.float64) / 10.0 / alpha) ** (1.0 / p)
+
+
+def sobp_layer_weights(r_lo_mm, r_hi_mm, n_layers, p=1.77):
+    """Relative fluence of n equally spaced range layers for a flat spread-out Bragg peak
+    over [r_lo, r_hi] (Bortfeld & Schlegel 1996): with pristine curves ~ (R - z)^(1/p - 1)
+    the flat superposition has weight density w(R) ~ (R_max - R)^(-1/p); each layer gets
+    the integral of w over its range bin (the deepest bin ends at R_max)."""
+    R = np.linspace(r_lo_mm, r_hi_mm, n_layers)
+    dR = (r_hi_mm - r_lo_mm) / (n_layers - 1)
+    lo = np.maximum(R - dR / 2.0, r_lo_mm - dR / 2.0)
+    hi = np.minimum(R + dR / 2.0, r_hi_mm)
+    q = 1.0 - 1.0 / p
+    w = ((r_hi_mm - lo) ** q - (r_hi_mm - hi) ** q) / q
+    return R, w / w.sum()
+
+
+def sobp_spots(total, r_lo_mm, r_hi_mm, n_layers=16, x_mm=0.0, y_mm=0.0, half_width_mm=10.0, pitch_mm=5.0,
+               sigma_xy_mm=3.0, energy_spread=0.008):
+    """A spread-out Bragg peak: n_layers energies (Bragg-Kleeman) for ranges r_lo..r_hi in
+    water, spaced closer than a pristine peak's width, energy spread 0.8 % (sigma), layer
+    fluences by the Bortfeld-Schlegel weighting, each layer a square grid of Gaussian
+    spots (sigma_xy) of side 2 half_width centred on (x, y); histories by largest
+    remainder."""
+    R, w = sobp_layer_weights(r_lo_mm, r_hi_mm, n_layers)
+    E = bragg_kleeman_energy(R)
+    g = np.arange(-half_width_mm + pitch_mm / 2.0, half_width_mm, pitch_mm)
+    gx, gy = np.meshgrid(g, g, indexing="xy")
+    n_grid = gx.size
+    spots = np.zeros(n_layers * n_grid, SPOT_DTYPE)
+    spots["E_MeV"] = np.repeat(E, n_grid)
+    spots["sigma_E_MeV"] = energy_spread * spots["E_MeV"]
+    spots["x_mm"] = np.tile(gx.ravel(), n_layers) + x_mm
+    spots["y_mm"] = np.tile(gy.ravel(), n_layers) + y_mm
+    spots["uz"] = 1.0
+    spots["sigma_xy_mm"] = sigma_xy_mm
+    spots["n_hist"] = largest_remainder(np.repeat(w / n_grid, n_grid), total)
+    return spots
+
+
+def ct_sobp(n_hist: int = 1_000_000, seed: int = 0, shape=(120, 120, 240), h: float = 1.0) -> Workload:
+    """Thorax-like CT phantom (HU -> density and one of five ICRU 44 materials) irradiated by
+    a spread-out Bragg peak, 16 layers covering ranges 90-140 mm in water, 20 x 20 mm
+    field of 5 mm-spaced Gaussian spots aimed at the tumour insert."""
+    nx, ny, nz = shape
+    origin, *_ = _grid(nx, ny, nz, h)
+    hu = thorax_hu(shape, h, seed)
+    spots = sobp_spots(n_hist, 90.0, 140.0, x_mm=0.2 * nx * h)
+    return Workload(f"ct_sobp{seed}", shape, (h, h, h), origin, hu_to_density(hu), hu_to_material(hu),
+                    list(CT_MATERIALS), spots, seed=seed, notes={"hu": hu})
+
+
+def sobp_water(n_hist: int = 1_000_000) -> Workload:
+    """The same spread-out Bragg peak in water (80 x 80 x 200 mm at 1 mm), for its flatness."""
+    nx, ny, nz, h = 80, 80, 200, 1.0
+    origin, *_ = _grid(nx, ny, nz, h)
+    return Workload("sobp_water", (nx, ny, nz), (h, h, h), origin, np.ones((nz, ny, nx), np.float32),
+                    np.zeros((nz, ny, nx), np.uint8), [WATER], sobp_spots(n_hist, 90.0, 140.0))
+
+
 WORKLOADS = {"water100": water100, "slab150": slab150, "insert150": insert150,
-             "plan2000": plan2000, "denoise_case": denoise_case}
+             "plan2000": plan2000, "denoise_case": denoise_case, "ct_sobp": ct_sobp, "sobp_water": sobp_water}
