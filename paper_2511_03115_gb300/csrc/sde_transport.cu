@@ -406,7 +406,11 @@ template <int TALLY, bool SMEM, bool AGG, bool CUT>
 __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
     extern __shared__ float4 s_tab[];
     __shared__ unsigned long long s_cnt[kCntWords];
+    // The warp's current batch of history ids [next, end) is warp-uniform: it lives in
+    // shared memory, not in four registers of every lane.
+    __shared__ unsigned long long s_batch[2 * kMaxWarpsPerBlock];
     if (threadIdx.x < kCntWords) s_cnt[threadIdx.x] = 0ull;
+    if (threadIdx.x < 2 * kMaxWarpsPerBlock) s_batch[threadIdx.x] = 0ull;
     const float4* tab = P.table;
     if (SMEM) {
         int rows = P.n_mats * P.N * kRowFloat4;
@@ -425,14 +429,15 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
     uint32_t vox = 0;
     int vcur = -1;
     uint4 x = make_uint4(0u, 0u, 0u, 0u);
-    uint32_t a_steps = 0;
-    unsigned long long b_next = 0, b_end = 0;
+    unsigned long long* const s_next = &s_batch[2 * (threadIdx.x >> 5)];
+    unsigned long long* const s_end = s_next + 1;
     bool drained = false;
 
     for (;;) {
         unsigned dead = __ballot_sync(0xffffffffu, !alive);
         if (dead != 0xffffffffu && __popc(dead) < P.refill_min) dead = 0;  // refill later
         while (dead && !drained) {
+            unsigned long long b_next = *s_next, b_end = *s_end;
             if (b_next >= b_end) {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(&P.counters[kCntCursor], (unsigned long long)P.batch);
@@ -460,6 +465,12 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
                 x = philox(P, 0u, kTagStep, h);
             }
             b_next += (unsigned long long)take;
+            __syncwarp();
+            if (lane == 0) {
+                *s_next = b_next;
+                *s_end = b_end;
+            }
+            __syncwarp();
             dead = __ballot_sync(0xffffffffu, !alive);
         }
         if (!__any_sync(0xffffffffu, alive)) break;
@@ -468,6 +479,7 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
         if (n >= (uint32_t)P.max_steps || vcur < 0) {  // step cap, or R_n outside the domain D
             if (n >= (uint32_t)P.max_steps) atomicOr(P.err, kErrStepCap);
             SDE_BLOCK_ADD(kCntEscaped, qfix(P, E));
+            SDE_BLOCK_ADD(kCntSteps, n);
             alive = false;
             continue;
         }
@@ -521,7 +533,6 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
             }
         }
         n += 1;
-        a_steps += 1;
         vcur = vnext;
         vox = vox_next;
         if (E < P.e_min) {  // absorbed; the rest is deposited where the proton is
@@ -532,12 +543,11 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
                 else
                     SDE_BLOCK_ADD(kCntEscaped, qr);
             }
+            SDE_BLOCK_ADD(kCntSteps, n);  // the history's steps, counted once at its end
             alive = false;
         }
     }
 
-    for (int off = 16; off > 0; off >>= 1) a_steps += __shfl_down_sync(0xffffffffu, a_steps, off);
-    if (lane == 0) SDE_BLOCK_ADD(kCntSteps, a_steps);
     __syncthreads();
     if (threadIdx.x < kCntWords && threadIdx.x != kCntCursor && threadIdx.x != kCntDeposited &&
         s_cnt[threadIdx.x])
