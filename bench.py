@@ -41,7 +41,7 @@ SMS = 152
 LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per clock each
 # DRAM traffic (read + write bytes) per transport launch from the ncu capture of the
 # same launch configuration; None until captured for the current kernel.
-TRANSPORT_DRAM_BYTES = 422_050_000  # 92.92 MB read + 329.13 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
+TRANSPORT_DRAM_BYTES = 318_644_480  # 84.13 MB read + 234.52 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
 
 CT_DESC = ("ct_sobp: thorax-like synthetic CT 120x120x240 mm at 1 mm (air, lung, adipose, soft tissue, "
            "cortical bone from HU), 16-layer spread-out Bragg peak 90-140 mm, 256 spots, 1e6 protons per GPU")
@@ -126,7 +126,7 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(target_s: float = 12.0):
+def cpu_baseline(target_s: float = 25.0):
     """The oracle as it stands on the host cores, on a bounded sample of the workload."""
     import oracle
     from sde_workloads import slab150
