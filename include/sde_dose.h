@@ -271,17 +271,18 @@ int sde_gemm_bf16(const void* d_A, const void* d_B, float* d_D, int M, int N, in
  * v = (z*H + y)*W + x, tap = 9 kz + 3 ky + kx, off = (kz-1, ky-1, kx-1).  d_x [batch][D*H*W][Cin],
  * d_w [Cout][27][Cin] BF16, d_bias [Cout] FP32 or NULL; y rows have y_cstride channels
  * (BF16, or FP32 when y_fp32 != 0), written at channel offset y_coffset (so two
- * producers can fill the halves of a concatenation).  Requires D*H*W a multiple of
- * 128, Cin a multiple of 16 in [16, 192], Cout a multiple of 16 in [16, 256].  The
- * data gradient of the convolution is this call on dy with the weights of
- * sde_conv3d_flip_weights.  Asynchronous; sde_denoise_status reports a timed-out wait. */
+ * producers can fill the halves of a concatenation).  Requires W <= 256, D*H*W a
+ * multiple of 128, Cin a multiple of 16 in [16, 192], Cout a multiple of 16 in
+ * [16, 256] (SDE_EINVAL otherwise).  The data gradient of the convolution is this call
+ * on dy with the weights of sde_conv3d_flip_weights.  Asynchronous;
+ * sde_denoise_status reports a timed-out wait. */
 int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int W, int Cin, const void* d_w,
                        const float* d_bias, int Cout, void* d_y, int y_cstride, int y_coffset, int y_fp32,
                        int relu, void* stream);
 
 /* Weight gradient of sde_conv3d_forward: d_dw[co][tap][ci] += sum over voxels of
- * dy[v][co] x[v + off(tap)][ci] (FP32 accumulation into d_dw; BF16 d_x, d_dy; Cout <= 128).
- * Asynchronous. */
+ * dy[v][co] x[v + off(tap)][ci] (FP32 accumulation into d_dw; BF16 d_x, d_dy; Cout <= 128;
+ * shape limits as sde_conv3d_forward).  Asynchronous. */
 int sde_conv3d_wgrad(const void* d_x, const void* d_dy, float* d_dw, int batch, int D, int H, int W, int Cin,
                      int Cout, void* stream);
 

@@ -178,121 +178,12 @@ extern "C" int sde_gemm_bf16(const void* d_A, const void* d_B, float* d_D, int M
 }
 
 // ============================================================================
-// 3D convolution (3x3x3, stride 1, zero padding 1) as an implicit GEMM.
-// Activations are channels-last BF16: x[n][z][y][x][c].  Weights w[co][tap][ci]
-// (tap = 9 kz + 3 ky + kx).  GEMM: rows = 128 output voxels of one sample,
-// columns = output channels, K = 27 taps x Cin.
+// 3D convolution (3x3x3, stride 1, zero padding 1) as implicit GEMMs on the tensor
+// core.  Activations are channels-last BF16: x[n][z][y][x][c].  Weights w[co][tap][ci]
+// (tap = 9 kz + 3 ky + kx).
 // ============================================================================
 namespace sde {
 namespace {
-
-__global__ void __launch_bounds__(128) k_conv3d(ConvArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int Cin = a.Cin, Cout = a.Cout, q8 = Cin >> 3;
-    const int a_bytes = 128 * Cin * 2, b_bytes = Cout * Cin * 2;
-    unsigned char* sA[2] = {smem, smem + a_bytes + b_bytes};
-    unsigned char* sB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * (a_bytes + b_bytes));
-    uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 2);
-    const long long tile0 = (long long)blockIdx.x * 128;
-    const int n = (int)(tile0 / a.nvox);
-    const int v = (int)(tile0 - (long long)n * a.nvox) + tid;  // this thread's output voxel
-    const int HW = a.H * a.W;
-    const int z = v / HW, y = (v / a.W) % a.H, xq = v % a.W;
-    const __nv_bfloat16* xin = a.x + (size_t)n * a.nvox * Cin;
-    const uint32_t ncols = Cout <= 32 ? 32u : Cout <= 64 ? 64u : Cout <= 128 ? 128u : 256u;
-    if (warp == 0) {
-        umma::tmem_alloc(slot, ncols);
-        umma::tmem_relinquish();
-    }
-    if (tid == 0) {
-        umma::mbar_init(&mbar[0], 1);
-        umma::mbar_init(&mbar[1], 1);
-    }
-    auto load = [&](int tap, int s) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const int zz = z + dz, yy = y + dy, xx = xq + dx;
-        const bool in = (unsigned)zz < (unsigned)a.D && (unsigned)yy < (unsigned)a.H && (unsigned)xx < (unsigned)a.W;
-        const __nv_bfloat16* src = in ? xin + ((size_t)(zz * a.H + yy) * a.W + xx) * Cin : xin;
-        const uint32_t dst = umma::smem_addr(sA[s]) + (uint32_t)((tid >> 3) * q8) * 128u + (uint32_t)(tid & 7) * 16u;
-        for (int q = 0; q < q8; ++q) umma::cp_async16(dst + q * 128, src + q * 8, in ? 16u : 0u);
-        const uint32_t bdst = umma::smem_addr(sB[s]);
-        for (int c = tid; c < Cout * q8; c += 128) {
-            const int co = c / q8, q = c - co * q8;
-            umma::cp_async16(bdst + umma::core_offset(co, q * 8, Cin), a.w + ((size_t)co * 27 + tap) * Cin + q * 8, 16u);
-        }
-        umma::cp_async_commit();
-    };
-    load(0, 0);
-    umma::fence_before_sync();
-    __syncthreads();
-    umma::fence_after_sync();
-    const uint32_t tbase = *slot;
-    const uint32_t idesc = umma::idesc_bf16_f32(128, Cout);
-    uint32_t waits[2] = {0u, 0u};
-    bool ok = true;
-    for (int t = 0; t < 27; ++t) {
-        const int s = t & 1;
-        umma::cp_async_wait_all();
-        umma::fence_async_smem();
-        umma::fence_before_sync();
-        __syncthreads();
-        umma::fence_after_sync();
-        if (tid == 0) {
-            for (int ks = 0; ks < (Cin >> 4); ++ks) {
-                uint64_t ad = umma::smem_desc(umma::smem_addr(sA[s]) + ks * 256, 128, 16 * Cin);
-                uint64_t bd = umma::smem_desc(umma::smem_addr(sB[s]) + ks * 256, 128, 16 * Cin);
-                umma::mma_bf16(tbase, ad, bd, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-            }
-            umma::mma_commit(&mbar[s]);
-        }
-        if (t + 1 < 27) {
-            const int s2 = (t + 1) & 1;
-            if (t >= 1) {  // the MMAs of tap t-1 read stage s2: wait before overwriting it
-                bool done = umma::mbar_wait(&mbar[s2], waits[s2] & 1u, kWaitCycles);
-                waits[s2] += 1;
-                if (!__syncthreads_and(done ? 1 : 0)) {
-                    ok = false;
-                    break;
-                }
-            }
-            load(t + 1, s2);
-        }
-    }
-    if (ok) {  // the last tap (26) used stage 0; its completion implies all earlier MMAs
-        bool done = umma::mbar_wait(&mbar[0], waits[0] & 1u, kWaitCycles);
-        ok = __syncthreads_and(done ? 1 : 0) != 0;
-    }
-    umma::fence_after_sync();
-    if (ok) {
-        const size_t vox = (size_t)n * a.nvox + (size_t)v;
-        for (int c = 0; c < Cout; c += 8) {
-            float r[8];
-            umma::tmem_ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, r);
-            for (int j = 0; j < 8; ++j) {
-                if (a.bias) r[j] += a.bias[c + j];
-                if (a.relu) r[j] = r[j] > 0.f ? r[j] : a.slope * r[j];
-            }
-            if (a.y_fp32) {
-                float* yo = static_cast<float*>(a.y) + vox * a.y_cstride + a.y_coffset + c;
-                reinterpret_cast<float4*>(yo)[0] = make_float4(r[0], r[1], r[2], r[3]);
-                reinterpret_cast<float4*>(yo)[1] = make_float4(r[4], r[5], r[6], r[7]);
-            } else {
-                __nv_bfloat162 p[4];
-                for (int j = 0; j < 4; ++j) p[j] = __floats2bfloat162_rn(r[2 * j], r[2 * j + 1]);
-                __nv_bfloat16* yo = static_cast<__nv_bfloat16*>(a.y) + vox * a.y_cstride + a.y_coffset + c;
-                *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<uint4*>(p);
-            }
-        }
-    } else if (tid == 0) {
-        atomicOr(a.status, 1u);
-    }
-    umma::fence_before_sync();
-    __syncthreads();
-    umma::fence_after_sync();
-    if (warp == 0) umma::tmem_dealloc(tbase, ncols);
-}
 
 // ----------------------------------------------------------------------------
 // Brick convolution.  A work item computes Ty full output rows (all x) of one z plane
@@ -590,117 +481,161 @@ __global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b
     if (warp == 0) umma::tmem_dealloc(tbase, (uint32_t)b.tcols);
 }
 
-__global__ void __launch_bounds__(128) k_conv3d_wgrad(WgradArgs a) {
-    constexpr int KV = 64;  // voxels per stage
-    extern __shared__ __align__(128) unsigned char smem[];
+// ----------------------------------------------------------------------------
+// Brick weight gradient: dW[co][tap][ci] = sum over output positions v of
+// dy[v][co] x[v + off(tap)][ci].  Per work item (Ty output rows of one z plane) the
+// output-gradient rows and the zero-padded input brick are staged once, both as 8-channel
+// planes with 16 bytes per position, i.e. M/N-major core matrices (8 positions x 8
+// channels).  The MMA's A operand is dy (M = co, padded to 128: rows past Cout read
+// whatever follows and are never stored), K = 16 positions; B is the brick read from the
+// tap's offset (N = Nc input channels).  All taps of the pass use the same A, so the
+// tensor core fetches it once per K step.  dW accumulates in tensor memory over all the
+// CTA's items and is added to global memory once, at the end.  Padding positions of dy
+// are zero, so brick positions under them contribute nothing -- provided they hold no
+// NaN or Inf: the few positions B reads just outside the staged data (before the first
+// plane, between planes, after the last) are zeroed once at start and never written.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b) {
+    extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int Cin = a.Cin, Cout = a.Cout;
-    const int a_bytes = KV * 128 * 2, b_bytes = KV * Cin * 2;
-    unsigned char* sA[2] = {smem, smem + a_bytes + b_bytes};
-    unsigned char* sB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * (a_bytes + b_bytes));
-    uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 2);
-    const int tap = blockIdx.y;
-    const int dz = tap / 9 - 1, dy_ = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const long long total = (long long)a.batch * a.nvox;
-    const long long c0 = (long long)blockIdx.x * a.chunk;
-    const long long c1 = min(c0 + a.chunk, total);
-    const int HW = a.H * a.W;
-    const uint32_t ncols = Cin <= 32 ? 32u : Cin <= 64 ? 64u : Cin <= 128 ? 128u : 256u;
+    const int Cin = a.Cin, Cout = a.Cout, W = a.W, H = a.H, D = a.D, Nc = b.Nc;
+    const int P = b.P, Yb = b.Yb;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);  // [kPipeStages]
+    uint64_t* empty = full + kPipeStages;                 // [kPipeStages]
+    uint64_t* dfull = empty + kPipeStages;                // all MMAs of the CTA done
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem + 128);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 132);
+    const uint32_t s_stage0 = umma::smem_addr(smem) + kPipeHeader;
+    const int pass = blockIdx.y;
+    const int c = pass / b.ngroups;  // input-channel chunk
+    const int t0 = (pass % b.ngroups) * b.ntap;
+    const int t1 = t0 + b.ntap < 27 ? t0 + b.ntap : 27;
+    const int my_items =
+        b.items > (int)blockIdx.x ? (b.items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    {  // zero both stages: gaps around the staged data must read as 0, not leftover bits
+        uint4* z = reinterpret_cast<uint4*>(smem + kPipeHeader);
+        const int n16 = kPipeStages * b.stage / 16;
+        for (int i = tid; i < n16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        umma::fence_async_smem();  // generic-proxy stores -> tensor-core reads
+    }
     if (warp == 0) {
-        umma::tmem_alloc(slot, ncols);
+        umma::tmem_alloc(slot, 512u);
         umma::tmem_relinquish();
     }
     if (tid == 0) {
-        umma::mbar_init(&mbar[0], 1);
-        umma::mbar_init(&mbar[1], 1);
+        for (int s = 0; s < kPipeStages; ++s) {
+            umma::mbar_init(&full[s], 128);
+            umma::mbar_init(&empty[s], 1);
+        }
+        umma::mbar_init(dfull, 1);
+        *abort_flag = 0;
     }
-    // stage s <- voxels [g, g+KV): A rows are 16-byte groups of 8 co (m-group), one per
-    // (voxel, m-group); B the same for ci of the shifted voxel.  M/N-major core matrix:
-    // row = voxel % 8, the 16 bytes = 8 channels; [k-group][m-group] order.
-    auto load = [&](long long g, int s) {
-        const uint32_t adst = umma::smem_addr(sA[s]), bdst = umma::smem_addr(sB[s]);
-        for (int c = tid; c < KV * 16; c += 128) {  // 128 rows of A = 16 m-groups of co
-            const int kv = c >> 4, mg = c & 15;
-            const long long gv = g + kv;
-            const bool in = gv < c1 && mg * 8 < Cout;
-            const __nv_bfloat16* src = in ? a.dy + (size_t)gv * Cout + mg * 8 : a.dy;
-            umma::cp_async16(adst + (uint32_t)(((kv >> 3) * 16 + mg) * 128 + (kv & 7) * 16), src, in ? 16u : 0u);
-        }
-        const int ng8 = Cin >> 3;
-        for (int c = tid; c < KV * ng8; c += 128) {
-            const int kv = c / ng8, ng = c - kv * ng8;
-            const long long gv = g + kv;
-            bool in = gv < c1;
-            const __nv_bfloat16* src = a.x;
-            if (in) {
-                const int nn = (int)(gv / a.nvox), v = (int)(gv - (long long)nn * a.nvox);
-                const int zz = v / HW + dz, yy = (v / a.W) % a.H + dy_, xx = v % a.W + dx;
-                in = (unsigned)zz < (unsigned)a.D && (unsigned)yy < (unsigned)a.H && (unsigned)xx < (unsigned)a.W;
-                if (in) src = a.x + ((size_t)nn * a.nvox + (size_t)(zz * a.H + yy) * a.W + xx) * Cin + ng * 8;
-            }
-            umma::cp_async16(bdst + (uint32_t)(((kv >> 3) * ng8 + ng) * 128 + (kv & 7) * 16), src, in ? 16u : 0u);
-        }
-        umma::cp_async_commit();
-    };
-    load(c0, 0);
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tbase = *slot;
-    const uint32_t idesc = umma::idesc_bf16_f32(128, Cin, 1, 1);
-    const int steps = (int)((c1 - c0 + KV - 1) / KV);
-    uint32_t waits[2] = {0u, 0u};
-    bool ok = true;
-    for (int t = 0; t < steps; ++t) {
-        const int s = t & 1;
-        umma::cp_async_wait_all();
-        umma::fence_async_smem();
-        umma::fence_before_sync();
-        __syncthreads();
-        umma::fence_after_sync();
-        if (tid == 0) {
-            for (int ks = 0; ks < KV / 16; ++ks) {  // two k-groups of 8 voxels per instruction
-                uint64_t ad = umma::smem_desc(umma::smem_addr(sA[s]) + ks * 2 * 16 * 128, 16 * 128, 128);
-                uint64_t bd = umma::smem_desc(umma::smem_addr(sB[s]) + ks * 2 * (Cin >> 3) * 128, (Cin >> 3) * 128, 128);
-                umma::mma_bf16(tbase, ad, bd, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-            }
-            umma::mma_commit(&mbar[s]);
-        }
-        if (t + 1 < steps) {
-            const int s2 = (t + 1) & 1;
-            if (t >= 1) {
-                bool done = umma::mbar_wait(&mbar[s2], waits[s2] & 1u, kWaitCycles);
-                waits[s2] += 1;
-                if (!__syncthreads_and(done ? 1 : 0)) {
+    const int npos_x = 3 * Yb * P;
+    const int fB = (Yb + 1) * P;  // brick position under output position 0 of the item
+
+    if (warp == 4) {
+        if (lane == 0) {
+            const uint32_t idesc = umma::idesc_bf16_f32(128, Nc, 1, 1);
+            bool ok = true;
+            for (int j = 0; j < my_items && ok; ++j) {
+                const int s = j % kPipeStages, u = j / kPipeStages;
+                if (!pipe_wait(&full[s], (uint32_t)u & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
+                umma::fence_after_sync();
+                umma::fence_async_smem();  // cp.async (generic proxy) data -> tensor core
+                const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
+                // M/N-major: leading byte offset = next 8 positions (K), stride = next 8 channels
+                const uint64_t a0 = umma::smem_desc(st, 128, (uint32_t)b.plane_dy);
+                const uint64_t b0 = umma::smem_desc(st + (uint32_t)b.x_off, 128, (uint32_t)b.plane_x);
+                for (int ks = 0; ks < b.kst; ++ks) {
+                    const uint64_t ad = a0 + (uint64_t)(16 * ks);  // 16 positions of 16 bytes
+                    // each tap's accumulator starts at its first MMA: item 0, K step 0
+                    const uint32_t accum = (j > 0 || ks > 0) ? 1u : 0u;
+                    for (int t = t0; t < t1; ++t) {
+                        const int d = ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P + (t % 3 - 1);
+                        // fB + d >= -1: one position before the brick at most (dy is zero there)
+                        const uint64_t bd = b0 + (uint64_t)(int64_t)(fB + 16 * ks + d);
+                        umma::mma_bf16(tbase + (uint32_t)((t - t0) * Nc), ad, bd, idesc, accum);
+                    }
+                }
+                umma::mma_commit(&empty[s]);
             }
-            load(c0 + (long long)(t + 1) * KV, s2);
+            if (ok) umma::mma_commit(dfull);
         }
-    }
-    if (ok && steps > 0) {
-        const int sl = (steps - 1) & 1;
-        bool done = umma::mbar_wait(&mbar[sl], waits[sl] & 1u, kWaitCycles);
-        ok = __syncthreads_and(done ? 1 : 0) != 0;
-    }
-    umma::fence_after_sync();
-    if (ok && steps > 0) {
-        const int co = 32 * warp + lane;
-        for (int c = 0; c < Cin; c += 8) {
-            float r[8];
-            umma::tmem_ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, r);
-            if (co < Cout)
-                for (int j = 0; j < 8; ++j) atomicAdd(&a.dw[((size_t)co * 27 + tap) * Cin + c + j], r[j]);
+        __syncwarp();
+    } else {
+        bool ok = true;
+        auto worker_wait = [&](uint64_t* m, uint32_t parity) {
+            bool done = true;
+            if (tid == 0) done = pipe_wait(m, parity, abort_flag);
+            return workers_all(done);
+        };
+        for (int j = 0; j < my_items && ok; ++j) {
+            const int s = j % kPipeStages, u = j / kPipeStages;
+            if (u >= 1 && !worker_wait(&empty[s], (uint32_t)(u - 1) & 1u)) {
+                ok = false;
+                break;
+            }
+            int r = (int)blockIdx.x + j * (int)gridDim.x;
+            const int z = r % D;
+            r /= D;
+            const int y0 = (r % b.nyb) * b.Ty;
+            const int n = r / b.nyb;
+            const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
+            {  // output-gradient rows: Cout/8 planes of kst*16 positions (zero at padding and past the rows)
+                const int groups = Cout >> 3, npos = b.kst * 16;
+                const __nv_bfloat16* dyn = a.dy + (size_t)n * a.nvox * Cout;
+                for (int i = tid; i < groups * npos; i += 128) {
+                    const int q = i / npos, f = i - q * npos;
+                    const int rr = f / P, xp = f - rr * P, yy = y0 + rr, xx = xp - 1;
+                    const bool in = rr < b.Ty && yy < H && (unsigned)xx < (unsigned)W;
+                    const __nv_bfloat16* src = in ? dyn + ((size_t)(z * H + yy) * W + xx) * Cout + 8 * q : dyn;
+                    umma::cp_async16(st + (uint32_t)(q * b.plane_dy + f * 16), src, in ? 16u : 0u);
+                }
+            }
+            {  // input brick of this chunk: Nc/8 planes (as the forward kernel)
+                const int groups = Nc >> 3;
+                const __nv_bfloat16* xin = a.x + (size_t)n * a.nvox * Cin + c * Nc;
+                for (int i = tid; i < groups * npos_x; i += 128) {
+                    const int g = i / npos_x, f = i - g * npos_x;
+                    const int row = f / P, xp = f - row * P, zb = row / Yb, yb = row - zb * Yb;
+                    const int zz = z + zb - 1, yy = y0 + yb - 1, xx = xp - 1;
+                    const bool in =
+                        (unsigned)zz < (unsigned)D && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
+                    const __nv_bfloat16* src = in ? xin + ((size_t)(zz * H + yy) * W + xx) * Cin + 8 * g : xin;
+                    umma::cp_async16(st + (uint32_t)(b.x_off + g * b.plane_x + f * 16), src, in ? 16u : 0u);
+                }
+            }
+            umma::cp_async_mbar_arrive(&full[s]);
         }
-    } else if (!ok && tid == 0) {
-        atomicOr(a.status, 1u);
+        umma::cp_async_wait_all();
+        if (ok && my_items > 0 && worker_wait(dfull, 0u)) {
+            umma::fence_after_sync();
+            const int co = 32 * warp + lane;
+            if (32 * warp < Cout) {  // warp-uniform: lanes past Cout load but do not store
+                for (int t = t0; t < t1; ++t)
+                    for (int cc = 0; cc < Nc; cc += 8) {
+                        float v[8];
+                        __syncwarp();
+                        umma::tmem_ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)((t - t0) * Nc + cc), v);
+                        if (co < Cout)
+                            for (int e = 0; e < 8; ++e)
+                                atomicAdd(&a.dw[((size_t)co * 27 + t) * Cin + c * Nc + cc + e], v[e]);
+                    }
+            }
+        }
     }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    if (warp == 0) umma::tmem_dealloc(tbase, ncols);
+    if (tid == 0 && *abort_flag) atomicOr(a.status, 1u);
+    if (warp == 0) umma::tmem_dealloc(tbase, 512u);
 }
 
 // wd[ci][26 - tap][co] = w[co][tap][ci]: the data gradient of a 3x3x3 convolution is
@@ -772,32 +707,70 @@ static bool brick_plan(const ConvArgs& a, int batch, BrickPlan* out, size_t* sme
 cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st) {
     BrickPlan bp{};
     size_t bsmem = 0;
-    if (brick_plan(a, batch, &bp, &bsmem)) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3d_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        const int ctas = bp.items < sms ? bp.items : sms;
-        k_conv3d_brick<<<ctas, 160, bsmem, st>>>(a, bp);
-        return cudaGetLastError();
-    }
-    const size_t smem = 2 * ((size_t)128 * a.Cin * 2 + (size_t)a.Cout * a.Cin * 2) + 64;
-    cudaError_t e = cudaFuncSetAttribute(k_conv3d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!brick_plan(a, batch, &bp, &bsmem)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)batch * a.nvox / 128;
-    k_conv3d<<<(unsigned)tiles, 128, smem, st>>>(a);
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int ctas = bp.items < sms ? bp.items : sms;
+    k_conv3d_brick<<<ctas, 160, bsmem, st>>>(a, bp);
     return cudaGetLastError();
 }
 
+// Plan of the brick weight gradient: Nc in {16, 32} input channels per pass, as many
+// taps per pass as 512 tensor-memory columns hold, and the largest Ty whose two stages
+// fit; the cost model (~46 cycles per MMA with a reused A; staging ~11 bytes per cycle per
+// SM) picks between the Nc options.  Measured alternative, slower on the denoiser's
+// layers: one input plane per pass with the nine taps of one dz (more rows per item).
+static bool wgrad_plan(const WgradArgs& a, WgradPlan* out, size_t* smem_out) {
+    const int P = a.W + 2;
+    double best = 1e300;
+    bool found = false;
+    for (int Nc = 16; Nc <= 32; Nc += 16) {
+        if (a.Cin % Nc) continue;
+        const int ntap = Nc == 16 ? 27 : 14;
+        const int ngroups = (27 + ntap - 1) / ntap;
+        for (int Ty = 1; Ty <= a.H; ++Ty) {
+            const int kst = (Ty * P + 15) / 16;
+            const size_t plane_dy = (size_t)kst * 256;
+            const size_t dy_bytes = (size_t)(a.Cout / 8) * plane_dy;
+            const size_t plane_x = ((size_t)3 * (Ty + 2) * P * 16 + 127) / 128 * 128;
+            const size_t x_off = (dy_bytes + 16 + 127) / 128 * 128;  // >= 16 bytes before the brick
+            size_t stage = (x_off + (size_t)(Nc / 8) * plane_x + 512 + 127) / 128 * 128;
+            if (stage < 16 * plane_dy) stage = (16 * plane_dy + 127) / 128 * 128;  // A rows past Cout stay inside
+            const size_t smem = kPipeHeader + kPipeStages * stage;
+            if (smem > 227 * 1024 || plane_x >= (1u << 18) || plane_dy >= (1u << 18)) break;
+            const double pos = (double)Ty * a.W;  // output voxels per item
+            const double mma = (double)kst * 27 * 46.0 * (a.Cin / Nc);
+            const double load = (double)(stage - 512) / 11.0 * (a.Cin / Nc) * ngroups;
+            const double cost = (mma > load ? mma : load) / pos;
+            if (cost < best) {
+                best = cost;
+                found = true;
+                const int nyb = (a.H + Ty - 1) / Ty;
+                const int items = a.batch * nyb * a.D;
+                const int passes = (a.Cin / Nc) * ngroups;
+                int G = (152 + passes - 1) / passes;
+                if (G > items) G = items;
+                *out = WgradPlan{Ty, nyb, P, Ty + 2, Nc, ntap, ngroups, kst, (int)plane_dy, (int)plane_x,
+                                 (int)x_off, (int)stage, items, G};
+                *smem_out = smem;
+            }
+        }
+    }
+    return found;
+}
+
 cudaError_t wgrad_launch(const WgradArgs& a, cudaStream_t st) {
-    const size_t smem = 2 * ((size_t)64 * 128 * 2 + (size_t)64 * a.Cin * 2) + 64;
-    cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    WgradPlan wp{};
+    size_t wsmem = 0;
+    if (!wgrad_plan(a, &wp, &wsmem)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
     if (e != cudaSuccess) return e;
-    const long long total = (long long)a.batch * a.nvox;
-    dim3 grid((unsigned)((total + a.chunk - 1) / a.chunk), 27);
-    k_conv3d_wgrad<<<grid, 128, smem, st>>>(a);
+    dim3 grid((unsigned)wp.G, (unsigned)((a.Cin / wp.Nc) * wp.ngroups));
+    k_wgrad_brick<<<grid, 160, wsmem, st>>>(a, wp);
     return cudaGetLastError();
 }
 
@@ -805,7 +778,7 @@ cudaError_t wgrad_launch(const WgradArgs& a, cudaStream_t st) {
 
 static bool conv_shape_ok(int D, int H, int W, int Cin, int Cout, int batch) {
     long long nvox = (long long)D * H * W;
-    return batch >= 1 && D >= 1 && H >= 1 && W >= 1 && nvox % 128 == 0 && nvox * batch < (1ll << 31) &&
+    return batch >= 1 && D >= 1 && H >= 1 && W >= 1 && W <= 256 && nvox % 128 == 0 && nvox * batch < (1ll << 31) &&
            Cin >= 16 && Cin <= 192 && Cin % 16 == 0 && Cout >= 16 && Cout <= 256 && Cout % 16 == 0;
 }
 
@@ -814,7 +787,7 @@ extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int 
                                   int y_fp32, int relu, void* stream) {
     if (!d_x || !d_w || !d_y || !conv_shape_ok(D, H, W, Cin, Cout, batch) || y_cstride < Cout + y_coffset ||
         y_coffset < 0 || (y_coffset % 8) || (y_cstride % 8)) {
-        set_last_error("sde_conv3d_forward: need D*H*W a multiple of 128, Cin in 16..192 and Cout in 16..256 "
+        set_last_error("sde_conv3d_forward: need W <= 256, D*H*W a multiple of 128, Cin in 16..192 and Cout in 16..256 "
                        "(multiples of 16), y_cstride >= Cout + y_coffset, both multiples of 8");
         return SDE_EINVAL;
     }
@@ -838,13 +811,13 @@ extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int 
     a.relu = relu;
     a.slope = 0.f;
     a.status = d_status;
-    return report(conv3d_launch(a, batch, (cudaStream_t)stream), "k_conv3d launch");
+    return report(conv3d_launch(a, batch, (cudaStream_t)stream), "conv3d launch");
 }
 
 extern "C" int sde_conv3d_wgrad(const void* d_x, const void* d_dy, float* d_dw, int batch, int D, int H, int W,
                                 int Cin, int Cout, void* stream) {
     if (!d_x || !d_dy || !d_dw || !conv_shape_ok(D, H, W, Cin, Cout, batch) || Cout > 128) {
-        set_last_error("sde_conv3d_wgrad: need D*H*W a multiple of 128, Cin in 16..192, Cout in 16..128 "
+        set_last_error("sde_conv3d_wgrad: need W <= 256, D*H*W a multiple of 128, Cin in 16..192, Cout in 16..128 "
                        "(multiples of 16)");
         return SDE_EINVAL;
     }
@@ -862,9 +835,8 @@ extern "C" int sde_conv3d_wgrad(const void* d_x, const void* d_dy, float* d_dw, 
     a.Cout = Cout;
     a.nvox = D * H * W;
     a.batch = batch;
-    a.chunk = 8192;
     a.status = d_status;
-    return report(wgrad_launch(a, (cudaStream_t)stream), "k_conv3d_wgrad launch");
+    return report(wgrad_launch(a, (cudaStream_t)stream), "wgrad launch");
 }
 
 extern "C" int sde_conv3d_flip_weights(const void* d_w, void* d_wd, int Cin, int Cout, void* stream) {

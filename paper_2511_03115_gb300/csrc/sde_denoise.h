@@ -38,15 +38,30 @@ struct BrickPlan {
     int items;   // batch x nsplit x nyb x D
 };
 
-// Weight gradient: dw[co][tap][ci] += sum_v dy[v][co] x[v + off(tap)][ci].  One CTA per
-// (tap, voxel chunk); the GEMM has rows = co (padded to 128), columns = ci, K = voxels,
-// with both operands M/N-major (channels contiguous, as stored).
+// Weight gradient: dw[co][tap][ci] += sum_v dy[v][co] x[v + off(tap)][ci] (brick kernel,
+// see sde_denoise.cu).
 struct WgradArgs {
     const __nv_bfloat16* x;   // [n][V][Cin]
     const __nv_bfloat16* dy;  // [n][V][Cout]
     float* dw;                // [Cout][27][Cin], accumulated
-    int D, H, W, Cin, Cout, nvox, batch, chunk;
+    int D, H, W, Cin, Cout, nvox, batch;
     unsigned int* status;
+};
+
+// Work decomposition of the brick weight-gradient kernel (host-chosen).  A pass is one
+// chunk of Nc input channels and one group of taps (its accumulators fill tensor memory);
+// a work item is Ty output rows of one z plane.
+struct WgradPlan {
+    int Ty, nyb, P, Yb;  // as BrickPlan
+    int Nc;              // input channels per pass (MMA N)
+    int ntap, ngroups;   // taps per pass, tap groups
+    int kst;             // K steps (16 positions) per item
+    int plane_dy;        // bytes between 8-channel planes of the output-gradient rows
+    int plane_x;         // bytes between 8-channel planes of the input brick
+    int x_off;           // offset of the input brick within a stage
+    int stage;           // bytes per stage
+    int items;           // batch x nyb x D
+    int G;               // CTAs per pass
 };
 
 cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st);

@@ -440,7 +440,6 @@ int wgrad(sde_denoiser* d, const bf16* x, const bf16* dy, const Layer& l, int ba
     a.Cout = l.Cout;
     a.nvox = D * H * W;
     a.batch = batch;
-    a.chunk = 16384;
     a.status = status;
     rc = fail(wgrad_launch(a, d->st), "wgrad launch");
     if (rc) return rc;

@@ -67,6 +67,27 @@ def test_conv3d_forward_dgrad_wgrad_match_torch(sde_gpu, Cin, Cout, shape):
         assert (dw.cpu().double() - dw_ref).abs().max().item() <= 1e-4 * dw_ref.abs().max().item() + 1e-4
 
 
+@pytest.mark.parametrize("Cin,Cout", [(32, 32), (96, 32), (16, 32)])
+def test_conv3d_wgrad_at_full_width_matches_float64(sde_gpu, Cin, Cout):
+    """The weight gradient at the denoiser's full row width (128 voxels: several M tiles
+    per item, many items per CTA, both channel-chunk plans) against a float64 reference.
+    Its padding positions multiply staged memory around the data by zero, so that memory
+    must be zero rather than leftover bits; a leftover NaN would show here."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(Cin + Cout)
+    D, H, W = 6, 128, 128
+    x = (0.5 * torch.randn(1, D, H, W, Cin, device="cuda", generator=g)).to(torch.bfloat16)
+    dy = (0.5 * torch.randn(1, D, H, W, Cout, device="cuda", generator=g)).to(torch.bfloat16)
+    dw = torch.zeros(Cout, 27, Cin, device="cuda")
+    sde_gpu.conv3d_wgrad(x, dy, dw)
+    sde_gpu.denoise_status()
+    ref = torch.nn.grad.conv3d_weight(x.double().permute(0, 4, 1, 2, 3), (Cout, Cin, 3, 3, 3),
+                                      dy.double().permute(0, 4, 1, 2, 3), padding=1)
+    ref = ref.permute(0, 2, 3, 4, 1).reshape(Cout, 27, Cin)
+    assert torch.isfinite(dw).all()
+    assert (dw.double() - ref).abs().max().item() <= 1e-4 * ref.abs().max().item()
+
+
 def _ref_network(layers, dose_low, rho, dose_high):
     """The denoiser written with plain PyTorch CPU float64 operations (test reference):
     same layers, skips, pooling, upsampling and input/output scaling as the library."""
