@@ -4,7 +4,8 @@
 weight gradient) of every layer shape of the 128 x 128 x 192 denoiser on random BF16
 data, then a full inference and a training step, and prints one line per layer with
 the achieved TFLOP/s (2 x voxels x 27 x Cin x Cout per forward).  ``--shape D H W Cin
-Cout`` runs only that convolution ``--reps`` times (a small case for a profiler).
+Cout`` runs only that convolution ``--reps`` times (a small case for a profiler), or with
+``--wgrad`` its weight gradient.
 """
 from __future__ import annotations
 
@@ -50,17 +51,24 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--shape", type=int, nargs=5, default=None, metavar=("D", "H", "W", "CIN", "COUT"))
     ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--wgrad", action="store_true", help="with --shape: run the weight gradient")
     args = ap.parse_args()
     torch.cuda.init()
     st = torch.cuda.current_stream()
     if args.shape:
         D, H, W, ci, co = args.shape
         x, w, b, y = _tensors(D, H, W, ci, co)
+        if args.wgrad:
+            dw = torch.zeros(co, 27, ci, device="cuda")
+            dy = (0.5 * torch.randn(1, D, H, W, co, device="cuda")).to(torch.bfloat16)
         for _ in range(args.reps):
-            S.conv3d(x, w, b, relu=True, y=y)
+            if args.wgrad:
+                S.conv3d_wgrad(x, dy, dw)
+            else:
+                S.conv3d(x, w, b, relu=True, y=y)
         torch.cuda.synchronize()
         S.denoise_status()
-        print(json.dumps({"shape": args.shape, "reps": args.reps, "ok": True}))
+        print(json.dumps({"shape": args.shape, "reps": args.reps, "wgrad": args.wgrad, "ok": True}))
         return
     rows = []
     for D, H, W, ci, co in LAYER_SHAPES:
