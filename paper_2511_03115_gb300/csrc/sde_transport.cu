@@ -92,24 +92,28 @@ __device__ __forceinline__ float cut_rate(const KParams& P, int m, const Phys& p
 // (CM cosine), inverted by Newton's method on its closed-form primitive
 // G(mu) = 2 mu/(1-mu^2) - sin(eta ln((1+mu)/(1-mu)))/(2 eta), which is odd in
 // mu: the root is sought in the forward variable s = 1 - |mu| and mirrored.
+// Newton starts 13 % off at most and converges quadratically (1e-7 relative after four
+// steps over 0.05-200 MeV); the fifth brings it to FP32 rounding.  The fast intrinsics
+// keep the root within a few ulp: the arguments stay inside [-2 pi, 2 pi] for the
+// fixed cut-off and the divisors far below 2^126.
 __device__ void mott_sample(float U, float eta, float s_cut, float s_back, float& c, float& sn) {
-    auto prim = [&](float s) {
-        float L = logf((2.f - s) / s);
-        return 2.f * (1.f - s) / (s * (2.f - s)) - sinf(eta * L) / (2.f * eta);
-    };
-    float g_hi = prim(s_cut), g_lo = -prim(s_back);
+    const float inv2eta = __fdividef(0.5f, eta);
+    float g_hi = mott_prim(s_cut, eta), g_lo = -mott_prim(s_back, eta);
     float target = g_lo + U * (g_hi - g_lo);
     float sg = target >= 0.f ? 1.f : -1.f;
     float y = fabsf(target);
     float q = sqrtf(1.f + y * y);
-    float s = (1.f + 1.f / (q + y)) / (1.f + q);  // root without the sine term
+    float s = __fdividef(1.f + __fdividef(1.f, q + y), 1.f + q);  // root without the sine term
     float s_min = sg > 0.f ? s_cut : s_back;
-    for (int it = 0; it < 6; ++it) {
-        float mu = 1.f - s, om2 = s * (2.f - s);
-        float L = logf((2.f - s) / s);
-        float G = 2.f * mu / om2 - sinf(eta * L) / (2.f * eta);
-        float dG = 2.f * (1.f + mu * mu) / (om2 * om2) - cosf(eta * L) / om2;
-        s = fminf(fmaxf(s + (G - y) / dG, s_min), 1.f);
+#pragma unroll 1
+    for (int it = 0; it < 5; ++it) {
+        float mu = 1.f - s, rom2 = __fdividef(1.f, s * (2.f - s));
+        float L = __logf(__fdividef(2.f - s, s));
+        float sl, cl;
+        __sincosf(eta * L, &sl, &cl);
+        float G = 2.f * mu * rom2 - sl * inv2eta;
+        float dG = (2.f * (1.f + mu * mu) * rom2 - cl) * rom2;
+        s = fminf(fmaxf(s + __fdividef(G - y, dG), s_min), 1.f);
     }
     c = sg * (1.f - s);
     sn = sqrtf(s * (2.f - s));
@@ -159,19 +163,24 @@ __device__ void cm_to_lab(float E, float Eout, bool elastic, float m2, float cc,
     sl = X * inv;
 }
 
-// A large-angle event of Eq. Npi at pre-step energy E: pick channel and element
-// by rate, sample the CM angle, convert to the lab, rotate; non-elastic events
-// scale the post-loss energy E1 by (1-u).  Refreshes the exponential clock.  CUT:
-// the energy-dependent cut-off s_c = 1 - cos(theta_c) of this step (compiled
+// Outcome of a large-angle event: the new direction, the refreshed clock, the factor
+// (1 - u) on the post-loss energy (1 for elastic events) and the kind (1 elastic, 2
+// non-elastic, 0 none).  Returned by value so that the caller's state stays in registers.
+struct JumpOut {
+    float ux, uy, uz, tau, e_fac;
+    int kind;
+};
+
+// A large-angle event of Eq. Npi at pre-step energy E (table interval k, fraction f):
+// pick channel and element by rate, sample the CM angle, convert to the lab, rotate.
+// CUT: the energy-dependent cut-off s_c = 1 - cos(theta_c) of this step (compiled
 // separately so that the fixed-cut-off kernel carries none of it).
 template <bool CUT>
-__device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1, float& ux, float& uy,
-                                    float& uz, float& tau, uint64_t h, uint32_t n, float s_c) {
+__device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k, float f, float ux, float uy,
+                                        float uz, float tau, uint64_t h, uint32_t n, float s_c) {
+    JumpOut o{ux, uy, uz, tau, 1.f, 0};
     uint4 J = philox(P, n, kTagJumpA, h);
     const MatJump& mj = P.mats[m];
-    int k;
-    float f;
-    grid_pos(P, E, k, f);
     const float* r0 = P.jrates + ((size_t)m * P.N + k) * (2 * SDE_MAX_ELEMENTS);
     const float* r1 = r0 + 2 * SDE_MAX_ELEMENTS;
     const float rE2 = __fdividef(1.f, E * E);  // elastic rates are stored times E^2
@@ -205,7 +214,7 @@ __device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1,
             }
         }
     if (pick < 0) pick = last;
-    if (pick < 0) return 0;  // no channel open (cannot happen when the clock fired)
+    if (pick < 0) return o;  // no channel open (cannot happen when the clock fired)
     int el = pick % SDE_MAX_ELEMENTS;
     bool elastic = pick < SDE_MAX_ELEMENTS;
     float m2 = mj.m2[el];
@@ -227,13 +236,14 @@ __device__ __noinline__ int do_jump(const KParams& P, int m, float E, float& E1,
         cc = mu;
         sc = sqrtf(fmaxf(0.f, (1.f - mu) * (1.f + mu)));
         cm_to_lab(E, E * (1.f - uu), false, m2, cc, sc, cl, sl);
-        E1 *= (1.f - uu);
+        o.e_fac = 1.f - uu;
     }
     float sp, cp;
     __sincosf(kTwoPiF * u01(J.z), &sp, &cp);
-    rotate(ux, uy, uz, cl, sl, cp, sp);
-    tau = -__logf(u01(J.w));
-    return elastic ? 1 : 2;
+    rotate(o.ux, o.uy, o.uz, cl, sl, cp, sp);
+    o.tau = -__logf(u01(J.w));
+    o.kind = elastic ? 1 : 2;
+    return o;
 }
 
 // One Euler-Maruyama step of Eq. VSDE at Y_n = (E, ., u) in material m of
@@ -281,7 +291,15 @@ __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int
         sj = cut_rate(P, m, ph, E, s_c) + ph.sn;
     }
     tau -= rho * sj;
-    if (tau <= 0.f) jump = do_jump<CUT>(P, m, E, E1, ux, uy, uz, tau, h, n, s_c);
+    if (tau <= 0.f) {
+        JumpOut o = do_jump<CUT>(P, m, E, ph.k, ph.f, ux, uy, uz, tau, h, n, s_c);
+        ux = o.ux;
+        uy = o.uy;
+        uz = o.uz;
+        tau = o.tau;
+        E1 *= o.e_fac;
+        jump = o.kind;
+    }
     E = E1;
     return jump;
 }
@@ -403,7 +421,7 @@ __device__ unsigned long long deposit_chord(const KParams& P, float ax, float ay
 #define SDE_BLOCK_ADD(idx, v) atomicAdd(&s_cnt[idx], (unsigned long long)(v))
 
 template <int TALLY, bool SMEM, bool AGG, bool CUT>
-__global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(KParams P) {
+__global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_constant__ KParams P) {
     extern __shared__ float4 s_tab[];
     __shared__ unsigned long long s_cnt[kCntWords];
     // The warp's current batch of history ids [next, end) is warp-uniform: it lives in
@@ -629,7 +647,7 @@ __global__ void __launch_bounds__(1024) k_prep_spots(const sde_spot* raw, int n,
     }
 }
 
-__global__ void k_probe(KParams P, int m, float rho, float E0, uint64_t h0, int n, float* Eo, float* co,
+__global__ void k_probe(const __grid_constant__ KParams P, int m, float rho, float E0, uint64_t h0, int n, float* Eo, float* co,
                         int* jo, float* uxo, float* uyo) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;

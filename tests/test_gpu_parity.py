@@ -329,6 +329,15 @@ def test_history_ranges_add_up_to_the_whole_run(sde_gpu, graph):
         d.run(spots, seed=5, first=total, count=100)
         _, e, b = d.fetch(dose=False)
         assert np.array_equal(e, ref) and b == rb
+        # the same shards with device-resident spots (the path the benchmark times)
+        import torch
+        raw = torch.from_numpy(spots.view(np.uint8).copy()).cuda()
+        d.reset()
+        for r in range(3):
+            first, count = sde_gpu.history_shard(total, r, 3)
+            d.run_device(raw.data_ptr(), len(spots), seed=5, first=first, count=count)
+        _, e, b = d.fetch(dose=False)
+        assert np.array_equal(e, ref) and b == rb
         d.reset()
         d.run(spots, seed=5, first=total - 10, count=10**12)
         _, e, b = d.fetch(dose=False)
