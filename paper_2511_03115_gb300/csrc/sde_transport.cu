@@ -152,7 +152,7 @@ __device__ void cm_to_lab(float E, float Eout, bool elastic, float m2, float cc,
     float gu = rsqrtf((1.f - ucm) * (1.f + ucm));
     float v;
     if (elastic) {
-        v = p1 * m2 / (mp * mp + Et * m2);
+        v = __fdividef(p1 * m2, mp * mp + Et * m2);
     } else {
         float po = sqrtf(Eout * (Eout + 2.f * mp)), Eo = Eout + mp;
         v = fabsf(po - ucm * Eo) / (Eo - ucm * po);
@@ -176,10 +176,9 @@ struct JumpOut {
 // CUT: the energy-dependent cut-off s_c = 1 - cos(theta_c) of this step (compiled
 // separately so that the fixed-cut-off kernel carries none of it).
 template <bool CUT>
-__device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k, float f, float ux, float uy,
-                                        float uz, float tau, uint64_t h, uint32_t n, float s_c) {
+__device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k, float f, uint4 J, float ux,
+                                        float uy, float uz, float tau, uint64_t h, uint32_t n, float s_c) {
     JumpOut o{ux, uy, uz, tau, 1.f, 0};
-    uint4 J = philox(P, n, kTagJumpA, h);
     const MatJump& mj = P.mats[m];
     const float* r0 = P.jrates + ((size_t)m * P.N + k) * (2 * SDE_MAX_ELEMENTS);
     const float* r1 = r0 + 2 * SDE_MAX_ELEMENTS;
@@ -224,7 +223,7 @@ __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k,
             mott_sample(u01(J.y), eta_h, CUT ? s_c : P.s_cut, P.s_back, cc, sc);
         } else {
             float span = CUT ? __fdividef(1.f, s_c) - 0.5f : P.ruth_span;
-            float s = 1.f / (0.5f + u01(J.y) * span);
+            float s = __fdividef(1.f, 0.5f + u01(J.y) * span);
             cc = 1.f - s;
             sc = sqrtf(s * (2.f - s));
         }
@@ -292,7 +291,9 @@ __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int
     }
     tau -= rho * sj;
     if (tau <= 0.f) {
-        JumpOut o = do_jump<CUT>(P, m, E, ph.k, ph.f, ux, uy, uz, tau, h, n, s_c);
+        // the event's Philox block (tag A) is drawn here, where the round keys are
+        // kernel-parameter operands rather than loads through a pointer
+        JumpOut o = do_jump<CUT>(P, m, E, ph.k, ph.f, philox(P, n, kTagJumpA, h), ux, uy, uz, tau, h, n, s_c);
         ux = o.ux;
         uy = o.uy;
         uz = o.uz;
