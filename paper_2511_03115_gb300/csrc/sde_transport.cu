@@ -245,17 +245,19 @@ __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k,
     return o;
 }
 
-// One Euler-Maruyama step of Eq. VSDE at Y_n = (E, ., u) in material m of
-// density rho, with the step's Philox block x.  On return E1 = energy after the
-// continuous loss, E = energy after any non-elastic event, u = new direction.
-// Returns 0/1/2 (no jump, elastic, non-elastic).  The jump clock is
-// exponential: tau ~ Exp(1) is spent at rate sigma per unit path; crossing zero
-// within a step is the step's jump, which has probability 1 - exp(-Delta sigma)
-// as in the paper.  Switched-off terms are multiplied by zero (no branches).
+// Continuous part of one Euler-Maruyama step of Eq. VSDE at Y_n = (E, ., u) in
+// material m of density rho, with the step's Philox block x: on return E1 = energy
+// after the continuous loss, u = direction after the Brownian increment, tau = the
+// jump clock after the step, s_c = the step's elastic cut-off and ph = the table
+// position of E.  The clock is exponential: tau ~ Exp(1) is spent at rate sigma per
+// unit path; crossing zero within a step is the step's jump, which has probability
+// 1 - exp(-Delta sigma) as in the paper.  Returns true when it crossed: the step then
+// ends with a large-angle event (do_jump at the pre-step energy E).  Switched-off terms
+// are multiplied by zero (no branches).
 template <bool CUT>
-__device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int m, float rho, uint4 x,
-                                        float& E, float& ux, float& uy, float& uz, float& tau, uint64_t h,
-                                        uint32_t n, float& E1_out) {
+__device__ __forceinline__ bool sde_step_cont(const KParams& P, const float4* tab, int m, float rho, uint4 x,
+                                              float E, float& ux, float& uy, float& uz, float& tau,
+                                              float& E1_out, float& s_c_out, Phys& ph_out) {
     Phys ph = lookup(tab, P, m, E);
     float c = rho * ph.c;                   // varsigma_1 Delta
     float s = sqrtf(rho) * ph.s * P.strag_on;  // varsigma_2 sqrt(Delta)
@@ -283,23 +285,38 @@ __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int
     __sincosf(kTwoPiF * u01(x.w), &sp, &cp);
     rotate(ux, uy, uz, ct, st, cp, sp);
     E1_out = E1;
-    int jump = 0;
     float sj = ph.sj, s_c = P.s_cut;
     if (CUT) {  // variable cut-off theta_c = k sigma(E): theta_c^2 = k^2 (z/Delta) t
         s_c = cut_s(P.cut_k2 * t_raw);
         sj = cut_rate(P, m, ph, E, s_c) + ph.sn;
     }
+    s_c_out = s_c;
+    ph_out = ph;
     tau -= rho * sj;
-    if (tau <= 0.f) {
-        // the event's Philox block (tag A) is drawn here, where the round keys are
-        // kernel-parameter operands rather than loads through a pointer
+    return tau <= 0.f;
+}
+
+// The whole step (continuous part and, when the clock fires, the event at once).  On
+// return E1 = energy after the continuous loss, E = energy after any non-elastic event,
+// u = new direction; returns 0/1/2 (no jump, elastic, non-elastic).
+template <bool CUT>
+__device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int m, float rho, uint4 x,
+                                        float& E, float& ux, float& uy, float& uz, float& tau, uint64_t h,
+                                        uint32_t n, float& E1_out) {
+    float E1, s_c;
+    Phys ph;
+    int jump = 0;
+    if (sde_step_cont<CUT>(P, tab, m, rho, x, E, ux, uy, uz, tau, E1, s_c, ph)) {
         JumpOut o = do_jump<CUT>(P, m, E, ph.k, ph.f, philox(P, n, kTagJumpA, h), ux, uy, uz, tau, h, n, s_c);
         ux = o.ux;
         uy = o.uy;
         uz = o.uz;
         tau = o.tau;
-        E1 *= o.e_fac;
         jump = o.kind;
+        E1_out = E1;
+        E1 *= o.e_fac;
+    } else {
+        E1_out = E1;
     }
     E = E1;
     return jump;
@@ -416,6 +433,7 @@ __device__ unsigned long long deposit_chord(const KParams& P, float ax, float ay
 #define SDE_MIN_BLOCKS 5
 #endif
 
+
 // Rare events (start, escape, non-elastic removal, jumps) go to per-block
 // shared-memory counters; the per-step deposit needs no counter at all: the
 // deposited total is the sum of the tally, reduced when the balance is read.
@@ -443,6 +461,10 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
     float E = 0.f, px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 1.f, tau = 1.f;
     unsigned long long h = 0;
     uint32_t n = 0;
+    // Pending large-angle event of step n - 1: the material of that step (-1: none),
+    // its pre-step energy and its cut-off.
+    int jm = -1;
+    float jE = 0.f, jsc = 0.f;
     // Software pipeline: the voxel word of R_n and the Philox block of step n are
     // fetched/computed during step n-1, so their latency overlaps the step's work.
     uint32_t vox = 0;
@@ -493,6 +515,40 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
             dead = __ballot_sync(0xffffffffu, !alive);
         }
         if (!__any_sync(0xffffffffu, alive)) break;
+        // A large-angle event whose clock fired in the previous step is sampled here,
+        // outside the step body, before the history's next step; each history keeps its
+        // own order of operations and random numbers.
+        if (jm >= 0) {
+            int k;
+            float f;
+            grid_pos(P, jE, k, f);  // the table position the step's lookup used
+            const uint32_t nj = n - 1u;
+            JumpOut o = do_jump<CUT>(P, jm, jE, k, f, philox(P, nj, kTagJumpA, h), ux, uy, uz, tau, h, nj, jsc);
+            ux = o.ux;
+            uy = o.uy;
+            uz = o.uz;
+            tau = o.tau;
+            jm = -1;
+            if (o.kind == 2) {
+                const float Ej = E * o.e_fac;  // E is still the step's post-loss energy E1
+                SDE_BLOCK_ADD(kCntRemoved, qfix(P, E) - qfix(P, Ej));
+                SDE_BLOCK_ADD(kCntJumpInel, 1);
+                E = Ej;
+            } else if (o.kind == 1) {
+                SDE_BLOCK_ADD(kCntJumpEl, 1);
+            }
+            if (E < P.e_min) {  // absorbed, as at the end of a step
+                unsigned long long qr = qfix(P, E);
+                if (qr) {
+                    if (vcur >= 0)
+                        atomicAdd(&P.edep[vcur], qr);
+                    else
+                        SDE_BLOCK_ADD(kCntEscaped, qr);
+                }
+                SDE_BLOCK_ADD(kCntSteps, n);
+                alive = false;
+            }
+        }
         if (!alive) continue;
 
         if (n >= (uint32_t)P.max_steps || vcur < 0) {  // step cap, or R_n outside the domain D
@@ -515,8 +571,15 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
         const uint4 xcur = x;
         x = philox(P, n + 1u, kTagStep, h);
         const unsigned long long q0 = qfix(P, E);
-        float E1;
-        int jump = sde_step<CUT>(P, tab, m, rho, xcur, E, ux, uy, uz, tau, h, n, E1);
+        float E1, s_c;
+        Phys ph;
+        const bool fired = sde_step_cont<CUT>(P, tab, m, rho, xcur, E, ux, uy, uz, tau, E1, s_c, ph);
+        if (fired) {  // the event waits; the step's deposit does not depend on it
+            jm = m;
+            jE = E;
+            jsc = s_c;
+        }
+        E = E1;
         unsigned long long q1 = qfix(P, E1);
         unsigned long long dq = q0 - q1;
         if (TALLY == 0) {
@@ -543,18 +606,10 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
                                                    ouz * P.step_mm, dq);
             if (esc) SDE_BLOCK_ADD(kCntEscaped, esc);
         }
-        if (jump) {
-            if (jump == 2) {
-                SDE_BLOCK_ADD(kCntRemoved, q1 - qfix(P, E));
-                SDE_BLOCK_ADD(kCntJumpInel, 1);
-            } else {
-                SDE_BLOCK_ADD(kCntJumpEl, 1);
-            }
-        }
         n += 1;
         vcur = vnext;
         vox = vox_next;
-        if (E < P.e_min) {  // absorbed; the rest is deposited where the proton is
+        if (!fired && E < P.e_min) {  // absorbed; the rest is deposited where the proton is
             unsigned long long qr = qfix(P, E);
             if (qr) {
                 if (vcur >= 0)
