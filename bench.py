@@ -41,7 +41,7 @@ SMS = 152
 LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per clock each
 # DRAM traffic (read + write bytes) per transport launch from the ncu capture of the
 # same launch configuration; None until captured for the current kernel.
-TRANSPORT_DRAM_BYTES = 318_644_480  # 84.13 MB read + 234.52 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
+TRANSPORT_DRAM_BYTES = 77_126_400  # 64.25 MB read + 12.88 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
 
 CT_DESC = ("ct_sobp: thorax-like synthetic CT 120x120x240 mm at 1 mm (air, lung, adipose, soft tissue, "
            "cortical bone from HU), 16-layer spread-out Bragg peak 90-140 mm, 256 spots, 1e6 protons per GPU")
@@ -331,6 +331,9 @@ def main():
                     help="slab150 (default) or ct_sobp: thorax-like synthetic CT with a 16-layer spread-out Bragg peak")
     ap.add_argument("--theta-cut-sigmas", type=float, default=0.0,
                     help="energy-dependent elastic cut-off theta_c = k sigma(E) (0: the paper's fixed 0.02 rad)")
+    ap.add_argument("--physics-mask", type=int, default=15,
+                    help="ablation: SDE_PHYS_* bits of the transport (15 = all terms; 11 = no large-angle "
+                         "elastic events, 3 = no jumps); a run with terms switched off is not the benchmark")
     ap.add_argument("--no-denoiser", action="store_true",
                     help="skip the learned-vs-plain time-to-dose and the denoiser throughput")
     ap.add_argument("--plan", action="store_true",
@@ -354,7 +357,7 @@ def main():
     wl = (ct_sobp if args.workload == "ct_sobp" else slab150)(args.histories * ws)
     first, count = S.history_shard(wl.n_histories, rank, ws)
     stream = torch.cuda.Stream(device=dev)
-    d = S.SdeDose(wl, stream=stream, theta_cut_sigmas=args.theta_cut_sigmas)
+    d = S.SdeDose(wl, stream=stream, theta_cut_sigmas=args.theta_cut_sigmas, physics_mask=args.physics_mask)
     spots_dev = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     seed_base = 1_000_003
@@ -466,6 +469,7 @@ def main():
                    "l2": "flushed (256 MB write) before every timed step", "tally": "int64 fixed point 2^-24 MeV",
                    "elastic_cut_off": (f"theta_c = {args.theta_cut_sigmas} sigma(E)" if args.theta_cut_sigmas > 0
                                        else "fixed 0.02 rad"),
+                   "physics_mask": args.physics_mask,
                    "tuning": d.get_tuning()},
         "e2e": {"value": hist_per_step / e2e_T, "unit": "histories/s",
                 "h2d_bytes_per_step": int(wl.spots.nbytes),
