@@ -38,7 +38,8 @@ __device__ __forceinline__ Phys lookup(const float4* tab, const KParams& P, int 
     int k;
     float f;
     grid_pos(P, E, k, f);
-    const float4* r = tab + ((size_t)m * P.N + k) * kRowFloat4;
+    // at most 16 materials x 4096 points x 3 rows: a 32-bit offset
+    const float4* r = tab + (uint32_t)(m * P.N + k) * (uint32_t)kRowFloat4;
     float4 a = r[0], b = r[1], c = r[2];
     const float mp = (float)kProtonMass;
     float tot = E + mp;
@@ -260,8 +261,8 @@ __device__ __forceinline__ bool sde_step_cont(const KParams& P, const float4* ta
                                               float& E1_out, float& s_c_out, Phys& ph_out) {
     Phys ph = lookup(tab, P, m, E);
     float c = rho * ph.c;                   // varsigma_1 Delta
-    float s = sqrtf(rho) * ph.s * P.strag_on;  // varsigma_2 sqrt(Delta)
-    float r = sqrtf(-2.f * __logf(u01(x.x)));
+    float s = step_sqrt(rho) * ph.s * P.strag_on;  // varsigma_2 sqrt(Delta)
+    float r = step_sqrt(-2.f * __logf(u01(x.x)));
     float zE = r * __cosf(kTwoPiF * u01(x.y));
     // The clamp keeps the energy non-increasing (Eq. VSDE); in FP32 (E - c) + c can
     // round one ulp above E, which would make the step's fixed-point deposit negative.
