@@ -77,7 +77,7 @@ __device__ __forceinline__ float cut_s(float th2) {
 // large_elastic_cm and its hydrogen form): R (1/s_c - 1/2) + Hc G(s_c) - Hc G(mu_lo),
 // from the coefficient rows (times E^2).
 __device__ __forceinline__ float cut_rate(const KParams& P, int m, const Phys& ph, float E, float s_c) {
-    const float4* r = P.cut + ((size_t)m * P.N + ph.k) * 2;
+    const float4* r = P.cut + (uint32_t)(m * P.N + ph.k) * 2u;
     float4 a = __ldg(r), b = __ldg(r + 1);
     float R = fmaf(a.y, ph.f, a.x), Hc = fmaf(a.w, ph.f, a.z), Hlo = fmaf(b.y, ph.f, b.x);
     float rate = R * (__fdividef(1.f, s_c) - 0.5f) - Hlo;
@@ -103,7 +103,7 @@ __device__ void mott_sample(float U, float eta, float s_cut, float s_back, float
     float target = g_lo + U * (g_hi - g_lo);
     float sg = target >= 0.f ? 1.f : -1.f;
     float y = fabsf(target);
-    float q = sqrtf(1.f + y * y);
+    float q = step_sqrt(1.f + y * y);
     float s = __fdividef(1.f + __fdividef(1.f, q + y), 1.f + q);  // root without the sine term
     float s_min = sg > 0.f ? s_cut : s_back;
 #pragma unroll 1
@@ -117,7 +117,7 @@ __device__ void mott_sample(float U, float eta, float s_cut, float s_back, float
         s = fminf(fmaxf(s + __fdividef(G - y, dG), s_min), 1.f);
     }
     c = sg * (1.f - s);
-    sn = sqrtf(s * (2.f - s));
+    sn = step_sqrt(s * (2.f - s));
 }
 
 // Kalbach-Mann angular law a/(2 sinh a) (cosh(a mu) + r sinh(a mu)): the CDF
@@ -148,7 +148,7 @@ __device__ float kalbach_a(float E, float u, float A) {
 __device__ void cm_to_lab(float E, float Eout, bool elastic, float m2, float cc, float sc, float& cl,
                           float& sl) {
     const float mp = (float)kProtonMass;
-    float p1 = sqrtf(E * (E + 2.f * mp)), Et = E + mp;
+    float p1 = step_sqrt(E * (E + 2.f * mp)), Et = E + mp;
     float ucm = p1 / (Et + m2);
     float gu = rsqrtf((1.f - ucm) * (1.f + ucm));
     float v;
@@ -181,7 +181,7 @@ __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k,
                                         float uy, float uz, float tau, uint64_t h, uint32_t n, float s_c) {
     JumpOut o{ux, uy, uz, tau, 1.f, 0};
     const MatJump& mj = P.mats[m];
-    const float* r0 = P.jrates + ((size_t)m * P.N + k) * (2 * SDE_MAX_ELEMENTS);
+    const float* r0 = P.jrates + (uint32_t)(m * P.N + k) * (uint32_t)(2 * SDE_MAX_ELEMENTS);
     const float* r1 = r0 + 2 * SDE_MAX_ELEMENTS;
     const float rE2 = __fdividef(1.f, E * E);  // elastic rates are stored times E^2
     const float eta_h = (float)kFineStructure * rsqrtf(2.f * E / (float)kProtonMass);
@@ -226,7 +226,7 @@ __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k,
             float span = CUT ? __fdividef(1.f, s_c) - 0.5f : P.ruth_span;
             float s = __fdividef(1.f, 0.5f + u01(J.y) * span);
             cc = 1.f - s;
-            sc = sqrtf(s * (2.f - s));
+            sc = step_sqrt(s * (2.f - s));
         }
         cm_to_lab(E, E, true, m2, cc, sc, cl, sl);
     } else {
@@ -342,11 +342,11 @@ __device__ SDE_INIT_ATTR void init_history(const KParams& P, uint64_t h, float& 
     const SpotDev& s = P.spots[lo];
     uint4 A = philox(P, 0u, kTagSrcA, h);
     uint4 B = philox(P, 0u, kTagSrcB, h);
-    float r = sqrtf(-2.f * __logf(u01(A.x)));
+    float r = step_sqrt(-2.f * __logf(u01(A.x)));
     float sa, ca;
     __sincosf(kTwoPiF * u01(A.y), &sa, &ca);
     float g1 = r * ca, g2 = r * sa;
-    float g3 = sqrtf(-2.f * __logf(u01(A.z))) * __cosf(kTwoPiF * u01(A.w));
+    float g3 = step_sqrt(-2.f * __logf(u01(A.z))) * __cosf(kTwoPiF * u01(A.w));
     E = fminf(fmaxf(s.E + s.sE * g3, P.e_min), P.e_max);
     px = s.px + s.sxy * (g1 * s.e1x + g2 * s.e2x);
     py = s.py + s.sxy * (g1 * s.e1y + g2 * s.e2y);
@@ -477,45 +477,48 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
 
     for (;;) {
         unsigned dead = __ballot_sync(0xffffffffu, !alive);
-        if (dead != 0xffffffffu && __popc(dead) < P.refill_min) dead = 0;  // refill later
-        while (dead && !drained) {
-            unsigned long long b_next = *s_next, b_end = *s_end;
-            if (b_next >= b_end) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&P.counters[kCntCursor], (unsigned long long)P.batch);
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (base >= total) {
-                    drained = true;
-                    break;
+        // refill when the whole warp is idle, or at least refill_min lanes are; once
+        // started, until every lane is busy or the queue is drained
+        if (dead == 0xffffffffu || (dead && __popc(dead) >= P.refill_min)) {
+            while (dead && !drained) {
+                unsigned long long b_next = *s_next, b_end = *s_end;
+                if (b_next >= b_end) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(&P.counters[kCntCursor], (unsigned long long)P.batch);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (base >= total) {
+                        drained = true;
+                        break;
+                    }
+                    b_next = base;
+                    b_end = min(base + (unsigned long long)P.batch, total);
                 }
-                b_next = base;
-                b_end = min(base + (unsigned long long)P.batch, total);
+                int nd = __popc(dead);
+                unsigned long long avail = b_end - b_next;
+                int take = (unsigned long long)nd < avail ? nd : (int)avail;
+                int rank = __popc(dead & ((1u << lane) - 1u));
+                if (((dead >> lane) & 1u) && rank < take) {
+                    h = b_next + (unsigned long long)rank;
+                    init_history(P, h, E, px, py, pz, ux, uy, uz, tau);
+                    SDE_BLOCK_ADD(kCntIncident, qfix(P, E));
+                    SDE_BLOCK_ADD(kCntHistories, 1);
+                    n = 0;
+                    alive = true;
+                    vcur = voxel_index(P, px, py, pz);
+                    vox = vcur >= 0 ? __ldg(&P.vox[vcur]) : 0u;
+                    x = philox(P, 0u, kTagStep, h);
+                }
+                b_next += (unsigned long long)take;
+                __syncwarp();
+                if (lane == 0) {
+                    *s_next = b_next;
+                    *s_end = b_end;
+                }
+                __syncwarp();
+                dead = __ballot_sync(0xffffffffu, !alive);
             }
-            int nd = __popc(dead);
-            unsigned long long avail = b_end - b_next;
-            int take = (unsigned long long)nd < avail ? nd : (int)avail;
-            int rank = __popc(dead & ((1u << lane) - 1u));
-            if (((dead >> lane) & 1u) && rank < take) {
-                h = b_next + (unsigned long long)rank;
-                init_history(P, h, E, px, py, pz, ux, uy, uz, tau);
-                SDE_BLOCK_ADD(kCntIncident, qfix(P, E));
-                SDE_BLOCK_ADD(kCntHistories, 1);
-                n = 0;
-                alive = true;
-                vcur = voxel_index(P, px, py, pz);
-                vox = vcur >= 0 ? __ldg(&P.vox[vcur]) : 0u;
-                x = philox(P, 0u, kTagStep, h);
-            }
-            b_next += (unsigned long long)take;
-            __syncwarp();
-            if (lane == 0) {
-                *s_next = b_next;
-                *s_end = b_end;
-            }
-            __syncwarp();
-            dead = __ballot_sync(0xffffffffu, !alive);
         }
-        if (!__any_sync(0xffffffffu, alive)) break;
+        if (dead == 0xffffffffu) break;  // queue drained and every lane idle
         // A large-angle event whose clock fired in the previous step is sampled here,
         // outside the step body, before the history's next step; each history keeps its
         // own order of operations and random numbers.
