@@ -725,13 +725,22 @@ __global__ void k_probe(const __grid_constant__ KParams P, int m, float rho, flo
     uyo[i] = uy;
 }
 
-// Dose to medium (Sec. 2.2.2): tally units -> J over voxel mass (kg).
+// Dose to medium (Sec. 2.2.2): tally units -> J over voxel mass (kg).  The FP64 unit of
+// this GPU is narrow and a double division is a long sequence on it, so 1/mass is the
+// FP32 reciprocal refined by one Newton step in FP64 (relative error ~1e-14).
 template <typename T>
 __global__ void k_convert(const unsigned long long* edep, const float* rho, size_t nv, double unit_J,
                           double vol_kg_per_rho, T* dose) {
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
-        double mass = (double)rho[v] * vol_kg_per_rho;
-        dose[v] = (T)(mass > 0.0 ? (double)edep[v] * unit_J / mass : 0.0);
+        const float r = rho[v];
+        double out = 0.0;
+        if (r > 0.f) {
+            const double mass = (double)r * vol_kg_per_rho;
+            double y = (double)__frcp_rn(__double2float_rn(mass));
+            y = fma(y, fma(-mass, y, 1.0), y);
+            out = (double)edep[v] * unit_J * y;
+        }
+        dose[v] = (T)out;
     }
 }
 
