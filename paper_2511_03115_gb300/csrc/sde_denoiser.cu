@@ -104,21 +104,42 @@ __device__ __forceinline__ void st8(bf16* p, const float (&f)[8]) {
 
 #define SDE_GRID_LOOP(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
+// Coarse-voxel kernels (pooling, upsampling) run one thread per (coarse voxel, 8-channel
+// group) on the grid (ceil(Wc G / 256), Hc, Dc batch) with 256 threads, G = C/8 a power of
+// two: no integer division per element.
+struct CoarseIdx {
+    int q, xc, yc, zc, b;
+    size_t vc;  // b Vc + (zc Hc + yc) Wc + xc
+};
+__device__ __forceinline__ bool coarse_idx(const Grid2& g, int G, CoarseIdx& c) {
+    const int Wc = g.W >> 1, Hc = g.H >> 1, Dc = g.D >> 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Wc * G) return false;
+    c.q = t & (G - 1);
+    c.xc = t >> (__ffs(G) - 1);
+    c.yc = blockIdx.y;
+    c.zc = blockIdx.z % Dc;
+    c.b = blockIdx.z / Dc;
+    c.vc = (((size_t)c.b * Dc + c.zc) * Hc + c.yc) * Wc + c.xc;
+    return true;
+}
+// fine voxel (with batch) of child d of c: (2 zc + d/4, 2 yc + (d/2)%2, 2 xc + d%2)
+__device__ __forceinline__ size_t fine_of(const Grid2& g, const CoarseIdx& c, int d) {
+    return (((size_t)c.b * g.D + 2 * c.zc + (d >> 2)) * g.H + 2 * c.yc + ((d >> 1) & 1)) * g.W + 2 * c.xc + (d & 1);
+}
+
 // out[b][vc][c] = mean of the 8 children of vc in in[b][v][ico + c] (row stride ics)
-__global__ void k_avgpool2(const bf16* __restrict__ in, int ics, int ico, int C, Grid2 g, int batch,
-                           bf16* __restrict__ out) {
-    const int G = C >> 3, Vf = g.D * g.H * g.W, Vc = Vf >> 3;
-    SDE_GRID_LOOP(i, Vc * batch * G) {
-        const int q = i % G, r = i / G, vc = r % Vc, b = r / Vc;
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int d = 0; d < 8; ++d) {
-            float f[8];
-            ld8(in + ((size_t)b * Vf + g.child(vc, d)) * ics + ico + 8 * q, f);
-            for (int e = 0; e < 8; ++e) acc[e] += f[e];
-        }
-        for (int e = 0; e < 8; ++e) acc[e] *= 0.125f;
-        st8(out + ((size_t)b * Vc + vc) * C + 8 * q, acc);
+__global__ void k_avgpool2(const bf16* __restrict__ in, int ics, int ico, int C, Grid2 g, bf16* __restrict__ out) {
+    CoarseIdx c;
+    if (!coarse_idx(g, C >> 3, c)) return;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int d = 0; d < 8; ++d) {
+        float f[8];
+        ld8(in + fine_of(g, c, d) * ics + ico + 8 * c.q, f);
+        for (int e = 0; e < 8; ++e) acc[e] += f[e];
     }
+    for (int e = 0; e < 8; ++e) acc[e] *= 0.125f;
+    st8(out + c.vc * C + 8 * c.q, acc);
 }
 
 // din[b][v][c] = dout[b][parent(v)][c] / 8 + add[b][v][aco + c]   (add may be NULL)
@@ -139,15 +160,23 @@ __global__ void k_avgpool2_bwd(const bf16* __restrict__ dout, const bf16* __rest
     }
 }
 
-// out[b][v][oco + c] = in[b][parent(v)][c]   (nearest-neighbour upsampling)
-__global__ void k_upsample2(const bf16* __restrict__ in, int C, Grid2 g, int batch, bf16* __restrict__ out, int ocs,
-                            int oco) {
-    const int G = C >> 3, Vf = g.D * g.H * g.W, Vc = Vf >> 3;
-    SDE_GRID_LOOP(i, Vf * batch * G) {
-        const int q = i % G, r = i / G, v = r % Vf, b = r / Vf;
-        *reinterpret_cast<uint4*>(out + ((size_t)b * Vf + v) * ocs + oco + 8 * q) =
-            *reinterpret_cast<const uint4*>(in + ((size_t)b * Vc + g.coarse_of(v)) * C + 8 * q);
-    }
+// out[b][v][oco + c] = in[b][parent(v)][c]   (nearest-neighbour upsampling): each coarse
+// 8-channel group is read once and written to its 8 children.
+__global__ void k_upsample2(const bf16* __restrict__ in, int C, Grid2 g, bf16* __restrict__ out, int ocs, int oco) {
+    CoarseIdx c;
+    if (!coarse_idx(g, C >> 3, c)) return;
+    const uint4 val = *reinterpret_cast<const uint4*>(in + c.vc * C + 8 * c.q);
+    for (int d = 0; d < 8; ++d) *reinterpret_cast<uint4*>(out + fine_of(g, c, d) * ocs + oco + 8 * c.q) = val;
+}
+
+// Launch geometry of the coarse-voxel kernels (C/8 must be a power of two).
+static bool coarse_grid(const Grid2& g, int C, int batch, dim3& grid) {
+    const int G = C >> 3;
+    if (C % 8 || G <= 0 || (G & (G - 1)) || (g.D | g.H | g.W) & 1) return false;
+    const long long z = (long long)(g.D >> 1) * batch;
+    if (z > 65535 || (g.H >> 1) > 65535) return false;
+    grid = dim3((unsigned)(((g.W >> 1) * G + 255) / 256), (unsigned)(g.H >> 1), (unsigned)z);
+    return true;
 }
 
 // dout[b][vc][c] = sum over the 8 children of din[b][v][ico + c]
@@ -470,16 +499,23 @@ int forward(sde_denoiser* d, const float* dose_low, const float* rho, int batch)
     Layer* L = d->L;
     DN_TRY(conv(d, d->in0, batch, D, H, W, L[0], L[0].w16, 32, d->e1a, 32, 0, false, true, L[0].b32));
     DN_TRY(conv(d, d->e1a, batch, D, H, W, L[1], L[1].w16, 32, d->cat1, 96, 64, false, true, L[1].b32));
-    k_avgpool2<<<kBlocks, 256, 0, d->st>>>(d->cat1, 96, 64, 32, g1, batch, d->p1);
+    dim3 grid;
+    if (!coarse_grid(g1, 64, batch, grid) || !coarse_grid(g2, 128, batch, grid))
+        return fail(cudaErrorInvalidValue, "pooling grid");
+    coarse_grid(g1, 32, batch, grid);
+    k_avgpool2<<<grid, 256, 0, d->st>>>(d->cat1, 96, 64, 32, g1, d->p1);
     DN_TRY(conv(d, d->p1, batch, D2, H2, W2, L[2], L[2].w16, 64, d->e2a, 64, 0, false, true, L[2].b32));
     DN_TRY(conv(d, d->e2a, batch, D2, H2, W2, L[3], L[3].w16, 64, d->cat2, 192, 128, false, true, L[3].b32));
-    k_avgpool2<<<kBlocks, 256, 0, d->st>>>(d->cat2, 192, 128, 64, g2, batch, d->p2);
+    coarse_grid(g2, 64, batch, grid);
+    k_avgpool2<<<grid, 256, 0, d->st>>>(d->cat2, 192, 128, 64, g2, d->p2);
     DN_TRY(conv(d, d->p2, batch, D3, H3, W3, L[4], L[4].w16, 128, d->b1, 128, 0, false, true, L[4].b32));
     DN_TRY(conv(d, d->b1, batch, D3, H3, W3, L[5], L[5].w16, 128, d->b2, 128, 0, false, true, L[5].b32));
-    k_upsample2<<<kBlocks, 256, 0, d->st>>>(d->b2, 128, g2, batch, d->cat2, 192, 0);
+    coarse_grid(g2, 128, batch, grid);
+    k_upsample2<<<grid, 256, 0, d->st>>>(d->b2, 128, g2, d->cat2, 192, 0);
     DN_TRY(conv(d, d->cat2, batch, D2, H2, W2, L[6], L[6].w16, 64, d->d2a, 64, 0, false, true, L[6].b32));
     DN_TRY(conv(d, d->d2a, batch, D2, H2, W2, L[7], L[7].w16, 64, d->d2, 64, 0, false, true, L[7].b32));
-    k_upsample2<<<kBlocks, 256, 0, d->st>>>(d->d2, 64, g1, batch, d->cat1, 96, 0);
+    coarse_grid(g1, 64, batch, grid);
+    k_upsample2<<<grid, 256, 0, d->st>>>(d->d2, 64, g1, d->cat1, 96, 0);
     DN_TRY(conv(d, d->cat1, batch, D, H, W, L[8], L[8].w16, 32, d->d1a, 32, 0, false, true, L[8].b32));
     DN_TRY(conv(d, d->d1a, batch, D, H, W, L[9], L[9].w16, 32, d->d1, 32, 0, false, true, L[9].b32));
     DN_TRY(conv(d, d->d1, batch, D, H, W, L[10], L[10].w16, 16, d->out, 16, 0, true, false, L[10].b32));
