@@ -331,6 +331,7 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
     P.inv_hz = (float)(1.0 / d->h[2]);
     P.step_mm = (float)(d->p.step_cm * 10.0);
     P.half_step_mm = (float)(d->p.step_cm * 5.0);
+    P.inv_delta_cm = (float)(1.0 / d->p.step_cm);
     P.e_min = (float)d->p.e_min_MeV;
     P.e_max = (float)d->p.e_max_MeV;
     P.qscale = (float)ldexp(1.0, d->p.fixed_point_shift);

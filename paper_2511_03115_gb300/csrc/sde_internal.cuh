@@ -66,6 +66,7 @@ struct KParams {
     int nx, ny, nz, n_mats;
     float inv_hx, inv_hy, inv_hz;
     float step_mm, half_step_mm;
+    float inv_delta_cm;  // 1 / Delta (1/cm): jump rates x Delta back to rates
     float e_min, e_max;
     float qscale;  // 2^S
     int max_steps, mask, tally_mode, N;

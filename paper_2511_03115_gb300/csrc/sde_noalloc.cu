@@ -186,6 +186,7 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     P.inv_hz = (float)(1.0 / voxel_mm[2]);
     P.step_mm = (float)(p.step_cm * 10.0);
     P.half_step_mm = (float)(p.step_cm * 5.0);
+    P.inv_delta_cm = (float)(1.0 / p.step_cm);
     P.e_min = (float)p.e_min_MeV;
     P.e_max = (float)p.e_max_MeV;
     P.qscale = (float)ldexp(1.0, p.fixed_point_shift);

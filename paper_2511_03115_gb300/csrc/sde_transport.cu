@@ -174,11 +174,14 @@ struct JumpOut {
 
 // A large-angle event of Eq. Npi at pre-step energy E (table interval k, fraction f):
 // pick channel and element by rate, sample the CM angle, convert to the lab, rotate.
+// sj = the step's total jump rate x Delta per unit density (the clock's rate), so the
+// per-element rates need only be summed until the pick.
 // CUT: the energy-dependent cut-off s_c = 1 - cos(theta_c) of this step (compiled
 // separately so that the fixed-cut-off kernel carries none of it).
 template <bool CUT>
 __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k, float f, uint4 J, float ux,
-                                        float uy, float uz, float tau, uint64_t h, uint32_t n, float s_c) {
+                                        float uy, float uz, float tau, uint64_t h, uint32_t n, float s_c,
+                                        float sj) {
     JumpOut o{ux, uy, uz, tau, 1.f, 0};
     const MatJump& mj = P.mats[m];
     const float* r0 = P.jrates + (uint32_t)(m * P.N + k) * (uint32_t)(2 * SDE_MAX_ELEMENTS);
@@ -194,12 +197,7 @@ __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k,
         float glo = -mott_prim(P.s_back, eta_h);
         scale_H *= (mott_prim(s_c, eta_h) - glo) / (mott_prim(P.s_cut, eta_h) - glo);
     }
-    float total = 0.f;
-    for (int i = 0; i < mj.n_el; ++i) {
-        total += fmaf(r1[i] - r0[i], f, r0[i]) * (mj.Z[i] == 1 ? scale_H : scale_R);
-        total += fmaf(r1[SDE_MAX_ELEMENTS + i] - r0[SDE_MAX_ELEMENTS + i], f, r0[SDE_MAX_ELEMENTS + i]);
-    }
-    float target = u01(J.x) * total, acc = 0.f;
+    float target = u01(J.x) * (sj * P.inv_delta_cm), acc = 0.f;
     int pick = -1, last = -1;
     for (int ch = 0; ch < 2 && pick < 0; ++ch)
         for (int i = 0; i < mj.n_el; ++i) {
@@ -258,7 +256,7 @@ __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k,
 template <bool CUT>
 __device__ __forceinline__ bool sde_step_cont(const KParams& P, const float4* tab, int m, float rho, uint4 x,
                                               float E, float& ux, float& uy, float& uz, float& tau,
-                                              float& E1_out, float& s_c_out, Phys& ph_out) {
+                                              float& E1_out, float& s_c_out, Phys& ph_out, float& sj_out) {
     Phys ph = lookup(tab, P, m, E);
     float c = rho * ph.c;                   // varsigma_1 Delta
     float s = step_sqrt(rho) * ph.s * P.strag_on;  // varsigma_2 sqrt(Delta)
@@ -292,6 +290,7 @@ __device__ __forceinline__ bool sde_step_cont(const KParams& P, const float4* ta
         sj = cut_rate(P, m, ph, E, s_c) + ph.sn;
     }
     s_c_out = s_c;
+    sj_out = sj;
     ph_out = ph;
     tau -= rho * sj;
     return tau <= 0.f;
@@ -304,11 +303,11 @@ template <bool CUT>
 __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int m, float rho, uint4 x,
                                         float& E, float& ux, float& uy, float& uz, float& tau, uint64_t h,
                                         uint32_t n, float& E1_out) {
-    float E1, s_c;
+    float E1, s_c, sj;
     Phys ph;
     int jump = 0;
-    if (sde_step_cont<CUT>(P, tab, m, rho, x, E, ux, uy, uz, tau, E1, s_c, ph)) {
-        JumpOut o = do_jump<CUT>(P, m, E, ph.k, ph.f, philox(P, n, kTagJumpA, h), ux, uy, uz, tau, h, n, s_c);
+    if (sde_step_cont<CUT>(P, tab, m, rho, x, E, ux, uy, uz, tau, E1, s_c, ph, sj)) {
+        JumpOut o = do_jump<CUT>(P, m, E, ph.k, ph.f, philox(P, n, kTagJumpA, h), ux, uy, uz, tau, h, n, s_c, sj);
         ux = o.ux;
         uy = o.uy;
         uz = o.uz;
@@ -463,9 +462,9 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
     unsigned long long h = 0;
     uint32_t n = 0;
     // Pending large-angle event of step n - 1: the material of that step (-1: none),
-    // its pre-step energy and its cut-off.
+    // its pre-step energy, its cut-off and its total jump rate.
     int jm = -1;
-    float jE = 0.f, jsc = 0.f;
+    float jE = 0.f, jsc = 0.f, jsj = 0.f;
     // Software pipeline: the voxel word of R_n and the Philox block of step n are
     // fetched/computed during step n-1, so their latency overlaps the step's work.
     uint32_t vox = 0;
@@ -527,7 +526,8 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
             float f;
             grid_pos(P, jE, k, f);  // the table position the step's lookup used
             const uint32_t nj = n - 1u;
-            JumpOut o = do_jump<CUT>(P, jm, jE, k, f, philox(P, nj, kTagJumpA, h), ux, uy, uz, tau, h, nj, jsc);
+            JumpOut o =
+                do_jump<CUT>(P, jm, jE, k, f, philox(P, nj, kTagJumpA, h), ux, uy, uz, tau, h, nj, jsc, jsj);
             ux = o.ux;
             uy = o.uy;
             uz = o.uz;
@@ -575,13 +575,14 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
         const uint4 xcur = x;
         x = philox(P, n + 1u, kTagStep, h);
         const unsigned long long q0 = qfix(P, E);
-        float E1, s_c;
+        float E1, s_c, sj;
         Phys ph;
-        const bool fired = sde_step_cont<CUT>(P, tab, m, rho, xcur, E, ux, uy, uz, tau, E1, s_c, ph);
+        const bool fired = sde_step_cont<CUT>(P, tab, m, rho, xcur, E, ux, uy, uz, tau, E1, s_c, ph, sj);
         if (fired) {  // the event waits; the step's deposit does not depend on it
             jm = m;
             jE = E;
             jsc = s_c;
+            jsj = sj;
         }
         E = E1;
         unsigned long long q1 = qfix(P, E1);
