@@ -41,7 +41,7 @@ SMS = 152
 LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per clock each
 # DRAM traffic (read + write bytes) per transport launch from the ncu capture of the
 # same launch configuration; None until captured for the current kernel.
-TRANSPORT_DRAM_BYTES = 76_002_304  # 62.31 MB read + 13.69 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
+TRANSPORT_DRAM_BYTES = 70_678_528  # 60.26 MB read + 10.42 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
 
 CT_DESC = ("ct_sobp: thorax-like synthetic CT 120x120x240 mm at 1 mm (air, lung, adipose, soft tissue, "
            "cortical bone from HU), 16-layer spread-out Bragg peak 90-140 mm, 256 spots, 1e6 protons per GPU")
