@@ -217,3 +217,36 @@ def test_trained_denoiser_gains_over_the_low_history_dose(sde_gpu):
     assert agg["gamma_denoised"] > agg["gamma_low"] + 0.02
     assert agg["max_err_denoised"] < agg["max_err_low"]
     net.close()
+
+
+def test_learned_dose_against_an_fp64_oracle_dose(sde_gpu, oracle_lib):
+    """The learned dose of a held-out plan (10^5 GPU histories + the trained network of
+    the repository) judged against a dose of the FP64 oracle for the same plan (10^6
+    histories, independent random numbers): closer to it than the 10^5-history dose, by
+    gamma 2 %/0.5 mm and by the maximum error relative to the oracle's maximum.  The
+    10^7-history GPU dose against the same oracle dose shows how much of what remains is
+    the oracle dose's own noise."""
+    import os
+    import torch
+    from paper_2511_03115_gb300 import denoise as DN
+    from sde_workloads import denoise_case
+    weights = os.path.join(os.path.dirname(DN.__file__), "weights", "denoiser_128x128x192.npy")
+    net = sde_gpu.Denoiser(DN.SHAPE[2], DN.SHAPE[1], DN.SHAPE[0], batch_max=1, seed=1)
+    net.set_params(np.load(weights).astype(np.float32))
+    seed = 100_000  # first held-out plan
+    r = DN.transport_doses(seed)
+    learned = net.infer(r["low"], r["density"])
+    sde_gpu.denoise_status()
+    net.close()
+    n_oracle = 1_000_000
+    oracle_lib.set_threads(0)  # every host core
+    dose_o, _, bal = oracle_lib.run_workload(denoise_case(seed, n_oracle, shape=DN.SHAPE), seed=7)
+    assert bal["incident"] == bal["deposited"] + bal["escaped"] + bal["removed"]
+    ref = torch.from_numpy((dose_o * (DN.N_LOW / n_oracle)).astype(np.float32)).cuda()
+    high = sde_gpu.scale_(r["high"], DN.N_LOW / DN.N_HIGH)
+    rmax = float(ref.max())
+    res = {name: (sde_gpu.gamma3d(ref, d, (1.0, 1.0, 1.0)), float((d - ref).abs().max()) / rmax)
+           for name, d in (("low_1e5", r["low"]), ("learned", learned), ("plain_1e7", high))}
+    print({k: {"gamma": round(g, 4), "max_err": round(e, 4)} for k, (g, e) in res.items()})
+    assert res["learned"][0] > res["low_1e5"][0] + 0.02
+    assert res["learned"][1] < res["low_1e5"][1]
