@@ -5,12 +5,13 @@
 // Execution model: one proton history per lane.  Warps are persistent: a warp
 // claims a batch of history ids from a global cursor, hands them to its idle
 // lanes, and advances all live lanes one Euler-Maruyama step per iteration.
-// When lanes die (absorbed or escaped) the warp refills them from its batch
-// (ballot + popc ranks), so every warp keeps 32 lanes busy until the queue is
-// drained.  The per-step physics comes from FP32 tables staged in shared
-// memory; each step draws one Philox4x32-10 block keyed by (seed, history,
-// step); the energy lost in the step is committed as a 64-bit fixed-point
-// integer atomic, so the tally does not depend on execution order.
+// By default a warp refills only when all 32 lanes are idle (ballot + popc
+// ranks), so it carries a cohort of histories of one spot in lock-step.  The
+// per-step physics comes from FP32 tables read through L1 (optionally staged
+// in shared memory); each step draws one Philox4x32-10 block keyed by (seed,
+// history, step); a large-angle event is sampled out of line at the top of the
+// next iteration; the energy lost in the step is committed as a 64-bit
+// fixed-point integer atomic, so the tally does not depend on execution order.
 #include <math.h>
 
 #include "sde_internal.cuh"
