@@ -82,12 +82,28 @@ def test_create_rejects_bad_arguments_on_the_host(sde):
     assert rc == sde.SDE_EINVAL
 
 
+@pytest.mark.parametrize("bad", [dict(theta_cut_sigmas=-1.0), dict(e_max_MeV=1500.0),
+                                 dict(fixed_point_shift=31), dict(step_cm=2.0), dict(physics_mask=16),
+                                 dict(tally_mode=2), dict(max_steps=0), dict(km_r=1.0)])
+def test_params_outside_their_ranges_are_rejected_on_the_host(sde, bad):
+    # the fixed-point tally relies on E <= 1000 MeV and S <= 30 (every Q(E) below 2^40)
+    rc, msg = _create(sde, params=sde.default_params(**bad))
+    assert rc == sde.SDE_EINVAL and "params" in msg, bad
+
+
+def test_energy_dependent_cut_off_is_off_by_default(sde):
+    assert sde.default_params().theta_cut_sigmas == 0.0
+
+
 def test_null_handle_calls_fail_cleanly(sde):
     L = sde.lib()
     assert L.sde_dose_run(None, None, 0, 0) == sde.SDE_EINVAL
     assert L.sde_dose_fetch(None, None, None, None) == sde.SDE_EINVAL
     assert L.sde_dose_reset(None) == sde.SDE_EINVAL
     assert L.sde_dose_set_tuning(None, None) == sde.SDE_EINVAL
+    assert L.sde_dose_run_range(None, None, 0, 0, 0, 0) == sde.SDE_EINVAL
+    assert L.sde_dose_run_device_range(None, None, 0, 0, 0, 0) == sde.SDE_EINVAL
+    assert L.sde_dose_fetch_device_f32(None, None) == sde.SDE_EINVAL
     L.sde_dose_destroy(None)
 
 
