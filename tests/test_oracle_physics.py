@@ -265,6 +265,20 @@ def test_nonelastic_rate_of_water_is_about_one_percent_per_cm(oracle_lib):
     assert O.fn("oracle_sigma_ne_element_mb")(1, 150.0) == 0.0
 
 
+def test_total_jump_rates_are_the_sums_over_elements(oracle_lib):
+    """The jump clock runs on the total rates; the event picks its element from the
+    per-element rates.  Both must describe the same channel set: each total is the sum
+    of its per-element parts, in every material and at every energy."""
+    from sde_workloads import BONE, TISSUE
+    for mat in (WATER, BONE, TISSUE):
+        for E in (0.5, 5.0, 50.0, 150.0, 250.0):
+            ph = O.physics(mat, 1.3, E)
+            n = ph.n_el
+            assert n == len(mat["elements"])
+            assert ph.sig_e == pytest.approx(sum(ph.sig_e_el[i] for i in range(n)), rel=1e-12)
+            assert ph.sig_ne == pytest.approx(sum(ph.sig_ne_el[i] for i in range(n)), rel=1e-12, abs=1e-300)
+
+
 def test_physics_mask_switches_rates(oracle_lib):
     a = O.physics(WATER, 1.0, 50.0, physics_mask=O.PHYS_ALL)
     b = O.physics(WATER, 1.0, 50.0, physics_mask=O.PHYS_MCS)
