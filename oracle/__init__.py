@@ -105,6 +105,7 @@ def lib():
                                          C.POINTER(PhysicsOut)]
             L.oracle_csda_range.argtypes = [C.POINTER(Material), d, C.POINTER(Params), d,
                                             C.POINTER(d)]
+            L.oracle_sample_source.argtypes = [C.POINTER(Spot), C.POINTER(Params), u64, u64, i, dp, dp, dp]
             L.oracle_single_step.argtypes = [C.POINTER(Material), d, C.POINTER(Params), d, u64, u64,
                                              i, dp, dp, dp, dp, dp]
             for name, nargs in (("oracle_sample_mu_rutherford", 2), ("oracle_sample_mu_mott", 4),
@@ -274,6 +275,18 @@ def single_step(material, rho, E, n, seed=0, h0=0, **param_kw):
                                     C.c_uint64(h0), int(n), E_out.ctypes.data, cos_out.ctypes.data,
                                     jump.ctypes.data, ux.ctypes.data, uy.ctypes.data))
     return {"E": E_out, "cos": cos_out, "jump": jump, "ux": ux, "uy": uy}
+
+
+def sample_source(spot, n, seed=0, h0=0, **param_kw):
+    """Y_0 of n histories of one spot (a numpy spot record): energy, entry point, direction."""
+    arr = _spots(np.asarray([spot], dtype=spot.dtype) if hasattr(spot, "dtype") else spot)
+    p = params(**param_kw)
+    E = np.empty(n)
+    r = np.empty((n, 3))
+    u = np.empty((n, 3))
+    _check(lib().oracle_sample_source(arr, C.byref(p), C.c_uint64(seed), C.c_uint64(h0), int(n),
+                                      E.ctypes.data, r.ctypes.data, u.ctypes.data))
+    return E, r, u
 
 
 def coulomb_eta_k(Z, E):

@@ -13,7 +13,9 @@
  *                              2011, Random123 distribution), golden file
  *   varsigma_1 (Bethe) ....... NIST PSTAR / ICRU 49 water stopping powers and
  *                              CSDA ranges (golden file, 1-2 %: no corrections)
- *   varsigma_2 ............... Bohr's low-energy limit 0.1569 Z/A rho MeV^2/cm
+ *   varsigma_2 ............... Bohr's low-energy limit 0.1569 Z/A rho MeV^2/cm;
+ *                              the relativistic factor against a quadrature of
+ *                              the free-electron second moment at 50-250 MeV
  *   sigma(E) Lynch-Dahl ...... Highland formula within its stated 11 %
  *   Rutherford rate/sampler .. textbook Rutherford in E_cm and sin(theta/2)
  *   Mott (hydrogen) .......... textbook spin-1/2 Mott formula; antiderivative
@@ -21,6 +23,11 @@
  *   CM -> lab ................ explicit Lorentz boost of four-vectors; the
  *                              non-relativistic limit tan = sin/(cos + 1/A)
  *   Kalbach-Mann sampler ..... KS test against the CDF of the printed pdf
+ *   Kalbach slope a(E,u) ..... limits and breakpoints of Kalbach's 1988
+ *                              systematics (C1 slope, quartic coefficients
+ *                              below 41 MeV, saturation at 41 and 130 MeV)
+ *   source sampling .......... Gaussian-spot moments in an independent frame:
+ *                              entry plane, lateral, energy and angular variances
  *   Euler step ............... mean loss = varsigma_1 Delta exactly, clamped
  *                              Gaussian variance closed form, E[cos] = e^-t,
  *                              jump probability 1 - exp(-Delta sigma)
@@ -31,6 +38,9 @@
  *                              fluence-loss rate: the ENDF data the paper uses
  *                              is not available, a named public
  *                              parameterisation stands in (see below).
+ *   non-elastic laws ......... PARITY UNPINNED as stand-ins: u ~ U(0,1), r and
+ *                              Kalbach's a(E,u) replace the ENDF tables; a(E,u)
+ *                              itself is pinned to Kalbach's systematics above.
  *
  * Readings of passages that are silent, garbled or inconsistent are marked
  * "Reading:" beside the code.
@@ -955,6 +965,28 @@ int oracle_fetch(oracle_dose* d, double* dose_Gy, uint64_t* edep_fixed, oracle_b
         }
     }
     if (bal) *bal = d->bal;
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------ source-sampling probe */
+int oracle_sample_source(const oracle_spot* s, const oracle_params* p, uint64_t seed, uint64_t h0, int n,
+                         double* E_out, double* r_out, double* u_out) {
+    if (!s || !p || n < 0 || check_params(p)) return fail(ORACLE_EINVAL, "bad source-probe arguments");
+    double un = s->ux * s->ux + s->uy * s->uy + s->uz * s->uz;
+    if (!(un > 0.0) || !(s->sigma_E_MeV >= 0.0) || !(s->sigma_xy_mm >= 0.0) || !(s->sigma_angle_rad >= 0.0))
+        return fail(ORACLE_EINVAL, "bad spot");
+    oracle_dose d;
+    memset(&d, 0, sizeof d);
+    d.p = *p;
+    for (int i = 0; i < n; ++i) {
+        double E, r[3], u[3], tau;
+        sample_source(&d, s, seed, h0 + (uint64_t)i, &E, r, u, &tau);
+        if (E_out) E_out[i] = E;
+        for (int a = 0; a < 3; ++a) {
+            if (r_out) r_out[3 * (size_t)i + a] = r[a];
+            if (u_out) u_out[3 * (size_t)i + a] = u[a];
+        }
+    }
     return ORACLE_OK;
 }
 

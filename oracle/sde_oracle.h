@@ -141,6 +141,10 @@ int oracle_csda_range(const oracle_material* m, double rho, const oracle_params*
 int oracle_single_step(const oracle_material* m, double rho, const oracle_params* p, double E,
                        uint64_t seed, uint64_t h0, int n, double* E_out, double* cos_out,
                        int* jump_out, double* ux_out, double* uy_out);
+/* Y_0 of histories h = h0 .. h0+n-1 of one spot (the source sampling of a run): energy,
+ * entry point (mm, 3 per history) and direction (3 per history); any output may be NULL. */
+int oracle_sample_source(const oracle_spot* s, const oracle_params* p, uint64_t seed, uint64_t h0, int n,
+                         double* E_out, double* r_out, double* u_out);
 /* Samplers of the large-angle laws (U in (0,1)): CM cosine. */
 double oracle_sample_mu_rutherford(double U, double mu_c);
 double oracle_sample_mu_mott(double U, double eta, double mu_lo, double mu_c);

@@ -289,3 +289,120 @@ def test_physics_mask_switches_rates(oracle_lib):
 def test_bragg_additive_I_of_water_close_to_75eV(oracle_lib):
     ph = O.physics({"name": "w", "elements": WATER["elements"], "I_eV": 0.0}, 1.0, 100.0)
     assert 74.0 < ph.I_eV < 76.5
+
+
+# --------------------------------------------------------------- straggling variance
+RE_CM = 2.8179403262e-13  # classical electron radius, cm (CODATA 2018)
+ME = 0.51099895000        # electron rest energy, MeV
+
+
+def _s2sq_free_electrons(E, rho, exact_wmax):
+    """varsigma_2^2 = n_e int_0^Wmax W^2 dsigma/dW dW for the spin-1/2 free-electron cross
+    section of a heavy charged particle, dsigma/dW = 2 pi r_e^2 m_e c^2 / (beta^2 W^2)
+    (1 - beta^2 W / Wmax), by numerical quadrature.  Wmax is the exact two-body maximum
+    energy transfer, or its heavy-projectile limit 2 m_e c^2 beta^2 gamma^2 (the limit in
+    which the paper's straggling formula, Sec. 2.1.3, is written)."""
+    g = (E + MP) / MP
+    b2 = 1.0 - 1.0 / (g * g)
+    wmax = 2.0 * ME * b2 * g * g
+    if exact_wmax:
+        wmax /= 1.0 + 2.0 * g * ME / MP + (ME / MP) ** 2
+    n_e = NA * rho * _water_Z_over_A()
+    dsdw = lambda W: 2.0 * math.pi * RE_CM ** 2 * ME / (b2 * W * W) * (1.0 - b2 * W / wmax)
+    val, _ = integrate.quad(lambda W: W * W * dsdw(W), 0.0, wmax, epsabs=0, epsrel=1e-12)
+    return n_e * val
+
+
+@pytest.mark.parametrize("E", [50.0, 150.0, 250.0])
+def test_straggling_equals_the_free_electron_second_moment(oracle_lib, E):
+    """The relativistic factor gamma^2 (1 - beta^2/2) of varsigma_2^2 follows from the
+    second moment of the energy transfer to free electrons: the oracle equals the
+    quadrature with the heavy-projectile Wmax to 1e-6, and exceeds the exact-Wmax value by
+    the recoil factor 1 + 2 gamma m_e/m_p + (m_e/m_p)^2 (< 0.15 % here).  At 50-250 MeV the
+    factor itself is 1.05-1.31, so dropping it or either of its parts fails."""
+    s2 = O.physics(WATER, 1.0, E).s2sq
+    lim = _s2sq_free_electrons(E, 1.0, exact_wmax=False)
+    ex = _s2sq_free_electrons(E, 1.0, exact_wmax=True)
+    assert s2 == pytest.approx(lim, rel=1e-6)
+    g = (E + MP) / MP
+    recoil = 2.0 * g * ME / MP + (ME / MP) ** 2
+    assert 0.0 < s2 / ex - 1.0 <= recoil * (1.0 + 1e-5) + 1e-6
+    assert s2 / O.physics(WATER, 1.0, 0.05).s2sq > 1.04  # the factor is not 1 here
+
+
+# -------------------------------------------------------------- Kalbach slope a(E, u)
+# Kalbach (1988) systematics for the slope of the Kalbach-Mann law (the form the ENDF-6
+# manual prints, Sec. 6.2.3.2, for incident and emitted protons, M = m = 1):
+#   a = C1 X1 + C2 X1^3 + C3 X3^4,  X1 = R1 e_b/e_a, X3 = R3 e_b/e_a,
+#   R1 = min(e_a, 130 MeV), R3 = min(e_a, 41 MeV),  C1 = 0.04, C2 = 1.8e-6, C3 = 6.7e-7.
+# The oracle's reading: separation energies neglected, e_a = E m2/(m_p + m2) (the CM
+# energy of the entrance channel), e_b = (1 - u) e_a.  The tests below check the law's
+# limits and breakpoints (its published structure), not a retyped copy of it.
+
+
+def _kal():
+    return O.fn("oracle_kalbach_a")
+
+
+def _E_for_ea(ea, A):
+    m2 = A * AMU
+    return ea * (MP + m2) / m2
+
+
+def test_kalbach_slope_is_linear_with_coefficient_C1_for_small_emission_energy(oracle_lib):
+    f = _kal()
+    A = 15.999
+    for ea in (10.0, 80.0, 200.0):
+        E = _E_for_ea(ea, A)
+        for eb in (1e-4, 1e-3):
+            u = 1.0 - eb / ea
+            X1 = min(ea, 130.0) * eb / ea
+            assert f(E, u, A) / X1 == pytest.approx(0.04, rel=1e-5)
+
+
+def test_kalbach_slope_below_41_MeV_is_a_polynomial_in_e_b_with_the_published_coefficients(oracle_lib):
+    """Below both breakpoints X1 = X3 = e_b: a least-squares fit of a(e_b) by a quartic
+    recovers (0, C1, 0, C2, C3), whatever e_a is."""
+    f = _kal()
+    A = 12.011
+    for ea in (20.0, 40.0):
+        E = _E_for_ea(ea, A)
+        eb = np.linspace(0.0, ea, 41)
+        a = np.array([f(E, 1.0 - x / ea, A) for x in eb])
+        c = np.polynomial.polynomial.polyfit(eb, a, 4)
+        assert np.allclose(c, [0.0, 0.04, 0.0, 1.8e-6, 6.7e-7], rtol=1e-6, atol=1e-12), c
+
+
+def test_kalbach_slope_saturates_at_the_41_and_130_MeV_breakpoints(oracle_lib):
+    """At fixed u the slope grows with e_a until R3 and R1 stop following it: between the
+    breakpoints only the X1 terms grow, and above 130 MeV a no longer depends on e_a.
+    The breakpoints sit at the entrance-channel CM energies 41 and 130 MeV (lab energies
+    E = e_a (m_p + m2)/m2), which pins the CM conversion too."""
+    f = _kal()
+    A = 15.999
+    u = 0.3
+    a = lambda ea: f(_E_for_ea(ea, A), u, A)
+    # above 130 MeV: constant
+    assert a(131.0) == pytest.approx(a(180.0), rel=1e-12)
+    assert a(131.0) == pytest.approx(a(130.0 + 1e-9), rel=1e-9)
+    assert a(129.0) < a(130.0) - 1e-3
+    # between 41 and 130 MeV: the C3 X3^4 part is frozen; it equals its value at 41 MeV,
+    # which is what is left when the X1 part (fitted as C1 X1 + C2 X1^3 below 41) is removed
+    x1 = lambda ea: min(ea, 130.0) * (1.0 - u)
+    c3part = lambda ea: a(ea) - 0.04 * x1(ea) - 1.8e-6 * x1(ea) ** 3
+    assert c3part(60.0) == pytest.approx(c3part(41.0), rel=1e-9)
+    assert c3part(120.0) == pytest.approx(c3part(41.0), rel=1e-9)
+    assert c3part(30.0) < c3part(41.0) * 0.5
+    # the breakpoint is at e_a, not at the lab energy: just below E(e_a = 130) a still grows
+    E130 = _E_for_ea(130.0, A)
+    assert f(E130 * (1.0 - 1e-3), u, A) < f(E130, u, A)
+    assert f(E130 * (1.0 + 1e-3), u, A) == pytest.approx(f(E130, u, A), rel=1e-12)
+
+
+def test_kalbach_slope_at_full_emission_energy_above_130_MeV(oracle_lib):
+    """u = 0 and e_a >= 130 MeV: X1 = 130, X3 = 41, so a = 0.04*130 + 1.8e-6*130^3 +
+    6.7e-7*41^4 = 5.2 + 3.9546 + 1.89325987 = 11.04785987 (arithmetic on the published
+    constants), for every target."""
+    f = _kal()
+    for A in (12.011, 15.999, 40.078):
+        assert f(_E_for_ea(150.0, A), 0.0, A) == pytest.approx(11.04785987, rel=1e-9)
