@@ -1,16 +1,23 @@
 """Benchmark of the GB300 jump-SDE proton dose engine.
 
 One step = one pass of the whole transport path over one batch: zero the tally, prepare
-the spots (device-resident), and transport every history of the workload (persistent
-kernel: source sampling, Euler-Maruyama steps, jumps, voxel lookup, fixed-point tally).
-The default workload is the longitudinally heterogeneous slab phantom: 150 MeV beam,
-lateral sigma 3 mm, 10^6 protons, 60 x 60 x 200 mm at 0.5 mm voxels (water / bone-like /
-lung-like / water).  Its inputs (29 MB phantom + 46 MB tally) fit in L2, so L2 is flushed
-(256 MB write) before every timed step, outside the timed events.
+the spots (device-resident), and transport every history of the workload in one
+persistent launch (source sampling, Euler-Maruyama steps, jumps, voxel lookup,
+fixed-point tally).  The default workload is the batched treatment plan: 2000 spots on a
+5 mm lateral grid, energies uniform in 70-200 MeV, lognormal(0, 0.7) weights, 10^8
+protons in total (histories per spot proportional to weight), 200 x 200 x 300 mm at
+1 mm, water with 30 random spherical inserts.  The launch shape is picked by the
+library's autotuner before the warm-up steps.  Its inputs (48 MB phantom + 96 MB tally)
+exceed L2, and L2 is also flushed (256 MB write) before every timed step, outside the
+timed events.
 
-Prints one JSON line (rank 0).  Under torchrun (N > 1) the ranks split one plan of N x 10^6
-histories by global history id (each rank its own 10^6, weak scaling, no collective in
-the timed steps) and the step time is the maximum over ranks; after timing, one exact
+Secondary keys of the same line: the plan run as one launch per spot (all 2000 spots),
+the slab phantom (150 MeV, 10^6 protons, 0.5 mm voxels), the learned-vs-plain time to
+dose and the denoiser's tensor throughput.
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) the ranks split one plan of N x
+10^8 histories by global history id (each rank its own 10^8, weak scaling, no collective
+in the timed steps) and the step time is the maximum over ranks; after timing, one exact
 integer all-reduce of the tallies gives the combined dose, and its time is reported.
 
 ``--impl reference`` times the FP64 CPU oracle instead (on the host cores, rank 0 only).
@@ -18,6 +25,7 @@ integer all-reduce of the tallies gives the combined dose, and its time is repor
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -31,22 +39,45 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "proton histories/s on 1 GB300; time-to-dose at \u226595% gamma 2%/0.5mm, learned vs plain"
+
 # Algorithmic lane operations per Euler-Maruyama step of the transport kernel (one
 # Philox4x32-10 block, two Box-Muller transforms, table interpolation of five fields,
 # kinematic factors, Lynch-Dahl width, spherical Brownian rotation, exponential jump
 # clock, two voxel lookups, fixed-point conversion and one 64-bit atomic).  The
 # breakdown is listed with the roofline in the design notes.
 ALGO_OPS_PER_STEP = 200
-SMS = 152
 LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per clock each
-# DRAM traffic (read + write bytes) per transport launch from the ncu capture of the
-# same launch configuration; None until captured for the current kernel.
-TRANSPORT_DRAM_BYTES = 70_678_528  # 60.26 MB read + 10.42 MB written, ncu 1-pass capture of the bench launch (profiles/k_transport_slab150.md)
 
-CT_DESC = ("ct_sobp: thorax-like synthetic CT 120x120x240 mm at 1 mm (air, lung, adipose, soft tissue, "
-           "cortical bone from HU), 16-layer spread-out Bragg peak 90-140 mm, 256 spots, 1e6 protons per GPU")
-WORKLOAD_DESC = ("slab150: 150 MeV pencil beam (sigma_xy 3 mm), 1e6 protons per GPU, "
-                 "60x60x200 mm at 0.5 mm (120x120x400 voxels), water/bone-like/lung-like/water slabs")
+# DRAM traffic (read + write bytes) of one transport launch, from a one-pass ncu capture of
+# the benchmark's own launch, valid only for the transport source it was taken on (the
+# hash of the kernel's source files); otherwise the line reports null.
+TRANSPORT_SOURCES = ("sde_transport.cu", "sde_internal.cuh", "sde_transport.h")
+TRANSPORT_DRAM = {}  # workload -> {"src": sha256 prefix, "bytes": per launch, "note": ...}
+
+WORKLOADS = {
+    "plan2000": ("plan2000: 2000 spots on a 5 mm grid, E U(70,200) MeV, lognormal(0,0.7) weights, "
+                 "1e8 protons per GPU, 200x200x300 mm at 1 mm, water + 30 random spheres (tissue/bone, "
+                 "0.2-1.9 g/cm3); one persistent autotuned launch", 100_000_000),
+    "slab150": ("slab150: 150 MeV pencil beam (sigma_xy 3 mm), 1e6 protons per GPU, "
+                "60x60x200 mm at 0.5 mm (120x120x400 voxels), water/bone-like/lung-like/water slabs", 1_000_000),
+    "ct_sobp": ("ct_sobp: thorax-like synthetic CT 120x120x240 mm at 1 mm (air, lung, adipose, soft tissue, "
+                "cortical bone from HU), 16-layer spread-out Bragg peak 90-140 mm, 256 spots, 1e6 protons per GPU",
+                1_000_000),
+}
+
+
+def _make_workload(name, total):
+    from sde_workloads import ct_sobp, plan2000, slab150
+    return {"plan2000": plan2000, "slab150": slab150, "ct_sobp": ct_sobp}[name](total)
+
+
+def transport_source_hash():
+    h = hashlib.sha256()
+    for f in TRANSPORT_SOURCES:
+        with open(os.path.join(ROOT, "paper_2511_03115_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -126,113 +157,176 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(target_s: float = 25.0):
-    """The oracle as it stands on the host cores, on a bounded sample of the workload."""
+def _oracle_rate(wl, n, seed, handle=None):
+    """Histories/s of the oracle on ``wl`` rescaled to ``n`` histories (same phantom and
+    spots, each spot's count in proportion); returns (rate, seconds, balance)."""
     import oracle
-    from sde_workloads import slab150
+    sample = wl.with_histories(n)
+    own = handle is None
+    d = oracle.OracleDose(sample) if own else handle
+    try:
+        d.reset()
+        t0 = time.perf_counter()
+        d.run(spots=sample.spots, seed=seed)
+        dt = time.perf_counter() - t0
+        bal = _oracle_balance(d)
+    finally:
+        if own:
+            d.close()
+    return n / dt, dt, bal
+
+
+def _oracle_balance(d):
+    import ctypes as C
+    import oracle
+    b = oracle.Balance()
+    oracle._check(oracle.lib().oracle_fetch(d.h, None, None, C.byref(b)))
+    return b.as_dict()
+
+
+def cpu_baseline(workload: str, target_s: float = 20.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload: the
+    same phantom and spot list with the history count scaled down (each spot keeps its share)."""
+    import oracle
 
     oracle.build()
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
-    cal = 20_000
-    t0 = time.perf_counter()
-    oracle.run_workload(slab150(cal), seed=12345)
-    dt = time.perf_counter() - t0
-    n = int(min(5_000_000, max(cal, cal * target_s / max(dt, 1e-3))))
-    t0 = time.perf_counter()
-    _, _, bal = oracle.run_workload(slab150(n), seed=777)
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "histories/s", "cores": cores, "kind": "oracle",
-            "sample": f"slab150 workload, {n} histories (seed 777), FP64 oracle, {cores} threads, "
-                      f"{dt:.1f} s", "steps_per_s": bal["steps"] / dt}
+    wl = _make_workload(workload, WORKLOADS[workload][1])
+    d = oracle.OracleDose(wl)
+    try:
+        cal = 20_000
+        rate, dt, _ = _oracle_rate(wl, cal, 12345, d)
+        n = int(min(5_000_000, max(cal, rate * target_s)))
+        rate, dt, bal = _oracle_rate(wl, n, 777, d)
+    finally:
+        d.close()
+    return {"value": rate, "unit": "histories/s", "cores": cores, "kind": "oracle",
+            "sample": f"{workload} phantom and spots, histories scaled to {n} (seed 777), FP64 oracle, "
+                      f"{cores} threads, {dt:.1f} s", "steps_per_s": bal["steps"] / dt}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, on the same workload, each step a
+    bounded sample of it (same phantom and spots, histories scaled down)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     import oracle
-    from sde_workloads import slab150
 
     oracle.build()
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
+    desc, full = WORKLOADS[args.workload]
+    wl = _make_workload(args.workload, full)
     n = args.ref_histories
-    for w in range(args.warmup):
-        oracle.run_workload(slab150(n), seed=10_000 + w)
-    times = []
-    for k in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.run_workload(slab150(n), seed=20_000 + k)
-        times.append(time.perf_counter() - t0)
+    d = oracle.OracleDose(wl)
+    try:
+        for w in range(args.warmup):
+            _oracle_rate(wl, n, 10_000 + w, d)
+        times = [_oracle_rate(wl, n, 20_000 + k, d)[1] for k in range(args.steps)]
+    finally:
+        d.close()
     T = sum(times) / len(times)
     v = n / T
     line = {
-        "impl": "reference", "metric": "proton histories/s on 1 GB300; time-to-dose at \u226595% gamma 2%/0.5mm, learned vs plain", "value": v,
+        "impl": "reference", "metric": METRIC, "value": v,
         "unit": "histories/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": T * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC.replace("1e6 protons per GPU", f"{n} protons per step (bounded sample)"),
-                   "histories_per_step": n, "parallelism": f"{cores} host threads"},
+        "config": {"workload": desc, "histories_per_step": n,
+                   "sample": f"{n} histories per step: the workload's phantom and spots, each spot's "
+                             f"history count scaled down in proportion", "parallelism": f"{cores} host threads"},
         "cpu_baseline": {"value": v, "unit": "histories/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{n} histories of the slab150 workload per step"},
+                         "sample": f"{n} histories of the {args.workload} workload per step"},
         "e2e": {"value": v, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def plan_benchmark(torch, S, dev, total=100_000_000, per_spot_sample=200):
-    """The 2000-spot plan phantom (200x200x300 mm, 30 spheres) with 1e8 protons:
-    default launch shape, autotuned shape, graph launch, and one launch per spot
-    (timed on the first ``per_spot_sample`` spots and scaled to all 2000)."""
-    from sde_workloads import plan2000
-    wl = plan2000(total)
-    st = torch.cuda.Stream(device=dev)
-    d = S.SdeDose(wl, stream=st)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    sp = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
+def time_steps(torch, d, spots_dev, n_spots, steps, warmup, stream, flush, first=None, count=None,
+               seed_base=1_000_003, barrier=None):
+    """W untimed steps, then K timed steps on the handle's stream (CUDA events), L2 flushed
+    before each timed step outside the events.  Returns (step ms, transport ms) lists: a
+    step is reset + spot prep + transport; the second time excludes the reset."""
+    def step(k):
+        d.reset()
+        d.run_device(spots_dev.data_ptr(), n_spots, seed=seed_base + k, first=first, count=count)
 
-    def timed(fn, reps=3):
-        ts = []
-        for r in range(reps + 1):
-            with torch.cuda.stream(st):
-                flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            d.reset()
-            a.record(st)
-            fn(r)
-            b.record(st)
-            st.synchronize()
-            if r:
-                ts.append(a.elapsed_time(b))
-        return min(ts)
+    for w in range(warmup):
+        step(10_000 + w)
+    d.sync()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        m = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        d.reset()
+        m.record(stream)
+        d.run_device(spots_dev.data_ptr(), n_spots, seed=seed_base + k, first=first, count=count)
+        e.record(stream)
+        evs.append((s, m, e))
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    return [s.elapsed_time(e) for s, _, e in evs], [m.elapsed_time(e) for _, m, e in evs]
 
-    out = {"workload": "plan2000: 2000 spots, E U(70,200) MeV, lognormal weights, 1e8 protons, "
-                       "200x200x300 mm at 1 mm, water + 30 spheres"}
-    out["one_launch_default_ms"] = timed(lambda r: d.run_device(sp.data_ptr(), len(wl.spots), seed=r))
-    out["autotuned"] = d.autotune(wl.spots, seed=5, max_histories=2_000_000)
-    out["one_launch_autotuned_ms"] = timed(lambda r: d.run_device(sp.data_ptr(), len(wl.spots), seed=r))
-    d.set_tuning(graph=2)
-    out["one_launch_graph_ms"] = timed(lambda r: d.run_device(sp.data_ptr(), len(wl.spots), seed=r))
-    d.set_tuning(graph=1)
-    n = per_spot_sample
+
+def alu_roofline(steps_per_launch, kernel_ms, sms, clk_mhz):
+    peak = sms * LANE_OPS_PER_CLK_PER_SM * clk_mhz * 1e6
+    achieved = steps_per_launch * ALGO_OPS_PER_STEP / (kernel_ms * 1e-3)
+    return achieved, peak
+
+
+def per_spot_benchmark(torch, S, wl, d, spots_dev, stream, flush):
+    """The plan as one launch per spot (all spots, one after another on the handle's stream),
+    against the one persistent launch: device time of the whole sequence."""
     rec = int(wl.spots.dtype.itemsize)
+    n = len(wl.spots)
 
-    def per_spot(r):
+    def seq(seed):
         for i in range(n):
-            d.run_device(sp.data_ptr() + i * rec, 1, seed=r * 10_000 + i)
+            d.run_device(spots_dev.data_ptr() + i * rec, 1, seed=seed * 10_000 + i)
 
-    t_sample = timed(per_spot, reps=1)
-    hist_sample = int(wl.spots["n_hist"][:n].sum())
-    out["per_spot_sample"] = {"spots": n, "histories": hist_sample, "ms": t_sample}
-    out["per_spot_all_2000_ms_estimated"] = t_sample * len(wl.spots) / n
-    out["histories_per_s_one_launch"] = wl.n_histories / (min(out["one_launch_default_ms"],
-                                                             out["one_launch_autotuned_ms"]) * 1e-3)
-    out["histories_per_s_per_spot"] = hist_sample / (t_sample * 1e-3)
-    d.close()
-    return out
+    ts = []
+    for r in range(2):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        d.reset()
+        a.record(stream)
+        seq(r)
+        b.record(stream)
+        stream.synchronize()
+        ts.append(a.elapsed_time(b))
+    d.sync()
+    ms = min(ts[1:] or ts)
+    return {"spots": n, "launches": 2 * n, "ms": ms, "histories_per_s": wl.n_histories / (ms * 1e-3),
+            "note": "every spot of the plan as its own prep + transport launch (no extrapolation)"}
+
+
+def slab_secondary(torch, S, dev, stream, flush, sms, clk_mhz, steps=10, warmup=3):
+    """The slab phantom (150 MeV, 10^6 protons, 0.5 mm voxels) as a secondary line."""
+    wl = _make_workload("slab150", WORKLOADS["slab150"][1])
+    sp = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
+    with S.SdeDose(wl, stream=stream) as d:
+        step_ms, kern_ms = time_steps(torch, d, sp, len(wl.spots), steps, warmup, stream, flush)
+        _, _, bal = d.fetch(dose=False, edep=False)
+    T, Tk = float(np.mean(step_ms)), float(np.mean(kern_ms))
+    ach, peak = alu_roofline(bal["steps"], Tk, sms, clk_mhz)
+    return {"workload": WORKLOADS["slab150"][0], "value": wl.n_histories / (T * 1e-3), "unit": "histories/s",
+            "ms_per_step": T, "kernel_ms": Tk, "euler_steps_per_launch": bal["steps"],
+            "alu_frac": ach / peak, "balance_exact": bal["incident"] == bal["deposited"] + bal["escaped"] + bal["removed"]}
 
 
 # Executed multiply-adds of one denoiser inference on 128 x 128 x 192 (16-channel padded
@@ -323,79 +417,59 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--histories", type=int, default=1_000_000)
+    ap.add_argument("--workload", default="plan2000", choices=sorted(WORKLOADS),
+                    help="plan2000 (default): the batched 2000-spot plan with 1e8 protons; slab150; ct_sobp")
+    ap.add_argument("--histories", type=int, default=0, help="protons per GPU (0: the workload's own count)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-histories", type=int, default=20_000)
-    ap.add_argument("--workload", default="slab150", choices=["slab150", "ct_sobp"],
-                    help="slab150 (default) or ct_sobp: thorax-like synthetic CT with a 16-layer spread-out Bragg peak")
+    ap.add_argument("--ref-histories", type=int, default=100_000,
+                    help="histories per step of the reference arm (a bounded sample of the workload)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     ap.add_argument("--theta-cut-sigmas", type=float, default=0.0,
                     help="energy-dependent elastic cut-off theta_c = k sigma(E) (0: the paper's fixed 0.02 rad)")
     ap.add_argument("--physics-mask", type=int, default=15,
                     help="ablation: SDE_PHYS_* bits of the transport (15 = all terms; 11 = no large-angle "
                          "elastic events, 3 = no jumps); a run with terms switched off is not the benchmark")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the per-spot launches of the plan and the slab-phantom line")
     ap.add_argument("--no-denoiser", action="store_true",
                     help="skip the learned-vs-plain time-to-dose and the denoiser throughput")
-    ap.add_argument("--plan", action="store_true",
-                    help="also time the 2000-spot plan (1e8 protons): one persistent launch, "
-                         "autotuned, graph-launched, and one launch per spot")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
 
     import torch
     import paper_2511_03115_gb300 as S
-    from sde_workloads import ct_sobp, slab150
 
     ws, rank, local = _dist()
+    barrier = None
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+        barrier = dist.barrier
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    desc, per_gpu = WORKLOADS[args.workload]
+    per_gpu = args.histories or per_gpu
     # one plan; this rank runs its shard of the history ids
-    wl = (ct_sobp if args.workload == "ct_sobp" else slab150)(args.histories * ws)
+    wl = _make_workload(args.workload, per_gpu * ws)
     first, count = S.history_shard(wl.n_histories, rank, ws)
     stream = torch.cuda.Stream(device=dev)
     d = S.SdeDose(wl, stream=stream, theta_cut_sigmas=args.theta_cut_sigmas, physics_mask=args.physics_mask)
     spots_dev = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    seed_base = 1_000_003
+    tuned = None
+    if not args.no_autotune:
+        # launch shape picked on a 2e6-history subsample of this rank's plan (outside timing)
+        tuned = d.autotune(wl.spots, seed=5, max_histories=2_000_000)
 
-    def step(k):
-        d.reset()
-        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + k, first=first, count=count)
-
-    for w in range(args.warmup):
-        step(10_000 + w)
-    d.sync()
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    evs = []
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        s = torch.cuda.Event(enable_timing=True)
-        m = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        d.reset()
-        m.record(stream)
-        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + k, first=first, count=count)
-        e.record(stream)
-        evs.append((s, m, e))
-    stream.synchronize()
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
+    step_ms, kern_ms = time_steps(torch, d, spots_dev, len(wl.spots), args.steps, args.warmup, stream, flush,
+                                  first=first, count=count, barrier=barrier)
     clocks = sampler.stop()
-    step_ms = [s.elapsed_time(e) for s, _, e in evs]
-    kern_ms = [m.elapsed_time(e) for _, m, e in evs]
     T = sum(step_ms) / len(step_ms)
     Tk = sum(kern_ms) / len(kern_ms)
     _, _, bal = d.fetch(dose=False, edep=False)
@@ -414,7 +488,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d.reset()
-        d.run(wl.spots, seed=seed_base + 50_000 + k, first=first, count=count)
+        d.run(wl.spots, seed=1_000_003 + 50_000 + k, first=first, count=count)
         d.fetch_into(dose_ptr=host_dose.data_ptr())
         t1 = time.perf_counter()
         if k > 0:
@@ -428,7 +502,7 @@ def main():
     combine = None
     if ws > 1:  # the one exchange step of the split: an exact integer sum of the tallies
         d.reset()
-        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=seed_base + 90_000, first=first, count=count)
+        d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=1_000_003 + 90_000, first=first, count=count)
         tally = torch.empty(wl.n_voxels, dtype=torch.int64, device=dev)
         rb = d.fetch_device(edep_ptr=tally.data_ptr(), balance=True)
         bt = torch.tensor([rb[k] for k in ("incident", "deposited", "escaped", "removed", "histories")],
@@ -447,10 +521,13 @@ def main():
 
     peaks = _peaks()
     clk_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak_ops = SMS * LANE_OPS_PER_CLK_PER_SM * clk_mhz * 1e6
-    achieved = steps_per_launch * ALGO_OPS_PER_STEP / (Tk * 1e-3)
+    achieved, peak_ops = alu_roofline(steps_per_launch, Tk, sms, clk_mhz)
+    src = transport_source_hash()
+    traffic_rec = TRANSPORT_DRAM.get(args.workload)
+    traffic = traffic_rec["bytes"] if traffic_rec and traffic_rec["src"] == src and count == traffic_rec.get(
+        "histories", count) else None
     line = {
-        "metric": "proton histories/s on 1 GB300; time-to-dose at \u226595% gamma 2%/0.5mm, learned vs plain",
+        "metric": METRIC,
         "value": value,
         "unit": "histories/s",
         "n_gpus": ws,
@@ -462,38 +539,46 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC if args.workload == "slab150" else CT_DESC,
-                   "histories_per_step": hist_per_step,
+        "config": {"workload": desc, "histories_per_step": hist_per_step,
                    "split": f"history ids {first}..{first + count - 1} of {wl.n_histories} on rank {rank}",
                    "euler_steps_per_launch": steps_per_launch, "parallelism": f"replicas x{ws}",
-                   "l2": "flushed (256 MB write) before every timed step", "tally": "int64 fixed point 2^-24 MeV",
+                   "l2": "inputs (phantom + tally) and a 256 MB flush write before every timed step",
+                   "tally": "int64 fixed point 2^-24 MeV",
                    "elastic_cut_off": (f"theta_c = {args.theta_cut_sigmas} sigma(E)" if args.theta_cut_sigmas > 0
                                        else "fixed 0.02 rad"),
                    "physics_mask": args.physics_mask,
-                   "tuning": d.get_tuning()},
+                   "autotuned": tuned is not None, "tuning": d.get_tuning()},
         "e2e": {"value": hist_per_step / e2e_T, "unit": "histories/s",
                 "h2d_bytes_per_step": int(wl.spots.nbytes),
                 "d2h_bytes_per_step": int(wl.n_voxels * 8 + 64)},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
-                     "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": TRANSPORT_DRAM_BYTES,
+                     "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": traffic,
+                     "traffic_note": (traffic_rec or {}).get("note") if traffic is not None else
+                     "null: no ncu capture of this transport source (hash %s) for this workload" % src,
                      "kernel": "k_transport (+ single-block spot prep)", "kernel_ms": Tk,
-                     "ops_per_step": ALGO_OPS_PER_STEP,
-                     "peak_note": f"{SMS} SMs x {LANE_OPS_PER_CLK_PER_SM} lane-ops/clk x {clk_mhz:.0f} MHz (max SM clock)"},
+                     "ops_per_step": ALGO_OPS_PER_STEP, "transport_src": src,
+                     "peak_note": f"{sms} SMs (device attribute) x {LANE_OPS_PER_CLK_PER_SM} lane-ops/clk x "
+                                  f"{clk_mhz:.0f} MHz (measured max SM clock)"},
         "clocks": clocks,
         "balance_exact": bal["incident"] == bal["deposited"] + bal["escaped"] + bal["removed"],
         "combine": combine,
     }
-    if args.plan:
-        line["batched_plan"] = plan_benchmark(torch, S, dev)
+    if rank == 0 and ws == 1 and not args.no_secondary:
+        if args.workload == "plan2000":
+            line["per_spot_launches"] = per_spot_benchmark(torch, S, wl, d, spots_dev, stream, flush)
+            line["per_spot_launches"]["one_launch_ms"] = T
+        if args.workload != "slab150":
+            line["slab150"] = slab_secondary(torch, S, dev, stream, flush, sms, clk_mhz)
+    d.close()
+    del flush
     if rank == 0 and ws == 1 and not args.no_denoiser:
         line["time_to_dose"] = time_to_dose(torch, S)
         line["denoiser"] = denoiser_roofline(torch, S, peaks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(args.workload)
     if rank == 0:
         print(json.dumps(line))
-    d.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
