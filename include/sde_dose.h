@@ -348,22 +348,26 @@ int sde_gamma3d(const float* d_ref, const float* d_eval, int nx, int ny, int nz,
 /* Transport without any memory allocation.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory -- code
  * running inside a framework that owns every device allocation through its own
- * pool, code called while someone else is building a CUDA graph, or services
- * that forbid allocation after start-up because cudaMalloc can block or fail
- * at an arbitrary moment.
+ * pool, and services that forbid allocation after start-up because cudaMalloc
+ * can block or fail at an arbitrary moment.
  *
  * It runs the same kernels as sde_dose_run_device on caller-owned device
  * inputs and output: d_vox[nx*ny*nz] packed voxel words (the FP32 density with
  * its low 4 mantissa bits replaced by the material id: word =
  * ((bits(density) + 8) & ~15) | material_id, material_id < n_mats), d_spots
  * (n_spots sde_spot records) and d_edep (nx*ny*nz 64-bit tally, ADDED to).
- * mats, params (not NULL) and bal (may be NULL) are host memory.  Every other
- * buffer (physics tables, device spot records, history prefix, work-queue
- * cursor, balance counters) lives in one static 1 MiB device array inside the
- * library, which each GPU that loads the library holds until the process
- * exits.  Limits set by that array: n_mats <= 4, params->table_points <= 256,
- * n_spots <= 4096; larger inputs fail with SDE_EINVAL.  No cudaMalloc,
- * cudaFree or allocating library routine is called.
+ * mats, params (not NULL) and bal (may be NULL) are host memory; d_status (may
+ * be NULL) is one caller-owned device word.  Every other buffer (physics
+ * tables, device spot records, history prefix, work-queue cursor, balance
+ * counters) lives in one static 1 MiB device array inside the library, which
+ * each GPU that loads the library holds until the process exits.  Limits set by
+ * that array: n_mats <= 4, params->table_points <= 256, n_spots <= 4096; larger
+ * inputs fail with SDE_EINVAL.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
+ *
+ * The voxel words are checked on the device before the transport uses them:
+ * a material id >= n_mats or a density that is not finite in [0, 1e3) g/cm^3
+ * raises device error bit 8 and no history runs (d_edep is left as it was).
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
@@ -371,15 +375,19 @@ int sde_gamma3d(const float* d_ref, const float* d_eval, int nx, int ny, int nz,
  * call clears what must start at zero.  All calls share the one array, so
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race and corrupt each other: serialise them.  Work is enqueued on
- * cuda_stream (a cudaStream_t, NULL = legacy default stream); with bal != NULL
- * the call waits for it and fills the balance of this call (its deposited
- * field is the sum of d_edep after the call; SDE_EDEVICE if the step cap was
- * hit or a spot was invalid), otherwise it returns without waiting. */
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream).  Device-side
+ * errors of the call (bits: 1 step cap reached, 2 invalid spot, 8 bad voxel
+ * word; 0 = none) are written to *d_status when it is not NULL.  With bal !=
+ * NULL the call waits for its work and fills the balance of this call alone
+ * (deposited = the increase of the tally's sum, so a tally that already held
+ * earlier deposits still balances: incident = deposited + escaped + removed),
+ * and returns SDE_EDEVICE when a device error bit was raised; with bal == NULL
+ * it returns without waiting and only d_status reports device-side errors. */
 int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_mm[3], const double origin_mm[3],
                           const uint32_t* d_vox, const sde_material* mats, int n_mats,
                           const sde_params* params, const sde_spot* d_spots, int n_spots,
                           uint64_t seed, unsigned long long* d_edep, sde_balance* bal,
-                          void* cuda_stream);
+                          unsigned int* d_status, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -1,20 +1,24 @@
 // sde_noalloc.cu -- a transport entry point that allocates no memory.
 //
 // Some callers cannot call cudaMalloc: code running inside a host framework that
-// owns every device allocation (a memory pool or arena it must account for), code
-// invoked while a CUDA graph is being built by someone else, or real-time
-// services that forbid allocation after start-up because an allocation can block
-// and fail at an arbitrary point.  sde_transport_noalloc serves them: the caller
-// passes the phantom, the spots and the tally buffer in device memory it already
-// owns, and every other buffer the transport needs (physics tables, spot records
-// in device form, the history prefix, the work-queue cursor and the balance
-// counters) lives in one fixed array compiled into this library.
+// owns every device allocation (a memory pool or arena it must account for), and
+// real-time services that forbid allocation after start-up because an allocation
+// can block and fail at an arbitrary point.  sde_transport_noalloc serves them:
+// the caller passes the phantom, the spots and the tally buffer in device memory
+// it already owns, and every other buffer the transport needs (physics tables,
+// spot records in device form, the history prefix, the work-queue cursor and the
+// balance counters) lives in one fixed array compiled into this library.
 //
 // The array is a file-scope __device__ object of kScratchBytes (1 MiB).  Every
 // GPU on which the library is loaded holds its own copy until the process exits.
 // Host code cannot use the array's name as a device address, so the first call
 // on each device looks the address up with cudaGetSymbolAddress (with that
 // device current) and caches it.
+//
+// The caller's voxel words are checked on the device before the transport reads
+// any table with them (material id < n_mats, density finite in [0, 1e3)): a bad
+// word raises a device error bit and leaves the work queue empty, so no history
+// runs and no table is indexed out of range.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -36,6 +40,28 @@ constexpr int kNoallocMaxSpots = 4096;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Device error bit of this entry point beside the transport's own (step cap 1, bad spot 2).
+constexpr unsigned int kErrBadVoxel = 8u;
+
+// Checks every caller-supplied voxel word before any kernel indexes a table with it:
+// material id < n_mats and density finite in [0, 1e3) g/cm^3 (the checks sde_dose_create
+// makes on the host).  A bad word raises kErrBadVoxel and moves the work-queue cursor
+// (set by the spot preparation just before) past every history id, so the transport
+// that follows claims no history.
+__global__ void k_check_voxels(const uint32_t* __restrict__ vox, size_t nv, int n_mats, unsigned int* err,
+                               unsigned long long* cursor) {
+    bool bad = false;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t w = vox[v];
+        const float rho = __uint_as_float(w & ~15u);
+        bad |= (int)(w & 15u) >= n_mats || !(rho >= 0.f && rho < 1e3f);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+        atomicOr(err, kErrBadVoxel);
+        atomicExch(cursor, 1ull << 62);  // above any plan's history count: the queue is drained
+    }
+}
 
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
@@ -66,7 +92,7 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
                                      const uint32_t* d_vox, const sde_material* mats, int n_mats,
                                      const sde_params* params, const sde_spot* d_spots, int n_spots,
                                      uint64_t seed, unsigned long long* d_edep, sde_balance* bal,
-                                     void* cuda_stream) {
+                                     unsigned int* d_status, void* cuda_stream) {
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (nx <= 0 || ny <= 0 || nz <= 0 || !voxel_mm || !origin_mm || !d_vox || !mats || !params || !d_spots ||
         !d_edep)
@@ -127,6 +153,7 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     };
     auto* counters = (unsigned long long*)carve(kCntWords * sizeof(unsigned long long));
     auto* err = (unsigned int*)carve(sizeof(unsigned int));
+    auto* dep = (unsigned long long*)carve(2 * sizeof(unsigned long long));  // tally sum before / after
     auto* d_mh = (MatHost*)carve(n_mats * sizeof(MatHost));
     auto* d_mj = (MatJump*)carve(n_mats * sizeof(MatJump));
     const size_t table_bytes = (size_t)n_mats * N * kRowFloat4 * sizeof(float4);
@@ -174,6 +201,13 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     tb.d_table = table;
     NA_TRY(build_tables(tb, st));
     NA_TRY(launch_prep(d_spots, n_spots, spots, prefix, counters, err, origin_mm, p.e_min_MeV, p.e_max_MeV, st));
+    const size_t nv = (size_t)nx * ny * nz;
+    k_check_voxels<<<sms * 4, 256, 0, st>>>(d_vox, nv, n_mats, err, counters + kCntCursor);
+    NA_TRY(cudaGetLastError());
+    if (bal) {  // the tally may already hold earlier calls' deposits: the balance takes the difference
+        NA_TRY(cudaMemsetAsync(dep, 0, 2 * sizeof(unsigned long long), st));
+        NA_TRY(launch_sum_u64(d_edep, nv, dep, sms, st));
+    }
 
     KParams P;
     memset(&P, 0, sizeof P);
@@ -230,16 +264,17 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     if (per_sm < 1) return noalloc_fail(SDE_ECUDA, "sde_transport_noalloc: transport kernel cannot be resident");
     NA_TRY(launch_transport(P, sms * per_sm, block, table_bytes, false, st));
 
+    if (d_status) NA_TRY(cudaMemcpyAsync(d_status, err, sizeof(unsigned int), cudaMemcpyDeviceToDevice, st));
     if (bal) {
-        NA_TRY(cudaMemsetAsync(counters + kCntDeposited, 0, sizeof(unsigned long long), st));
-        NA_TRY(launch_sum_u64(d_edep, (size_t)nx * ny * nz, counters + kCntDeposited, sms, st));
-        unsigned long long c[kCntWords];
+        NA_TRY(launch_sum_u64(d_edep, nv, dep + 1, sms, st));
+        unsigned long long c[kCntWords], sums[2];
         unsigned int flag = 0;
         NA_TRY(cudaMemcpyAsync(c, counters, sizeof c, cudaMemcpyDeviceToHost, st));
+        NA_TRY(cudaMemcpyAsync(sums, dep, sizeof sums, cudaMemcpyDeviceToHost, st));
         NA_TRY(cudaMemcpyAsync(&flag, err, sizeof flag, cudaMemcpyDeviceToHost, st));
         NA_TRY(cudaStreamSynchronize(st));
         bal->incident = c[kCntIncident];
-        bal->deposited = c[kCntDeposited];
+        bal->deposited = sums[1] - sums[0];  // this call's deposit (unsigned difference, exact)
         bal->escaped = c[kCntEscaped];
         bal->removed = c[kCntRemoved];
         bal->histories = c[kCntHistories];
@@ -247,8 +282,12 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
         bal->jumps_elastic = c[kCntJumpEl];
         bal->jumps_inelastic = c[kCntJumpInel];
         if (flag)
-            return noalloc_fail(SDE_EDEVICE, (flag & kErrStepCap) ? "sde_transport_noalloc: step cap reached"
-                                                                   : "sde_transport_noalloc: invalid spot");
+            return noalloc_fail(SDE_EDEVICE,
+                                (flag & kErrBadVoxel)
+                                    ? "sde_transport_noalloc: a voxel word has a material id >= n_mats or a density "
+                                      "outside [0, 1e3) g/cm3; no history was run"
+                                    : (flag & kErrStepCap) ? "sde_transport_noalloc: step cap reached"
+                                                           : "sde_transport_noalloc: invalid spot");
     }
 #undef NA_TRY
     return SDE_OK;
