@@ -53,7 +53,12 @@ LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per cl
 # the benchmark's own launch, valid only for the transport source it was taken on (the
 # hash of the kernel's source files); otherwise the line reports null.
 TRANSPORT_SOURCES = ("sde_transport.cu", "sde_internal.cuh", "sde_transport.h")
-TRANSPORT_DRAM = {}  # workload -> {"src": sha256 prefix, "bytes": per launch, "note": ...}
+TRANSPORT_DRAM = {  # workload -> {"src": sha256 prefix, "bytes": per launch, "note": ...}
+    "plan2000": {"src": "87b60e0a75a78414", "bytes": 2_593_619_968 + 3_182_972_160, "histories": 100_000_000,
+                 "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first timed launch of "
+                         "`bench.py --steps 2 --warmup 1 --no-denoiser --no-cpu-baseline --no-secondary` "
+                         "(1 pass; profiles/k_transport_plan2000.md)"},
+}
 
 WORKLOADS = {
     "plan2000": ("plan2000: 2000 spots on a 5 mm grid, E U(70,200) MeV, lognormal(0,0.7) weights, "
@@ -505,16 +510,13 @@ def main():
         d.run_device(spots_dev.data_ptr(), len(wl.spots), seed=1_000_003 + 90_000, first=first, count=count)
         tally = torch.empty(wl.n_voxels, dtype=torch.int64, device=dev)
         rb = d.fetch_device(edep_ptr=tally.data_ptr(), balance=True)
-        bt = torch.tensor([rb[k] for k in ("incident", "deposited", "escaped", "removed", "histories")],
-                          dtype=torch.int64, device=dev)
         torch.cuda.synchronize()
         dist.barrier()
         c0 = time.perf_counter()
-        dist.all_reduce(tally, op=dist.ReduceOp.SUM)
+        tot = S.combine_shards(tally, rb)
         torch.cuda.synchronize()
         c1 = time.perf_counter()
-        dist.all_reduce(bt, op=dist.ReduceOp.SUM)
-        inc, dep, esc, rem, nh = [int(v) for v in bt.tolist()]
+        inc, dep, esc, rem, nh = (tot[k] for k in ("incident", "deposited", "escaped", "removed", "histories"))
         combine = {"allreduce_ms": (c1 - c0) * 1e3, "bytes": wl.n_voxels * 8, "histories": nh,
                    "balance_exact": inc == dep + esc + rem and nh == wl.n_histories,
                    "tally_sum_equals_deposited": int(tally.sum()) == dep}

@@ -48,6 +48,29 @@ def history_shard(total: int, rank: int, world: int):
     return first, total * (rank + 1) // world - first
 
 
+BALANCE_KEYS = ("incident", "deposited", "escaped", "removed", "histories", "steps", "jumps_elastic",
+                "jumps_inelastic")
+
+
+def combine_shards(tally, balance, group=None):
+    """The one exchange step of a plan split across GPUs by global history id: an exact
+    integer sum over the ranks of the 64-bit tallies and of the balance counters.
+
+    ``tally`` is this rank's tally as a torch int64 tensor (the library's unsigned words
+    viewed as signed: two's-complement addition gives the same bits as unsigned addition
+    modulo 2^64), on the rank's GPU for NCCL or on the CPU for gloo; it is summed in place.
+    ``balance`` is this rank's balance dict.  Integer addition is exact and does not
+    depend on the order of the ranks, so the result is the single-GPU run's bit for bit.
+    Returns the summed balance (counters must stay below 2^63, i.e. < 5.5e11 MeV of
+    incident energy at the default 2^-24 MeV unit)."""
+    import torch
+    import torch.distributed as dist
+    b = torch.tensor([int(balance[k]) for k in BALANCE_KEYS], dtype=torch.int64, device=tally.device)
+    dist.all_reduce(tally, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM, group=group)
+    return {k: int(v) for k, v in zip(BALANCE_KEYS, b.tolist())}
+
+
 class SdeError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"sde error {code}: {msg}")
@@ -127,7 +150,7 @@ def lib():
         L.sde_dose_tables.argtypes = [vp, i, vp, vp, vp]
         L.sde_dose_probe_steps.argtypes = [vp, i, d, d, u64, u64, i, vp, vp, vp, vp, vp]
         L.sde_transport_noalloc.argtypes = [i, i, i, C.POINTER(d), C.POINTER(d), vp, C.POINTER(Material), i,
-                                            C.POINTER(Params), vp, i, u64, vp, C.POINTER(Balance), vp]
+                                            C.POINTER(Params), vp, i, u64, vp, C.POINTER(Balance), vp, vp]
         L.sde_gemm_bf16.argtypes = [vp, vp, vp, i, i, i, vp]
         L.sde_conv3d_forward.argtypes = [vp, i, i, i, i, i, vp, vp, i, vp, i, i, i, i, vp]
         L.sde_conv3d_wgrad.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp]

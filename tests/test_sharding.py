@@ -3,8 +3,8 @@
 Every history's random stream is keyed by its global id, and tallies are integers, so
 disjoint history ranges run with one seed must add up to the whole run exactly.  The
 ranges are produced by ``history_shard``; two ``gloo`` ranks run the oracle on their
-shards and sum their tallies with ``all_reduce``, as GPUs would with an integer
-reduce of their dose grids.
+shards and sum their tallies with ``combine_shards`` (the integer all-reduce the
+benchmark's multi-GPU path uses on NCCL), as GPUs would with their dose grids.
 """
 import os
 import socket
@@ -86,12 +86,12 @@ def _rank_main(rank, world, port, n_hist, seed, out_path):
         d.run(seed=seed, first=first, count=count)
         _, edep, bal = d.fetch()
         d.close()
-        t = torch.from_numpy(edep.astype(np.int64).ravel().copy())
-        b = torch.tensor([int(bal[k]) for k in BAL_KEYS], dtype=torch.int64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dist.all_reduce(b, op=dist.ReduceOp.SUM)
+        # the combine of the benchmark's multi-GPU path, on CPU tensors over gloo
+        from paper_2511_03115_gb300 import combine_shards
+        t = torch.from_numpy(edep.view(np.int64).ravel().copy())
+        tot = combine_shards(t, bal)
         if rank == 0:
-            np.savez(out_path, edep=t.numpy(), bal=b.numpy())
+            np.savez(out_path, edep=t.numpy(), bal=np.array([tot[k] for k in BAL_KEYS], np.int64))
     finally:
         dist.destroy_process_group()
 
