@@ -59,7 +59,8 @@ class Params(C.Structure):
                 ("e_min_MeV", C.c_double), ("K", C.c_double), ("inel_u_lo", C.c_double),
                 ("inel_u_hi", C.c_double), ("km_r", C.c_double), ("tally_mode", C.c_int),
                 ("fixed_point_shift", C.c_int), ("jump_clock", C.c_int), ("max_steps", C.c_int),
-                ("physics_mask", C.c_int), ("theta_cut_sigmas", C.c_double)]
+                ("physics_mask", C.c_int), ("theta_cut_sigmas", C.c_double),
+                ("secondary_fraction", C.c_double)]
 
 
 class Balance(C.Structure):
@@ -105,6 +106,8 @@ def lib():
                                          C.POINTER(PhysicsOut)]
             L.oracle_csda_range.argtypes = [C.POINTER(Material), d, C.POINTER(Params), d,
                                             C.POINTER(d)]
+            L.oracle_single_step_secondary.argtypes = [C.POINTER(Material), d, C.POINTER(Params), d, u64, u64,
+                                                       i, dp]
             L.oracle_sample_source.argtypes = [C.POINTER(Spot), C.POINTER(Params), u64, u64, i, dp, dp, dp]
             L.oracle_single_step.argtypes = [C.POINTER(Material), d, C.POINTER(Params), d, u64, u64,
                                              i, dp, dp, dp, dp, dp]
@@ -275,6 +278,17 @@ def single_step(material, rho, E, n, seed=0, h0=0, **param_kw):
                                     C.c_uint64(h0), int(n), E_out.ctypes.data, cos_out.ctypes.data,
                                     jump.ctypes.data, ux.ctypes.data, uy.ctypes.data))
     return {"E": E_out, "cos": cos_out, "jump": jump, "ux": ux, "uy": uy}
+
+
+def single_step_secondary(material, rho, E, n, seed=0, h0=0, **param_kw):
+    """One step per history with the branching model's emission (see the C header)."""
+    blk = _MaterialBlock([material])
+    p = params(**param_kw)
+    out = np.empty((n, 10))
+    _check(lib().oracle_single_step_secondary(blk.arr, float(rho), C.byref(p), float(E), C.c_uint64(seed),
+                                              C.c_uint64(h0), int(n), out.ctypes.data))
+    keys = ("jump", "E1", "E2", "spawn", "sec_E", "sec_ux", "sec_uy", "sec_uz", "ux", "uy")
+    return {k: out[:, i] for i, k in enumerate(keys)}
 
 
 def sample_source(spot, n, seed=0, h0=0, **param_kw):

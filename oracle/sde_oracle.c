@@ -169,7 +169,10 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 }
 
 /* Stream layout: counter = (step index n, stream tag, history lo, history hi),
- * key = (seed lo, seed hi).  Each 32-bit word becomes a uniform in (0,1). */
+ * key = (seed lo, seed hi).  Each 32-bit word becomes a uniform in (0,1).  A track of
+ * the branching model (secondary_fraction > 0) other than the primary has segment
+ * index j >= 1 (the j-th non-elastic event of its primary), carried in the tag word's
+ * upper 24 bits: tag | j << 8; the primary is segment 0, so its stream is unchanged. */
 enum { TAG_STEP = 0, TAG_JUMP_A = 1, TAG_JUMP_B = 2, TAG_SRC_A = 3, TAG_SRC_B = 4, TAG_BERN = 5 };
 
 static void draw4(uint64_t seed, uint64_t h, uint32_t n, uint32_t tag, double U[4]) {
@@ -495,6 +498,7 @@ void oracle_default_params(oracle_params* p) {
     p->max_steps = 100000;
     p->physics_mask = ORACLE_PHYS_ALL;
     p->theta_cut_sigmas = 0.0;
+    p->secondary_fraction = 0.0;
 }
 
 static int check_params(const oracle_params* p) {
@@ -505,7 +509,8 @@ static int check_params(const oracle_params* p) {
         !(p->km_r >= 0.0 && p->km_r < 1.0) || (p->tally_mode != 0 && p->tally_mode != 1) ||
         p->fixed_point_shift < 0 || p->fixed_point_shift > 30 || p->max_steps <= 0 ||
         (p->jump_clock != 0 && p->jump_clock != 1) || p->physics_mask < 0 || p->physics_mask > 15 ||
-        !(p->theta_cut_sigmas >= 0.0 && p->theta_cut_sigmas <= 100.0))
+        !(p->theta_cut_sigmas >= 0.0 && p->theta_cut_sigmas <= 100.0) ||
+        !(p->secondary_fraction >= 0.0 && p->secondary_fraction <= 1.0))
         return fail(ORACLE_EINVAL, "invalid parameters");
     return ORACLE_OK;
 }
@@ -693,14 +698,19 @@ typedef struct {
     double E0, E1, E2;
     double r0[3];
     int jump;
+    /* branching model: a secondary proton emitted by this step's non-elastic event */
+    int spawn;
+    double sec_E, sec_u[3], sec_tau;
 } or_step_ev;
 
 static void sde_step(const or_mat* m, double rho, const oracle_params* p, uint64_t seed, uint64_t h,
-                     uint32_t n, double* E, double r[3], double u[3], double* tau, or_step_ev* ev) {
+                     uint32_t seg, uint32_t n, double* E, double r[3], double u[3], double* tau,
+                     or_step_ev* ev) {
     oracle_physics_out ph;
     physics_eval(m, rho, p, *E, &ph);
+    const uint32_t sg = seg << 8; /* segment bits of the stream tags */
     double U[4];
-    draw4(seed, h, n, TAG_STEP, U);
+    draw4(seed, h, n, TAG_STEP | sg, U);
     double D = p->step_cm;
     ev->E0 = *E;
     for (int i = 0; i < 3; ++i) ev->r0[i] = r[i];
@@ -739,7 +749,7 @@ static void sde_step(const or_mat* m, double rho, const oracle_params* p, uint64
     if (sig > 0.0) {
         if (p->jump_clock == 0) {
             double B[4];
-            draw4(seed, h, n, TAG_BERN, B);
+            draw4(seed, h, n, TAG_BERN | sg, B);
             jump = B[0] < -expm1(-D * sig);
         } else {
             *tau -= D * sig;
@@ -747,9 +757,10 @@ static void sde_step(const or_mat* m, double rho, const oracle_params* p, uint64
         }
     }
     ev->jump = 0;
+    ev->spawn = 0;
     if (jump) {
         double J[4];
-        draw4(seed, h, n, TAG_JUMP_A, J);
+        draw4(seed, h, n, TAG_JUMP_A | sg, J);
         /* channel and element by rate (Eq. Npi and Bragg additivity of the
          * point processes): elastic of element 0..n-1, then non-elastic. */
         double target = J[0] * sig, acc = 0.0;
@@ -780,8 +791,25 @@ static void sde_step(const or_mat* m, double rho, const oracle_params* p, uint64
             ev->jump = 1;
         } else {
             double J2[4];
-            draw4(seed, h, n, TAG_JUMP_B, J2);
+            draw4(seed, h, n, TAG_JUMP_B | sg, J2);
             double uu = p->inel_u_lo + (p->inel_u_hi - p->inel_u_lo) * J[1];
+            if (seg == 0 && p->secondary_fraction > 0.0) {
+                /* Branching model (reading): the secondary proton carries the fraction
+                 * kappa of the deficit u E1; it leaves R_{n+1} at a Kalbach-Mann angle of
+                 * its own (slope a at emission fraction kappa u, i.e. e_b/e_a = kappa u)
+                 * about the incoming (diffused, pre-event) direction, converted to the lab
+                 * with outgoing energy kappa u E_n as for the continuing proton, uniform
+                 * azimuth, and a fresh clock; the draws are J2[1..3]. */
+                double ks = p->secondary_fraction * uu;
+                double a2 = oracle_kalbach_a(*E, 1.0 - ks, m->A[el]);
+                double mu2 = oracle_sample_mu_kalbach(J2[1], a2, p->km_r);
+                double th2 = oracle_cm_to_lab(*E, *E * ks, m2, mu2);
+                for (int i = 0; i < 3; ++i) ev->sec_u[i] = u[i];
+                rotate_dir(ev->sec_u, cos(th2), sin(th2), 2.0 * OR_PI * J2[2]);
+                ev->sec_E = ks * E1;
+                ev->sec_tau = -log(J2[3]);
+                ev->spawn = 1;
+            }
             double a = oracle_kalbach_a(*E, uu, m->A[el]);
             double mu = oracle_sample_mu_kalbach(J2[0], a, p->km_r);
             double thL = oracle_cm_to_lab(*E, *E * (1.0 - uu), m2, mu);
@@ -806,12 +834,17 @@ typedef struct {
     or_acc acc;
 } or_job;
 
-static void transport_history(const oracle_dose* d, const oracle_spot* s, uint64_t seed, uint64_t h,
-                              or_acc* acc) {
+/* Transport one track (segment seg of history h) from state (E, r, u, tau) until it is
+ * absorbed or leaves the domain.  A primary (seg 0) of the branching model records the
+ * secondaries its non-elastic events emit in sec[] (up to max_sec; more raise an error). */
+typedef struct {
     double E, r[3], u[3], tau;
-    sample_source(d, s, seed, h, &E, r, u, &tau);
-    acc->bal.incident += Q(d, E);
-    acc->bal.histories += 1;
+} or_sec;
+
+#define OR_MAX_SEC 256
+
+static void transport_track(const oracle_dose* d, uint64_t seed, uint64_t h, uint32_t seg, double E, double r[3],
+                            double u[3], double tau, or_acc* acc, or_sec* sec, int* n_sec) {
     for (uint32_t n = 0;; ++n) {
         if ((int)n >= d->p.max_steps) {
             acc->error = ORACLE_ESTEPCAP;
@@ -826,7 +859,7 @@ static void transport_history(const oracle_dose* d, const oracle_spot* s, uint64
         const or_mat* m = &d->mats[d->mid[v]];
         double rho = d->rho[v];
         or_step_ev ev;
-        sde_step(m, rho, &d->p, seed, h, n, &E, r, u, &tau, &ev);
+        sde_step(m, rho, &d->p, seed, h, seg, n, &E, r, u, &tau, &ev);
         acc->bal.steps += 1;
         uint64_t dq = Q(d, ev.E0) - Q(d, ev.E1);
         if (d->p.tally_mode == 0) {
@@ -840,7 +873,25 @@ static void transport_history(const oracle_dose* d, const oracle_spot* s, uint64
         if (ev.jump == 1) acc->bal.jumps_elastic += 1;
         if (ev.jump == 2) {
             acc->bal.jumps_inelastic += 1;
-            acc->bal.removed += Q(d, ev.E1) - Q(d, ev.E2);
+            /* the deficit leaves the transport, except what a secondary carries on; the
+             * three integer terms may differ from their real counterparts by rounding,
+             * and the sum over a run is exact in 64-bit modular arithmetic */
+            uint64_t q_sec = ev.spawn ? Q(d, ev.sec_E) : 0;
+            acc->bal.removed += Q(d, ev.E1) - Q(d, ev.E2) - q_sec;
+            if (ev.spawn) {
+                if (*n_sec >= OR_MAX_SEC) {
+                    acc->error = ORACLE_EINVAL;
+                    acc->bal.removed += q_sec;
+                } else {
+                    or_sec* s = &sec[(*n_sec)++];
+                    s->E = ev.sec_E;
+                    s->tau = ev.sec_tau;
+                    for (int i = 0; i < 3; ++i) {
+                        s->r[i] = r[i];
+                        s->u[i] = ev.sec_u[i];
+                    }
+                }
+            }
         }
         /* Termination (Sec. 2.1.3): absorbed below e_min, the rest deposited
          * at the current position. */
@@ -848,6 +899,29 @@ static void transport_history(const oracle_dose* d, const oracle_spot* s, uint64
             deposit_at(acc, voxel_of(d, r), Q(d, E));
             return;
         }
+    }
+}
+
+static void transport_history(const oracle_dose* d, const oracle_spot* s, uint64_t seed, uint64_t h,
+                              or_acc* acc) {
+    double E, r[3], u[3], tau;
+    sample_source(d, s, seed, h, &E, r, u, &tau);
+    acc->bal.incident += Q(d, E);
+    acc->bal.histories += 1;
+    or_sec sec[OR_MAX_SEC];
+    int n_sec = 0;
+    transport_track(d, seed, h, 0u, E, r, u, tau, acc, sec, &n_sec);
+    /* the secondaries of the branching model, in the order their primary emitted them
+     * (segment j = 1, 2, ...); they emit none themselves.  One starting below the
+     * absorption energy deposits its energy where it was emitted. */
+    for (int j = 0; j < n_sec; ++j) {
+        or_sec* q = &sec[j];
+        if (q->E < d->p.e_min_MeV) {
+            deposit_at(acc, voxel_of(d, q->r), Q(d, q->E));
+            continue;
+        }
+        int none = 0;
+        transport_track(d, seed, h, (uint32_t)(j + 1), q->E, q->r, q->u, q->tau, acc, NULL, &none);
     }
 }
 
@@ -968,6 +1042,36 @@ int oracle_fetch(oracle_dose* d, double* dose_Gy, uint64_t* edep_fixed, oracle_b
     return ORACLE_OK;
 }
 
+/* ----------------------------------------------- secondary-emission probe */
+int oracle_single_step_secondary(const oracle_material* mat, double rho, const oracle_params* p, double E,
+                                 uint64_t seed, uint64_t h0, int n, double* out) {
+    or_mat m;
+    int rc = resolve_material(mat, &m);
+    if (rc) return rc;
+    if (!p || check_params(p) || !(E > 0.0) || !(rho >= 0.0) || n < 0 || !out)
+        return fail(ORACLE_EINVAL, "bad probe arguments");
+    for (int i = 0; i < n; ++i) {
+        uint64_t h = h0 + (uint64_t)i;
+        double e = E, r[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 1.0}, tau, B[4];
+        draw4(seed, h, 0u, TAG_SRC_B, B);
+        tau = -log(B[2]);
+        or_step_ev ev;
+        sde_step(&m, rho, p, seed, h, 0u, 0u, &e, r, u, &tau, &ev);
+        double* o = out + 10 * (size_t)i;
+        o[0] = ev.jump;
+        o[1] = ev.E1;
+        o[2] = ev.E2;
+        o[3] = ev.spawn;
+        o[4] = ev.spawn ? ev.sec_E : 0.0;
+        for (int a = 0; a < 3; ++a) {
+            o[5 + a] = ev.spawn ? ev.sec_u[a] : 0.0;
+        }
+        o[8] = u[0];
+        o[9] = u[1];
+    }
+    return ORACLE_OK;
+}
+
 /* ------------------------------------------------------ source-sampling probe */
 int oracle_sample_source(const oracle_spot* s, const oracle_params* p, uint64_t seed, uint64_t h0, int n,
                          double* E_out, double* r_out, double* u_out) {
@@ -1006,7 +1110,7 @@ int oracle_single_step(const oracle_material* mat, double rho, const oracle_para
         draw4(seed, h, 0u, TAG_SRC_B, B);
         tau = -log(B[2]);
         or_step_ev ev;
-        sde_step(&m, rho, p, seed, h, 0u, &e, r, u, &tau, &ev);
+        sde_step(&m, rho, p, seed, h, 0u, 0u, &e, r, u, &tau, &ev);
         if (E_out) E_out[i] = e;
         if (cos_out) cos_out[i] = u[2];
         if (jump_out) jump_out[i] = ev.jump;

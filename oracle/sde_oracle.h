@@ -78,6 +78,11 @@ typedef struct {
     double theta_cut_sigmas; /* 0: fixed theta_cut_rad; k > 0: energy-dependent cut-off
                                 theta_c = k sigma(E) (Sec. 2.1.3, k = 2.5), clamped to
                                 [1e-4, 1] rad */
+    double secondary_fraction; /* 0: the paper's single-proton model.  kappa in (0, 1]:
+                                  branching SDE (Sec. 2.1.1, the extension the paper leaves
+                                  to future work): each non-elastic event of a primary also
+                                  emits a secondary proton carrying kappa u E' of the energy
+                                  deficit u E', transported by the same SDE */
 } oracle_params;
 
 typedef struct {
@@ -141,6 +146,11 @@ int oracle_csda_range(const oracle_material* m, double rho, const oracle_params*
 int oracle_single_step(const oracle_material* m, double rho, const oracle_params* p, double E,
                        uint64_t seed, uint64_t h0, int n, double* E_out, double* cos_out,
                        int* jump_out, double* ux_out, double* uy_out);
+/* As oracle_single_step, with what the branching model emits: per history 10 values
+ * (jump kind, E1 = energy after the continuous loss, energy after the event, spawned
+ * (0/1), secondary energy, secondary direction x/y/z, continuing direction x/y). */
+int oracle_single_step_secondary(const oracle_material* m, double rho, const oracle_params* p, double E,
+                                 uint64_t seed, uint64_t h0, int n, double* out);
 /* Y_0 of histories h = h0 .. h0+n-1 of one spot (the source sampling of a run): energy,
  * entry point (mm, 3 per history) and direction (3 per history); any output may be NULL. */
 int oracle_sample_source(const oracle_spot* s, const oracle_params* p, uint64_t seed, uint64_t h0, int n,
