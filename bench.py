@@ -432,6 +432,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     ap.add_argument("--theta-cut-sigmas", type=float, default=0.0,
                     help="energy-dependent elastic cut-off theta_c = k sigma(E) (0: the paper's fixed 0.02 rad)")
+    ap.add_argument("--secondary-fraction", type=float, default=0.0,
+                    help="branching model: each non-elastic event of a primary also emits a secondary "
+                         "proton with this fraction of the energy deficit (0: the paper's model)")
     ap.add_argument("--physics-mask", type=int, default=15,
                     help="ablation: SDE_PHYS_* bits of the transport (15 = all terms; 11 = no large-angle "
                          "elastic events, 3 = no jumps); a run with terms switched off is not the benchmark")
@@ -461,7 +464,8 @@ def main():
     wl = _make_workload(args.workload, per_gpu * ws)
     first, count = S.history_shard(wl.n_histories, rank, ws)
     stream = torch.cuda.Stream(device=dev)
-    d = S.SdeDose(wl, stream=stream, theta_cut_sigmas=args.theta_cut_sigmas, physics_mask=args.physics_mask)
+    d = S.SdeDose(wl, stream=stream, theta_cut_sigmas=args.theta_cut_sigmas, physics_mask=args.physics_mask,
+                  secondary_fraction=args.secondary_fraction)
     spots_dev = torch.from_numpy(wl.spots.view(np.uint8).copy()).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tuned = None
@@ -549,6 +553,8 @@ def main():
                    "elastic_cut_off": (f"theta_c = {args.theta_cut_sigmas} sigma(E)" if args.theta_cut_sigmas > 0
                                        else "fixed 0.02 rad"),
                    "physics_mask": args.physics_mask,
+                   "secondaries": (f"branching model, kappa {args.secondary_fraction} (one queued generation)"
+                                   if args.secondary_fraction > 0 else "none (the paper's single-proton model)"),
                    "autotuned": tuned is not None, "tuning": d.get_tuning()},
         "e2e": {"value": hist_per_step / e2e_T, "unit": "histories/s",
                 "h2d_bytes_per_step": int(wl.spots.nbytes),

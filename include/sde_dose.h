@@ -105,6 +105,18 @@ typedef struct {
                                (k = 2.5), sigma the Lynch-Dahl width over z at the step's
                                energy and density, clamped to [1e-4, 1] rad; it sets the
                                large-angle elastic rates and the jump's CM angle range   */
+    double secondary_fraction; /* 0: the paper's model, one proton per history (default).
+                               kappa in (0, 1]: branching SDE (Sec. 2.1.1 names it as the
+                               extension of the model): every non-elastic event of a primary
+                               also emits a secondary proton with energy kappa u E' (E' = the
+                               energy after the step's continuous loss, u the event's loss
+                               fraction), from the event point, at a Kalbach-Mann CM angle of
+                               its own (slope at emission fraction kappa u) about the incoming
+                               direction, with uniform azimuth; it is transported by the same
+                               SDE and emits no secondaries itself.  Its energy moves from
+                               "removed" to the tally or "escaped".  Secondaries wait in a
+                               device queue between two launches per chunk of histories; an
+                               overflow is SDE_EDEVICE (the balance stays exact)           */
 } sde_params;
 
 /* Energy balance in tally units: incident == deposited + escaped + removed

@@ -96,7 +96,8 @@ class Params(C.Structure):
                                           "backscatter_rad", "e_min_MeV", "K", "inel_u_lo",
                                           "inel_u_hi", "km_r", "e_max_MeV")] + [
         (n, C.c_int) for n in ("tally_mode", "fixed_point_shift", "max_steps", "physics_mask",
-                               "table_points")] + [("theta_cut_sigmas", C.c_double)]
+                               "table_points")] + [("theta_cut_sigmas", C.c_double),
+                                                   ("secondary_fraction", C.c_double)]
 
 
 class Balance(C.Structure):

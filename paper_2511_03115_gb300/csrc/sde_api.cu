@@ -73,7 +73,15 @@ struct sde_dose {
     // updated in place when only kernel arguments change
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    // branching model: the secondary queue (allocated on first use) and its two counters
+    SecRec* d_secq = nullptr;
+    unsigned long long* d_secctl = nullptr;
 };
+
+// Queue capacity of the branching model, in secondaries; histories run in chunks of this
+// many, so the queue overflows only if a chunk's primaries average more than one
+// non-elastic event each (about 0.1-0.4 do in water and bone at 70-230 MeV).
+static constexpr unsigned long long kSecQueueCap = 1ull << 21;
 
 extern "C" int sde_default_params(sde_params* p) {
     if (!p) return set_err(SDE_EINVAL, "params pointer is NULL");
@@ -94,6 +102,7 @@ extern "C" int sde_default_params(sde_params* p) {
     p->physics_mask = SDE_PHYS_ALL;
     p->theta_cut_sigmas = 0.0;
     p->table_points = 256;
+    p->secondary_fraction = 0.0;
     return SDE_OK;
 }
 
@@ -113,7 +122,8 @@ static int check_params(const sde_params& p) {
               (p.tally_mode == 0 || p.tally_mode == 1) && p.fixed_point_shift >= 0 &&
               p.fixed_point_shift <= 30 && p.max_steps > 0 && p.physics_mask >= 0 &&
               p.physics_mask <= SDE_PHYS_ALL && p.table_points >= 64 && p.table_points <= 4096 &&
-              p.theta_cut_sigmas >= 0.0 && p.theta_cut_sigmas <= 100.0;
+              p.theta_cut_sigmas >= 0.0 && p.theta_cut_sigmas <= 100.0 && p.secondary_fraction >= 0.0 &&
+              p.secondary_fraction <= 1.0;
     return ok ? SDE_OK : set_err(SDE_EINVAL, "invalid sde_params");
 }
 
@@ -121,7 +131,7 @@ static void free_all(sde_dose* d) {
     void* ptrs[] = {d->d_rho,   d->d_vox,      d->d_edep,   d->d_mats,        d->d_mj,
                     d->d_raw,   d->d_jrates,   d->d_csda,   d->d_table,       d->d_counters,
                     d->d_err,   d->d_raw_spots, d->d_spots, d->d_prefix,      d->d_dose,
-                    d->d_cut};
+                    d->d_cut,   d->d_secq,      d->d_secctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
@@ -374,7 +384,41 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
     P.n_spots = n_spots;
     P.counters = d->d_counters;
     P.err = d->d_err;
+    P.branch = 0;
+    P.sec_frac = (float)d->p.secondary_fraction;
+    P.sec_q = d->d_secq;
+    P.sec_ctl = d->d_secctl;
+    P.sec_cap = kSecQueueCap;
     return P;
+}
+
+// Branching model: per chunk of at most kSecQueueCap history ids, one launch of the
+// primaries (each non-elastic event queues a secondary) and one of the queued secondaries.
+// The spot preparation runs once; the plan's history count is read back to size the chunks.
+static int enqueue_branching(sde_dose* d, KParams P, const sde_spot* raw, int n, uint64_t h_begin, uint64_t h_end,
+                             int grid, int block) {
+    if (!d->d_secq) {
+        CUDA_TRY(cudaMalloc(&d->d_secq, kSecQueueCap * sizeof(SecRec)));
+        CUDA_TRY(cudaMalloc(&d->d_secctl, 2 * sizeof(unsigned long long)));
+    }
+    P.sec_q = d->d_secq;
+    P.sec_ctl = d->d_secctl;
+    CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
+                         d->p.e_max_MeV, d->stream, h_begin));
+    unsigned long long total = 0;
+    CUDA_TRY(cudaMemcpyAsync(&total, d->d_prefix + n, sizeof total, cudaMemcpyDeviceToHost, d->stream));
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+    const uint64_t end = std::min<uint64_t>(h_end, total);
+    for (uint64_t b = h_begin; b < end; b += kSecQueueCap) {
+        const uint64_t e = std::min<uint64_t>(end, b + kSecQueueCap);
+        CUDA_TRY(launch_branch_chunk(d->d_counters, d->d_secctl, b, d->stream));
+        P.branch = 1;
+        P.h_end = e;
+        CUDA_TRY(launch_transport(P, grid, block, 0, false, d->stream));
+        P.branch = 2;
+        CUDA_TRY(launch_transport(P, grid, block, 0, false, d->stream));
+    }
+    return SDE_OK;
 }
 
 // Histories with global ids in [h_begin, h_end) of the plan are transported.
@@ -386,12 +430,14 @@ static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t s
     int block = warps * 32;
     bool smem = d->tune.table_smem == 1 && d->table_bytes <= 96 * 1024;
     const bool cut = P.cut_k2 > 0.f;  // own kernels: no shared-memory tables or tally aggregation
-    if (cut) smem = false;
+    const bool branching = d->p.secondary_fraction > 0.0;  // so has the branching model
+    if (cut || branching) smem = false;
     int per_sm = transport_max_blocks_per_sm(block, smem ? d->table_bytes : 0, smem, d->p.tally_mode,
-                                             d->tune.aggregate == 2, cut);
+                                             d->tune.aggregate == 2, cut, branching ? 1 : 0);
     if (per_sm < 1) return set_err(SDE_ECUDA, "transport kernel cannot be resident with %d warps per block", warps);
     if (d->tune.blocks_per_sm > 0) per_sm = std::min(per_sm, d->tune.blocks_per_sm);
     int grid = d->num_sms * per_sm;
+    if (branching) return enqueue_branching(d, P, raw, n, h_begin, h_end, grid, block);
     if (d->tune.graph != 2) {
         CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
                              d->p.e_max_MeV, d->stream, h_begin));
@@ -591,9 +637,11 @@ static int read_counters(sde_dose* d, sde_balance* bal) {
     if (err) {
         CUDA_TRY(cudaMemsetAsync(d->d_err, 0, sizeof(unsigned int), d->stream));
         CUDA_TRY(cudaStreamSynchronize(d->stream));
-        return set_err(SDE_EDEVICE, "device error flag 0x%x:%s%s", err,
+        return set_err(SDE_EDEVICE, "device error flag 0x%x:%s%s%s", err,
                        (err & kErrStepCap) ? " step cap reached (history stopped, energy counted as escaped);" : "",
-                       (err & kErrBadSpot) ? " invalid device-resident spot (its histories were not run);" : "");
+                       (err & kErrBadSpot) ? " invalid device-resident spot (its histories were not run);" : "",
+                       (err & kErrSecQueue) ? " secondary queue full (those secondaries' energy counted as removed);"
+                                            : "");
     }
     return SDE_OK;
 }

@@ -26,7 +26,18 @@ constexpr float kTwoPiF = 6.28318530717958648f;
 enum : uint32_t { kTagStep = 0, kTagJumpA = 1, kTagJumpB = 2, kTagSrcA = 3, kTagSrcB = 4 };
 
 // Error flag bits raised on the device.
-enum : uint32_t { kErrStepCap = 1u, kErrBadSpot = 2u, kErrNaN = 4u };
+enum : uint32_t { kErrStepCap = 1u, kErrBadSpot = 2u, kErrNaN = 4u, kErrSecQueue = 16u };
+
+// A secondary proton of the branching model waiting for transport: its history, its
+// segment index (the j-th non-elastic event of the primary; it selects the random
+// streams through the upper bits of the Philox tag word), and its initial state.
+struct SecRec {
+    unsigned long long h;
+    uint32_t seg;
+    float E, px, py, pz, ux, uy, uz, tau;
+    uint32_t pad;
+};
+static_assert(sizeof(SecRec) == 48, "secondary record is 48 bytes");
 
 // Hot table row per (material, energy point E_k): three float4 =
 //   {f1, df1, f2, df2}  f1 = varsigma_1 beta^2 Delta / rho, f2 = sqrt(varsigma_2^2 Delta / rho)
@@ -91,6 +102,13 @@ struct KParams {
     int n_spots;
     unsigned long long* counters;  // kCntWords
     unsigned int* err;
+    // branching model: 0 plain transport; 1 primaries that queue their secondaries;
+    // 2 the queued secondaries.  sec_ctl[0] = records pushed, sec_ctl[1] = records claimed.
+    int branch;
+    float sec_frac;  // kappa
+    SecRec* sec_q;
+    unsigned long long* sec_ctl;
+    unsigned long long sec_cap;
 };
 
 // ------------------------------------------------------------ Philox4x32-10

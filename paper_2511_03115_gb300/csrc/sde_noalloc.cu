@@ -106,6 +106,9 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     const sde_params& p = *params;
     if (p.theta_cut_sigmas != 0.0)
         return noalloc_fail(SDE_EINVAL, "sde_transport_noalloc: the energy-dependent cut-off needs sde_dose_create");
+    if (p.secondary_fraction != 0.0)
+        return noalloc_fail(SDE_EINVAL, "sde_transport_noalloc: the branching model (secondary_fraction) needs "
+                                        "sde_dose_create");
     if (p.table_points < 64 || p.table_points > kNoallocMaxTablePoints)
         return noalloc_fail(SDE_EINVAL, "sde_transport_noalloc: table_points must be 64..256 (scratch limit)");
     if (!(p.step_cm > 0.0 && p.step_cm <= 1.0 && p.msc_z_cm > 0.0 && p.F > 0.0 && p.F < 1.0 &&

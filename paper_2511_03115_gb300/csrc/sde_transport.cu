@@ -171,6 +171,8 @@ __device__ void cm_to_lab(float E, float Eout, bool elastic, float m2, float cc,
 struct JumpOut {
     float ux, uy, uz, tau, e_fac;
     int kind;
+    float uu;  // non-elastic loss fraction u (0 for elastic events)
+    int el;    // element of the event
 };
 
 // A large-angle event of Eq. Npi at pre-step energy E (table interval k, fraction f):
@@ -182,8 +184,8 @@ struct JumpOut {
 template <bool CUT>
 __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k, float f, uint4 J, float ux,
                                         float uy, float uz, float tau, uint64_t h, uint32_t n, float s_c,
-                                        float sj) {
-    JumpOut o{ux, uy, uz, tau, 1.f, 0};
+                                        float sj, uint32_t segtag) {
+    JumpOut o{ux, uy, uz, tau, 1.f, 0, 0.f, 0};
     const MatJump& mj = P.mats[m];
     const float* r0 = P.jrates + (uint32_t)(m * P.N + k) * (uint32_t)(2 * SDE_MAX_ELEMENTS);
     const float* r1 = r0 + 2 * SDE_MAX_ELEMENTS;
@@ -229,14 +231,16 @@ __device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k,
         }
         cm_to_lab(E, E, true, m2, cc, sc, cl, sl);
     } else {
-        uint4 J2 = philox(P, n, kTagJumpB, h);
+        uint4 J2 = philox(P, n, kTagJumpB | segtag, h);
         float uu = P.inel_lo + P.inel_span * u01(J.y);
         float mu = kalbach_mu(u01(J2.x), kalbach_a(E, uu, mj.A[el]), P.km_r);
         cc = mu;
         sc = sqrtf(fmaxf(0.f, (1.f - mu) * (1.f + mu)));
         cm_to_lab(E, E * (1.f - uu), false, m2, cc, sc, cl, sl);
         o.e_fac = 1.f - uu;
+        o.uu = uu;
     }
+    o.el = el;
     float sp, cp;
     __sincosf(kTwoPiF * u01(J.z), &sp, &cp);
     rotate(o.ux, o.uy, o.uz, cl, sl, cp, sp);
@@ -308,7 +312,7 @@ __device__ __forceinline__ int sde_step(const KParams& P, const float4* tab, int
     Phys ph;
     int jump = 0;
     if (sde_step_cont<CUT>(P, tab, m, rho, x, E, ux, uy, uz, tau, E1, s_c, ph, sj)) {
-        JumpOut o = do_jump<CUT>(P, m, E, ph.k, ph.f, philox(P, n, kTagJumpA, h), ux, uy, uz, tau, h, n, s_c, sj);
+        JumpOut o = do_jump<CUT>(P, m, E, ph.k, ph.f, philox(P, n, kTagJumpA, h), ux, uy, uz, tau, h, n, s_c, sj, 0u);
         ux = o.ux;
         uy = o.uy;
         uz = o.uz;
@@ -362,6 +366,48 @@ __device__ SDE_INIT_ATTR void init_history(const KParams& P, uint64_t h, float& 
         rotate(ux, uy, uz, ct, st, cp, sp);
     }
     tau = -__logf(u01(B.z));
+}
+
+// Branching model: the secondary proton of a primary's non-elastic event (its j-th), in
+// the order of the oracle: energy kappa u E1 (E1 = the primary's post-loss energy), a
+// Kalbach-Mann CM angle at slope a(E_n, 1 - kappa u) converted to the lab with outgoing
+// energy kappa u E_n, about the incoming (diffused) direction, uniform azimuth, a fresh
+// clock; draws y, z, w of the event's second Philox block.  Starts at the primary's
+// position R_{n+1}.  Pushed to the queue; returns its energy in tally units, or 0 when the
+// queue is full (the caller then counts that energy as removed and the flag is raised).
+__device__ __noinline__ unsigned long long spawn_secondary(const KParams& P, int m, int el, float En, float E1,
+                                                           float uu, float ux, float uy, float uz, float px,
+                                                           float py, float pz, uint64_t h, uint32_t n,
+                                                           uint32_t j) {
+    const MatJump& mj = P.mats[m];
+    const float ks = P.sec_frac * uu;
+    const float Es = ks * E1;
+    const uint4 J2 = philox(P, n, kTagJumpB, h);
+    const float mu = kalbach_mu(u01(J2.y), kalbach_a(En, 1.f - ks, mj.A[el]), P.km_r);
+    float cl, sl;
+    cm_to_lab(En, En * ks, false, mj.m2[el], mu, sqrtf(fmaxf(0.f, (1.f - mu) * (1.f + mu))), cl, sl);
+    float sp, cp;
+    __sincosf(kTwoPiF * u01(J2.z), &sp, &cp);
+    rotate(ux, uy, uz, cl, sl, cp, sp);
+    const unsigned long long slot = atomicAdd(P.sec_ctl, 1ull);
+    if (slot >= P.sec_cap) {
+        atomicOr(P.err, kErrSecQueue);
+        return 0ull;
+    }
+    SecRec r;
+    r.h = h;
+    r.seg = j;
+    r.E = Es;
+    r.px = px;
+    r.py = py;
+    r.pz = pz;
+    r.ux = ux;
+    r.uy = uy;
+    r.uz = uz;
+    r.tau = -__logf(u01(J2.w));
+    r.pad = 0u;
+    P.sec_q[slot] = r;
+    return qfix(P, Es);
 }
 
 __device__ __forceinline__ int voxel_index(const KParams& P, float px, float py, float pz) {
@@ -440,7 +486,9 @@ __device__ unsigned long long deposit_chord(const KParams& P, float ax, float ay
 // deposited total is the sum of the tally, reduced when the balance is read.
 #define SDE_BLOCK_ADD(idx, v) atomicAdd(&s_cnt[idx], (unsigned long long)(v))
 
-template <int TALLY, bool SMEM, bool AGG, bool CUT>
+// BR: 0 plain transport; 1 primaries that queue the secondaries of the branching model;
+// 2 the queued secondaries (work items are queue records, not history ids).
+template <int TALLY, bool SMEM, bool AGG, bool CUT, int BR>
 __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_constant__ KParams P) {
     extern __shared__ float4 s_tab[];
     __shared__ unsigned long long s_cnt[kCntWords];
@@ -457,11 +505,15 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const unsigned long long total = P.prefix[P.n_spots] < P.h_end ? P.prefix[P.n_spots] : P.h_end;
+    unsigned long long total = P.prefix[P.n_spots] < P.h_end ? P.prefix[P.n_spots] : P.h_end;
+    if (BR == 2) total = P.sec_ctl[0] < P.sec_cap ? P.sec_ctl[0] : P.sec_cap;
+    unsigned long long* const cursor = BR == 2 ? &P.sec_ctl[1] : &P.counters[kCntCursor];
     bool alive = false;
     float E = 0.f, px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 1.f, tau = 1.f;
     unsigned long long h = 0;
     uint32_t n = 0;
+    uint32_t segtag = 0;  // BR 2: the track's segment index << 8 (Philox tag bits)
+    uint32_t nsec = 0;    // BR 1: non-elastic events of the primary so far
     // Pending large-angle event of step n - 1: the material of that step (-1: none),
     // its pre-step energy, its cut-off and its total jump rate.
     int jm = -1;
@@ -484,7 +536,7 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
                 unsigned long long b_next = *s_next, b_end = *s_end;
                 if (b_next >= b_end) {
                     unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(&P.counters[kCntCursor], (unsigned long long)P.batch);
+                    if (lane == 0) base = atomicAdd(cursor, (unsigned long long)P.batch);
                     base = __shfl_sync(0xffffffffu, base, 0);
                     if (base >= total) {
                         drained = true;
@@ -498,15 +550,40 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
                 int take = (unsigned long long)nd < avail ? nd : (int)avail;
                 int rank = __popc(dead & ((1u << lane) - 1u));
                 if (((dead >> lane) & 1u) && rank < take) {
-                    h = b_next + (unsigned long long)rank;
-                    init_history(P, h, E, px, py, pz, ux, uy, uz, tau);
-                    SDE_BLOCK_ADD(kCntIncident, qfix(P, E));
-                    SDE_BLOCK_ADD(kCntHistories, 1);
                     n = 0;
                     alive = true;
+                    if (BR == 2) {
+                        const SecRec& r = P.sec_q[b_next + (unsigned long long)rank];
+                        h = r.h;
+                        segtag = r.seg << 8;
+                        E = r.E;
+                        px = r.px;
+                        py = r.py;
+                        pz = r.pz;
+                        ux = r.ux;
+                        uy = r.uy;
+                        uz = r.uz;
+                        tau = r.tau;
+                    } else {
+                        h = b_next + (unsigned long long)rank;
+                        init_history(P, h, E, px, py, pz, ux, uy, uz, tau);
+                        SDE_BLOCK_ADD(kCntIncident, qfix(P, E));
+                        SDE_BLOCK_ADD(kCntHistories, 1);
+                        nsec = 0;
+                    }
                     vcur = voxel_index(P, px, py, pz);
                     vox = vcur >= 0 ? __ldg(&P.vox[vcur]) : 0u;
-                    x = philox(P, 0u, kTagStep, h);
+                    x = philox(P, 0u, kTagStep | segtag, h);
+                    if (BR == 2 && E < P.e_min) {  // emitted below the absorption energy
+                        unsigned long long qr = qfix(P, E);
+                        if (qr) {
+                            if (vcur >= 0)
+                                atomicAdd(&P.edep[vcur], qr);
+                            else
+                                SDE_BLOCK_ADD(kCntEscaped, qr);
+                        }
+                        alive = false;
+                    }
                 }
                 b_next += (unsigned long long)take;
                 __syncwarp();
@@ -527,8 +604,11 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
             float f;
             grid_pos(P, jE, k, f);  // the table position the step's lookup used
             const uint32_t nj = n - 1u;
-            JumpOut o =
-                do_jump<CUT>(P, jm, jE, k, f, philox(P, nj, kTagJumpA, h), ux, uy, uz, tau, h, nj, jsc, jsj);
+            JumpOut o = do_jump<CUT>(P, jm, jE, k, f, philox(P, nj, kTagJumpA | segtag, h), ux, uy, uz, tau, h,
+                                     nj, jsc, jsj, segtag);
+            unsigned long long q_sec = 0;
+            if (BR == 1 && o.kind == 2)  // the secondary leaves the incoming direction at R_{n+1}
+                q_sec = spawn_secondary(P, jm, o.el, jE, E, o.uu, ux, uy, uz, px, py, pz, h, nj, ++nsec);
             ux = o.ux;
             uy = o.uy;
             uz = o.uz;
@@ -536,7 +616,9 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
             jm = -1;
             if (o.kind == 2) {
                 const float Ej = E * o.e_fac;  // E is still the step's post-loss energy E1
-                SDE_BLOCK_ADD(kCntRemoved, qfix(P, E) - qfix(P, Ej));
+                // the deficit leaves the transport except what a secondary carries on (the
+                // three terms are roundings; their sum over a launch is exact modulo 2^64)
+                SDE_BLOCK_ADD(kCntRemoved, qfix(P, E) - qfix(P, Ej) - q_sec);
                 SDE_BLOCK_ADD(kCntJumpInel, 1);
                 E = Ej;
             } else if (o.kind == 1) {
@@ -574,7 +656,7 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
         const int vnext = voxel_index(P, px, py, pz);
         const uint32_t vox_next = vnext >= 0 ? __ldg(&P.vox[vnext]) : 0u;
         const uint4 xcur = x;
-        x = philox(P, n + 1u, kTagStep, h);
+        x = philox(P, n + 1u, kTagStep | segtag, h);
         const unsigned long long q0 = qfix(P, E);
         float E1, s_c, sj;
         Phys ph;
@@ -747,43 +829,56 @@ __global__ void k_convert(const unsigned long long* edep, const float* rho, size
 }
 
 // ---------------------------------------------------------------- launchers
-template <int TALLY, bool SMEM, bool AGG, bool CUT>
+template <int TALLY, bool SMEM, bool AGG, bool CUT, int BR>
 static cudaError_t allow_smem(size_t smem) {
     if (!SMEM) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG, CUT>,
+    cudaError_t e = cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG, CUT, BR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
 #ifdef SDE_SMEM_CARVEOUT
-    e = cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG, CUT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(k_transport<TALLY, SMEM, AGG, CUT, BR>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              SDE_SMEM_CARVEOUT);
 #endif
     return e;
 }
 
-template <int TALLY, bool SMEM, bool AGG, bool CUT>
+template <int TALLY, bool SMEM, bool AGG, bool CUT, int BR = 0>
 static cudaError_t launch_t(const KParams& P, int grid, int block, size_t smem, cudaStream_t st) {
-    cudaError_t e = allow_smem<TALLY, SMEM, AGG, CUT>(smem);
+    cudaError_t e = allow_smem<TALLY, SMEM, AGG, CUT, BR>(smem);
     if (e != cudaSuccess) return e;
-    k_transport<TALLY, SMEM, AGG, CUT><<<grid, block, SMEM ? smem : 0, st>>>(P);
+    k_transport<TALLY, SMEM, AGG, CUT, BR><<<grid, block, SMEM ? smem : 0, st>>>(P);
     return cudaGetLastError();
 }
 
-template <int TALLY, bool SMEM, bool AGG, bool CUT>
+template <int TALLY, bool SMEM, bool AGG, bool CUT, int BR = 0>
 static int blocks_per_sm_t(int block, size_t smem) {
-    if (allow_smem<TALLY, SMEM, AGG, CUT>(smem) != cudaSuccess) return 0;
+    if (allow_smem<TALLY, SMEM, AGG, CUT, BR>(smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<TALLY, SMEM, AGG, CUT>, block,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transport<TALLY, SMEM, AGG, CUT, BR>, block,
                                                       SMEM ? smem : 0) != cudaSuccess)
         return 0;
     return nb;
 }
 
+// Branching-model kernels: tables through L1 and per-lane atomics, either tally mode and
+// either cut-off; BR 1 (primaries) or 2 (queued secondaries).
+template <int BR>
+static cudaError_t launch_branch(const KParams& P, int grid, int block, cudaStream_t st) {
+    if (P.cut_k2 > 0.f)
+        return P.tally_mode == 1 ? launch_t<1, false, false, true, BR>(P, grid, block, 0, st)
+                                 : launch_t<0, false, false, true, BR>(P, grid, block, 0, st);
+    return P.tally_mode == 1 ? launch_t<1, false, false, false, BR>(P, grid, block, 0, st)
+                             : launch_t<0, false, false, false, BR>(P, grid, block, 0, st);
+}
+
 // Variant selection: tally mode (midpoint, chord), table placement, and warp
 // aggregation of the tally; the energy-dependent cut-off has its own kernels (midpoint
 // or chord tally, tables through L1, per-lane atomics) so that the fixed-cut-off ones
-// carry none of its arithmetic.
+// carry none of its arithmetic; so has the branching model.
 cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_table, bool use_smem,
                              cudaStream_t st) {
+    if (P.branch == 1) return launch_branch<1>(P, grid, block, st);
+    if (P.branch == 2) return launch_branch<2>(P, grid, block, st);
     if (P.cut_k2 > 0.f)
         return P.tally_mode == 1 ? launch_t<1, false, false, true>(P, grid, block, 0, st)
                                  : launch_t<0, false, false, true>(P, grid, block, 0, st);
@@ -797,7 +892,24 @@ cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_
                     : launch_t<0, false, false, false>(P, grid, block, 0, st);
 }
 
-int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode, bool aggregate, bool cut) {
+int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode, bool aggregate, bool cut,
+                                int branch) {
+    if (branch) {
+        // the primary and secondary kernels of one configuration run with one grid
+        int a, b;
+        if (cut) {
+            a = tally_mode == 1 ? blocks_per_sm_t<1, false, false, true, 1>(block, 0)
+                                : blocks_per_sm_t<0, false, false, true, 1>(block, 0);
+            b = tally_mode == 1 ? blocks_per_sm_t<1, false, false, true, 2>(block, 0)
+                                : blocks_per_sm_t<0, false, false, true, 2>(block, 0);
+        } else {
+            a = tally_mode == 1 ? blocks_per_sm_t<1, false, false, false, 1>(block, 0)
+                                : blocks_per_sm_t<0, false, false, false, 1>(block, 0);
+            b = tally_mode == 1 ? blocks_per_sm_t<1, false, false, false, 2>(block, 0)
+                                : blocks_per_sm_t<0, false, false, false, 2>(block, 0);
+        }
+        return a < b ? a : b;
+    }
     if (cut)
         return tally_mode == 1 ? blocks_per_sm_t<1, false, false, true>(block, 0)
                                : blocks_per_sm_t<0, false, false, true>(block, 0);
@@ -809,6 +921,21 @@ int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally
                         : blocks_per_sm_t<0, false, true, false>(block, 0);
     return use_smem ? blocks_per_sm_t<0, true, false, false>(block, smem)
                     : blocks_per_sm_t<0, false, false, false>(block, 0);
+}
+
+// Start of one chunk of the branching model: the work-queue cursor at the chunk's first
+// history id and an empty secondary queue.
+__global__ void k_branch_chunk(unsigned long long* counters, unsigned long long* sec_ctl,
+                               unsigned long long h_begin) {
+    counters[kCntCursor] = h_begin;
+    sec_ctl[0] = 0ull;
+    sec_ctl[1] = 0ull;
+}
+
+cudaError_t launch_branch_chunk(unsigned long long* counters, unsigned long long* sec_ctl,
+                                unsigned long long h_begin, cudaStream_t st) {
+    k_branch_chunk<<<1, 1, 0, st>>>(counters, sec_ctl, h_begin);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,

@@ -13,7 +13,9 @@ constexpr int kMaxWarpsPerBlock = 8;  // the transport kernel is compiled for <=
 cudaError_t launch_transport(const KParams& P, int grid, int block, size_t smem_table, bool use_smem,
                              cudaStream_t st);
 int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally_mode, bool aggregate,
-                                bool cut = false);
+                                bool cut = false, int branch = 0);
+cudaError_t launch_branch_chunk(unsigned long long* counters, unsigned long long* sec_ctl,
+                                unsigned long long h_begin, cudaStream_t st);
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,
                         unsigned long long* counters, unsigned int* err, const double o[3], double e_min,
                         double e_lim, cudaStream_t st, unsigned long long h_begin = 0);
