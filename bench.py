@@ -66,6 +66,8 @@ WORKLOADS = {
                  "0.2-1.9 g/cm3); one persistent autotuned launch", 100_000_000),
     "slab150": ("slab150: 150 MeV pencil beam (sigma_xy 3 mm), 1e6 protons per GPU, "
                 "60x60x200 mm at 0.5 mm (120x120x400 voxels), water/bone-like/lung-like/water slabs", 1_000_000),
+    "insert150": ("insert150: 150 MeV beam (sigma_xy 3 mm), 1e7 protons per GPU, 80x80x200 mm at 1 mm, water with "
+                  "a bone-like half-space insert (x > 0, z 30-80 mm) whose edge lies on the beam axis", 10_000_000),
     "ct_sobp": ("ct_sobp: thorax-like synthetic CT 120x120x240 mm at 1 mm (air, lung, adipose, soft tissue, "
                 "cortical bone from HU), 16-layer spread-out Bragg peak 90-140 mm, 256 spots, 1e6 protons per GPU",
                 1_000_000),
@@ -73,8 +75,8 @@ WORKLOADS = {
 
 
 def _make_workload(name, total):
-    from sde_workloads import ct_sobp, plan2000, slab150
-    return {"plan2000": plan2000, "slab150": slab150, "ct_sobp": ct_sobp}[name](total)
+    from sde_workloads import ct_sobp, insert150, plan2000, slab150
+    return {"plan2000": plan2000, "slab150": slab150, "insert150": insert150, "ct_sobp": ct_sobp}[name](total)
 
 
 def transport_source_hash():
@@ -423,7 +425,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="plan2000", choices=sorted(WORKLOADS),
-                    help="plan2000 (default): the batched 2000-spot plan with 1e8 protons; slab150; ct_sobp")
+                    help="plan2000 (default): the batched 2000-spot plan with 1e8 protons; slab150; insert150; ct_sobp")
     ap.add_argument("--histories", type=int, default=0, help="protons per GPU (0: the workload's own count)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -341,6 +341,10 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
     P.inv_hz = (float)(1.0 / d->h[2]);
     P.step_mm = (float)(d->p.step_cm * 10.0);
     P.half_step_mm = (float)(d->p.step_cm * 5.0);
+    P.sv_xy = make_float2((float)(d->p.step_cm * 10.0 / d->h[0]), (float)(d->p.step_cm * 10.0 / d->h[1]));
+    P.sv_z = (float)(d->p.step_cm * 10.0 / d->h[2]);
+    P.hv_xy = make_float2((float)(d->p.step_cm * 5.0 / d->h[0]), (float)(d->p.step_cm * 5.0 / d->h[1]));
+    P.hv_z = (float)(d->p.step_cm * 5.0 / d->h[2]);
     P.inv_delta_cm = (float)(1.0 / d->p.step_cm);
     P.e_min = (float)d->p.e_min_MeV;
     P.e_max = (float)d->p.e_max_MeV;
@@ -403,7 +407,7 @@ static int enqueue_branching(sde_dose* d, KParams P, const sde_spot* raw, int n,
     }
     P.sec_q = d->d_secq;
     P.sec_ctl = d->d_secctl;
-    CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
+    CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->h, d->p.e_min_MeV,
                          d->p.e_max_MeV, d->stream, h_begin));
     unsigned long long total = 0;
     CUDA_TRY(cudaMemcpyAsync(&total, d->d_prefix + n, sizeof total, cudaMemcpyDeviceToHost, d->stream));
@@ -439,7 +443,7 @@ static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t s
     int grid = d->num_sms * per_sm;
     if (branching) return enqueue_branching(d, P, raw, n, h_begin, h_end, grid, block);
     if (d->tune.graph != 2) {
-        CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
+        CUDA_TRY(launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->h, d->p.e_min_MeV,
                              d->p.e_max_MeV, d->stream, h_begin));
         CUDA_TRY(launch_transport(P, grid, block, d->table_bytes, smem, d->stream));
         return SDE_OK;
@@ -449,7 +453,7 @@ static int enqueue_transport(sde_dose* d, const sde_spot* raw, int n, uint64_t s
     // the same shape) or re-instantiate, then launch it on the handle's stream.
     if (!d->capture_stream) CUDA_TRY(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamBeginCapture(d->capture_stream, cudaStreamCaptureModeRelaxed));
-    cudaError_t e1 = launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->p.e_min_MeV,
+    cudaError_t e1 = launch_prep(raw, n, d->d_spots, d->d_prefix, d->d_counters, d->d_err, d->o, d->h, d->p.e_min_MeV,
                                  d->p.e_max_MeV, d->capture_stream, h_begin);
     cudaError_t e2 = e1 == cudaSuccess
                          ? launch_transport(P, grid, block, d->table_bytes, smem, d->capture_stream)

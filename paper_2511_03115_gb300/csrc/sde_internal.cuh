@@ -58,8 +58,9 @@ struct MatJump {
     float m2[SDE_MAX_ELEMENTS];  // target rest energy, MeV
 };
 
-// Beam spot in device form: position relative to the phantom origin (mm),
-// unit direction and the two unit vectors spanning the lateral plane.
+// Beam spot in device form: position relative to the phantom origin in voxel units
+// (mm over the voxel size of each axis), unit direction, and the two unit vectors
+// spanning the lateral plane times the lateral sigma, in voxel units per axis.
 struct SpotDev {
     float E, sE, sxy, sang;
     float px, py, pz, pad0;
@@ -77,6 +78,10 @@ struct KParams {
     int nx, ny, nz, n_mats;
     float inv_hx, inv_hy, inv_hz;
     float step_mm, half_step_mm;
+    // Positions are kept in voxel units: one step and half a step along each axis
+    // (x and y as a pair for the packed FP32x2 multiply-add).
+    float2 sv_xy, hv_xy;
+    float sv_z, hv_z;
     float inv_delta_cm;  // 1 / Delta (1/cm): jump rates x Delta back to rates
     float e_min, e_max;
     float qscale;  // 2^S
@@ -114,18 +119,19 @@ struct KParams {
 // ------------------------------------------------------------ Philox4x32-10
 // Salmon et al., SC'11.  Counter (n, tag, h_lo, h_hi); the ten round keys of
 // the seed are precomputed on the host (Weyl sequence 0x9E3779B9, 0xBB67AE85).
+// Each round's two 32x32 -> 64-bit products are formed as 64-bit multiplies (one
+// wide integer multiply-add each, high and low halves together).
 __device__ __forceinline__ uint4 philox(const KParams& P, uint32_t n, uint32_t tag, uint64_t h) {
     uint32_t c0 = n, c1 = tag, c2 = (uint32_t)h, c3 = (uint32_t)(h >> 32);
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        uint32_t n0 = hi1 ^ c1 ^ P.rk0[r];
-        uint32_t n2 = hi0 ^ c3 ^ P.rk1[r];
+        const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u, p1 = (uint64_t)c2 * 0xCD9E8D57u;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ P.rk0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ P.rk1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
         c0 = n0;
-        c1 = lo1;
         c2 = n2;
-        c3 = lo0;
     }
     return make_uint4(c0, c1, c2, c3);
 }

@@ -203,7 +203,8 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     tb.d_csda = csda;
     tb.d_table = table;
     NA_TRY(build_tables(tb, st));
-    NA_TRY(launch_prep(d_spots, n_spots, spots, prefix, counters, err, origin_mm, p.e_min_MeV, p.e_max_MeV, st));
+    NA_TRY(launch_prep(d_spots, n_spots, spots, prefix, counters, err, origin_mm, voxel_mm, p.e_min_MeV,
+                       p.e_max_MeV, st));
     const size_t nv = (size_t)nx * ny * nz;
     k_check_voxels<<<sms * 4, 256, 0, st>>>(d_vox, nv, n_mats, err, counters + kCntCursor);
     NA_TRY(cudaGetLastError());
@@ -223,6 +224,10 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     P.inv_hz = (float)(1.0 / voxel_mm[2]);
     P.step_mm = (float)(p.step_cm * 10.0);
     P.half_step_mm = (float)(p.step_cm * 5.0);
+    P.sv_xy = make_float2((float)(p.step_cm * 10.0 / voxel_mm[0]), (float)(p.step_cm * 10.0 / voxel_mm[1]));
+    P.sv_z = (float)(p.step_cm * 10.0 / voxel_mm[2]);
+    P.hv_xy = make_float2((float)(p.step_cm * 5.0 / voxel_mm[0]), (float)(p.step_cm * 5.0 / voxel_mm[1]));
+    P.hv_z = (float)(p.step_cm * 5.0 / voxel_mm[2]);
     P.inv_delta_cm = (float)(1.0 / p.step_cm);
     P.e_min = (float)p.e_min_MeV;
     P.e_max = (float)p.e_max_MeV;

@@ -9,8 +9,8 @@
 // ranks), so it carries a cohort of histories of one spot in lock-step.  The
 // per-step physics comes from FP32 tables read through L1 (optionally staged
 // in shared memory); each step draws one Philox4x32-10 block keyed by (seed,
-// history, step); a large-angle event is sampled out of line at the top of the
-// next iteration; the energy lost in the step is committed as a 64-bit
+// history, step); a large-angle event is sampled at the top of the next
+// iteration, outside the step body; the energy lost in the step is committed as a 64-bit
 // fixed-point integer atomic, so the tally does not depend on execution order.
 #include <math.h>
 
@@ -182,7 +182,7 @@ struct JumpOut {
 // CUT: the energy-dependent cut-off s_c = 1 - cos(theta_c) of this step (compiled
 // separately so that the fixed-cut-off kernel carries none of it).
 template <bool CUT>
-__device__ __noinline__ JumpOut do_jump(const KParams& P, int m, float E, int k, float f, uint4 J, float ux,
+__device__ __forceinline__ JumpOut do_jump(const KParams& P, int m, float E, int k, float f, uint4 J, float ux,
                                         float uy, float uz, float tau, uint64_t h, uint32_t n, float s_c,
                                         float sj, uint32_t segtag) {
     JumpOut o{ux, uy, uz, tau, 1.f, 0, 0.f, 0};
@@ -352,9 +352,9 @@ __device__ SDE_INIT_ATTR void init_history(const KParams& P, uint64_t h, float& 
     float g1 = r * ca, g2 = r * sa;
     float g3 = step_sqrt(-2.f * __logf(u01(A.z))) * __cosf(kTwoPiF * u01(A.w));
     E = fminf(fmaxf(s.E + s.sE * g3, P.e_min), P.e_max);
-    px = s.px + s.sxy * (g1 * s.e1x + g2 * s.e2x);
-    py = s.py + s.sxy * (g1 * s.e1y + g2 * s.e2y);
-    pz = s.pz + s.sxy * (g1 * s.e1z + g2 * s.e2z);
+    px = fmaf(g1, s.e1x, fmaf(g2, s.e2x, s.px));  // voxel units (the basis carries sigma / h)
+    py = fmaf(g1, s.e1y, fmaf(g2, s.e2y, s.py));
+    pz = fmaf(g1, s.e1z, fmaf(g2, s.e2z, s.pz));
     ux = s.ux;
     uy = s.uy;
     uz = s.uz;
@@ -410,10 +410,11 @@ __device__ __noinline__ unsigned long long spawn_secondary(const KParams& P, int
     return qfix(P, Es);
 }
 
-__device__ __forceinline__ int voxel_index(const KParams& P, float px, float py, float pz) {
-    int ix = __float2int_rd(px * P.inv_hx);
-    int iy = __float2int_rd(py * P.inv_hy);
-    int iz = __float2int_rd(pz * P.inv_hz);
+// Voxel containing a point given in voxel units (floor convention; -1 outside).
+__device__ __forceinline__ int voxel_index(const KParams& P, float gx, float gy, float gz) {
+    int ix = __float2int_rd(gx);
+    int iy = __float2int_rd(gy);
+    int iz = __float2int_rd(gz);
     if ((unsigned)ix >= (unsigned)P.nx || (unsigned)iy >= (unsigned)P.ny || (unsigned)iz >= (unsigned)P.nz)
         return -1;
     return ix + P.nx * (iy + P.ny * iz);
@@ -424,14 +425,14 @@ __device__ __forceinline__ int voxel_index(const KParams& P, float px, float py,
 __device__ __forceinline__ int vox_mat(uint32_t w) { return (int)(w & 15u); }
 __device__ __forceinline__ float vox_rho(uint32_t w) { return __uint_as_float(w & ~15u); }
 
-// Split dq along the chord (ax,ay,az) + t (dx,dy,dz), t in [0,1], over the
-// voxels it crosses, in proportion to the length inside each (Amanatides-Woo
+// Split dq along the chord (ax,ay,az) + t (dx,dy,dz), t in [0,1] (voxel units), over
+// the voxels it crosses, in proportion to the length inside each (Amanatides-Woo
 // traversal).  Pieces are cumulative roundings of t dq, so they sum to dq.
 // Returns the part that falls outside the grid.
 __device__ unsigned long long deposit_chord(const KParams& P, float ax, float ay, float az, float dx,
                                             float dy, float dz, unsigned long long dq) {
-    float g[3] = {ax * P.inv_hx, ay * P.inv_hy, az * P.inv_hz};
-    float v[3] = {dx * P.inv_hx, dy * P.inv_hy, dz * P.inv_hz};
+    float g[3] = {ax, ay, az};
+    float v[3] = {dx, dy, dz};
     int n[3] = {P.nx, P.ny, P.nz};
     int i[3], st[3];
     float tmax[3], tdel[3];
@@ -509,7 +510,9 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
     if (BR == 2) total = P.sec_ctl[0] < P.sec_cap ? P.sec_ctl[0] : P.sec_cap;
     unsigned long long* const cursor = BR == 2 ? &P.sec_ctl[1] : &P.counters[kCntCursor];
     bool alive = false;
-    float E = 0.f, px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 1.f, tau = 1.f;
+    // position (voxel units) and direction; x and y as pairs for packed FP32x2 arithmetic
+    float2 pxy = make_float2(0.f, 0.f), uxy = make_float2(0.f, 0.f);
+    float E = 0.f, pz = 0.f, uz = 1.f, tau = 1.f;
     unsigned long long h = 0;
     uint32_t n = 0;
     uint32_t segtag = 0;  // BR 2: the track's segment index << 8 (Philox tag bits)
@@ -557,21 +560,19 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
                         h = r.h;
                         segtag = r.seg << 8;
                         E = r.E;
-                        px = r.px;
-                        py = r.py;
+                        pxy = make_float2(r.px, r.py);
                         pz = r.pz;
-                        ux = r.ux;
-                        uy = r.uy;
+                        uxy = make_float2(r.ux, r.uy);
                         uz = r.uz;
                         tau = r.tau;
                     } else {
                         h = b_next + (unsigned long long)rank;
-                        init_history(P, h, E, px, py, pz, ux, uy, uz, tau);
+                        init_history(P, h, E, pxy.x, pxy.y, pz, uxy.x, uxy.y, uz, tau);
                         SDE_BLOCK_ADD(kCntIncident, qfix(P, E));
                         SDE_BLOCK_ADD(kCntHistories, 1);
                         nsec = 0;
                     }
-                    vcur = voxel_index(P, px, py, pz);
+                    vcur = voxel_index(P, pxy.x, pxy.y, pz);
                     vox = vcur >= 0 ? __ldg(&P.vox[vcur]) : 0u;
                     x = philox(P, 0u, kTagStep | segtag, h);
                     if (BR == 2 && E < P.e_min) {  // emitted below the absorption energy
@@ -604,13 +605,13 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
             float f;
             grid_pos(P, jE, k, f);  // the table position the step's lookup used
             const uint32_t nj = n - 1u;
-            JumpOut o = do_jump<CUT>(P, jm, jE, k, f, philox(P, nj, kTagJumpA | segtag, h), ux, uy, uz, tau, h,
-                                     nj, jsc, jsj, segtag);
+            JumpOut o = do_jump<CUT>(P, jm, jE, k, f, philox(P, nj, kTagJumpA | segtag, h), uxy.x, uxy.y, uz,
+                                     tau, h, nj, jsc, jsj, segtag);
             unsigned long long q_sec = 0;
             if (BR == 1 && o.kind == 2)  // the secondary leaves the incoming direction at R_{n+1}
-                q_sec = spawn_secondary(P, jm, o.el, jE, E, o.uu, ux, uy, uz, px, py, pz, h, nj, ++nsec);
-            ux = o.ux;
-            uy = o.uy;
+                q_sec = spawn_secondary(P, jm, o.el, jE, E, o.uu, uxy.x, uxy.y, uz, pxy.x, pxy.y, pz, h, nj,
+                                        ++nsec);
+            uxy = make_float2(o.ux, o.uy);
             uz = o.uz;
             tau = o.tau;
             jm = -1;
@@ -649,18 +650,18 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
         const float rho = vox_rho(vox);
         // Position line of Eq. VSDE along the pre-step direction; the next voxel word
         // is requested now and consumed by the next step.
-        const float ox = px, oy = py, oz = pz, oux = ux, ouy = uy, ouz = uz;
-        px = fmaf(oux, P.step_mm, px);
-        py = fmaf(ouy, P.step_mm, py);
-        pz = fmaf(ouz, P.step_mm, pz);
-        const int vnext = voxel_index(P, px, py, pz);
+        const float2 oxy = pxy, ouxy = uxy;
+        const float oz = pz, ouz = uz;
+        pxy = __ffma2_rn(ouxy, P.sv_xy, pxy);
+        pz = fmaf(ouz, P.sv_z, pz);
+        const int vnext = voxel_index(P, pxy.x, pxy.y, pz);
         const uint32_t vox_next = vnext >= 0 ? __ldg(&P.vox[vnext]) : 0u;
         const uint4 xcur = x;
         x = philox(P, n + 1u, kTagStep | segtag, h);
         const unsigned long long q0 = qfix(P, E);
         float E1, s_c, sj;
         Phys ph;
-        const bool fired = sde_step_cont<CUT>(P, tab, m, rho, xcur, E, ux, uy, uz, tau, E1, s_c, ph, sj);
+        const bool fired = sde_step_cont<CUT>(P, tab, m, rho, xcur, E, uxy.x, uxy.y, uz, tau, E1, s_c, ph, sj);
         if (fired) {  // the event waits; the step's deposit does not depend on it
             jm = m;
             jE = E;
@@ -672,8 +673,8 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
         unsigned long long dq = q0 - q1;
         if (TALLY == 0) {
             // deposit at the step midpoint (Sec. 2.2.2)
-            int mv = voxel_index(P, fmaf(oux, P.half_step_mm, ox), fmaf(ouy, P.half_step_mm, oy),
-                                 fmaf(ouz, P.half_step_mm, oz));
+            const float2 mxy = __ffma2_rn(ouxy, P.hv_xy, oxy);
+            int mv = voxel_index(P, mxy.x, mxy.y, fmaf(ouz, P.hv_z, oz));
             if (mv < 0) {
                 if (dq) SDE_BLOCK_ADD(kCntEscaped, dq);
             } else if (AGG) {
@@ -690,8 +691,8 @@ __global__ void __launch_bounds__(256, SDE_MIN_BLOCKS) k_transport(const __grid_
                 atomicAdd(&P.edep[mv], dq);
             }
         } else if (dq) {
-            unsigned long long esc = deposit_chord(P, ox, oy, oz, oux * P.step_mm, ouy * P.step_mm,
-                                                   ouz * P.step_mm, dq);
+            const float2 dxy = __fmul2_rn(ouxy, P.sv_xy);
+            unsigned long long esc = deposit_chord(P, oxy.x, oxy.y, oz, dxy.x, dxy.y, ouz * P.sv_z, dq);
             if (esc) SDE_BLOCK_ADD(kCntEscaped, esc);
         }
         n += 1;
@@ -731,8 +732,9 @@ __global__ void k_sum_u64(const unsigned long long* __restrict__ v, size_t n, un
 __global__ void __launch_bounds__(1024) k_prep_spots(const sde_spot* raw, int n, SpotDev* out,
                                                      unsigned long long* prefix,
                                                      unsigned long long* counters, unsigned int* err,
-                                                     double ox, double oy, double oz, double e_min,
-                                                     double e_lim, unsigned long long h_begin) {
+                                                     double ox, double oy, double oz, double ihx, double ihy,
+                                                     double ihz, double e_min, double e_lim,
+                                                     unsigned long long h_begin) {
     __shared__ unsigned long long scan[1024];
     unsigned long long carry = 0;
     for (int base = 0; base < n; base += blockDim.x) {
@@ -756,18 +758,19 @@ __global__ void __launch_bounds__(1024) k_prep_spots(const sde_spot* raw, int n,
                 d.sE = (float)s.sigma_E_MeV;
                 d.sxy = (float)s.sigma_xy_mm;
                 d.sang = (float)s.sigma_angle_rad;
-                d.px = (float)(s.x_mm - ox);
-                d.py = (float)(s.y_mm - oy);
-                d.pz = (float)(s.z_mm - oz);
+                const double sx = s.sigma_xy_mm * ihx, sy = s.sigma_xy_mm * ihy, sz = s.sigma_xy_mm * ihz;
+                d.px = (float)((s.x_mm - ox) * ihx);
+                d.py = (float)((s.y_mm - oy) * ihy);
+                d.pz = (float)((s.z_mm - oz) * ihz);
                 d.ux = (float)x;
                 d.uy = (float)y;
                 d.uz = (float)z;
-                d.e1x = (float)(1.0 + sg * x * x * a);
-                d.e1y = (float)(sg * b);
-                d.e1z = (float)(-sg * x);
-                d.e2x = (float)b;
-                d.e2y = (float)(sg + y * y * a);
-                d.e2z = (float)(-y);
+                d.e1x = (float)((1.0 + sg * x * x * a) * sx);
+                d.e1y = (float)(sg * b * sy);
+                d.e1z = (float)(-sg * x * sz);
+                d.e2x = (float)(b * sx);
+                d.e2y = (float)((sg + y * y * a) * sy);
+                d.e2z = (float)(-y * sz);
             } else {
                 atomicOr(err, kErrBadSpot);
             }
@@ -939,10 +942,10 @@ cudaError_t launch_branch_chunk(unsigned long long* counters, unsigned long long
 }
 
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,
-                        unsigned long long* counters, unsigned int* err, const double o[3], double e_min,
-                        double e_lim, cudaStream_t st, unsigned long long h_begin) {
-    k_prep_spots<<<1, 1024, 0, st>>>(raw, n, out, prefix, counters, err, o[0], o[1], o[2], e_min, e_lim,
-                                     h_begin);
+                        unsigned long long* counters, unsigned int* err, const double o[3], const double h[3],
+                        double e_min, double e_lim, cudaStream_t st, unsigned long long h_begin) {
+    k_prep_spots<<<1, 1024, 0, st>>>(raw, n, out, prefix, counters, err, o[0], o[1], o[2], 1.0 / h[0], 1.0 / h[1],
+                                     1.0 / h[2], e_min, e_lim, h_begin);
     return cudaGetLastError();
 }
 

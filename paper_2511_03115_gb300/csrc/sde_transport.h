@@ -16,9 +16,11 @@ int transport_max_blocks_per_sm(int block, size_t smem, bool use_smem, int tally
                                 bool cut = false, int branch = 0);
 cudaError_t launch_branch_chunk(unsigned long long* counters, unsigned long long* sec_ctl,
                                 unsigned long long h_begin, cudaStream_t st);
+// Spot records -> device form (positions in voxel units of voxel size h) and the history
+// prefix; sets the work-queue cursor to h_begin.
 cudaError_t launch_prep(const sde_spot* raw, int n, SpotDev* out, unsigned long long* prefix,
-                        unsigned long long* counters, unsigned int* err, const double o[3], double e_min,
-                        double e_lim, cudaStream_t st, unsigned long long h_begin = 0);
+                        unsigned long long* counters, unsigned int* err, const double o[3], const double h[3],
+                        double e_min, double e_lim, cudaStream_t st, unsigned long long h_begin = 0);
 cudaError_t launch_probe(const KParams& P, int m, float rho, float E0, uint64_t h0, int n, float* Eo,
                          float* co, int* jo, float* uxo, float* uyo, cudaStream_t st);
 cudaError_t launch_sum_u64(const unsigned long long* v, size_t n, unsigned long long* out, int num_sms,

@@ -88,32 +88,55 @@ def test_conv3d_wgrad_at_full_width_matches_float64(sde_gpu, Cin, Cout):
     assert (dw.double() - ref).abs().max().item() <= 1e-4 * ref.abs().max().item()
 
 
-def _ref_network(layers, dose_low, rho, dose_high):
+def _bf16_round():
+    """Rounding to BF16 in the forward pass and of the gradient in the backward pass: the
+    library stores every activation and every activation gradient in BF16."""
+    import torch
+
+    class R(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x):
+            return x.to(torch.bfloat16).double()
+
+        @staticmethod
+        def backward(ctx, g):
+            return g.to(torch.bfloat16).double()
+
+    return R.apply
+
+
+def _ref_network(layers, dose_low, rho, dose_high, bf16=False):
     """The denoiser written with plain PyTorch CPU float64 operations (test reference):
-    same layers, skips, pooling, upsampling and input/output scaling as the library."""
+    same layers, skips, pooling, upsampling and input/output scaling as the library.  With
+    bf16=True the weights, the input channels, every stored activation and every stored
+    activation gradient are rounded to BF16 where the library rounds them (arithmetic in
+    float64 otherwise; the library accumulates in FP32)."""
     import torch
     import torch.nn.functional as F
+    rd = _bf16_round() if bf16 else (lambda t: t)
     D, H, W = dose_low.shape
     s = 1.0 / dose_low.abs().max()
     x = torch.zeros(1, 16, D, H, W, dtype=torch.float64)
     x[0, 0] = dose_low * s
     x[0, 1] = rho * 0.5
+    x = rd(x)
 
     def conv(t, i, relu=True):
         w, b = layers[i]
         co, _, ci = w.shape
-        y = F.conv3d(t, w.reshape(co, 3, 3, 3, ci).permute(0, 4, 1, 2, 3), b, padding=1)
-        return F.leaky_relu(y, 0.1) if relu else y
+        wq = rd(w) if bf16 else w
+        y = F.conv3d(t, wq.reshape(co, 3, 3, 3, ci).permute(0, 4, 1, 2, 3), b, padding=1)
+        return rd(F.leaky_relu(y, 0.1)) if relu else y
 
     e1a = conv(x, 0)
     e1 = conv(e1a, 1)
-    e2a = conv(F.avg_pool3d(e1, 2), 2)
+    e2a = conv(rd(F.avg_pool3d(e1, 2)), 2)
     e2 = conv(e2a, 3)
-    b1 = conv(F.avg_pool3d(e2, 2), 4)
+    b1 = conv(rd(F.avg_pool3d(e2, 2)), 4)
     b2 = conv(b1, 5)
-    d2a = conv(torch.cat([F.interpolate(b2, scale_factor=2, mode="nearest"), e2], 1), 6)
+    d2a = conv(torch.cat([rd(F.interpolate(b2, scale_factor=2, mode="nearest")), e2], 1), 6)
     d2 = conv(d2a, 7)
-    d1a = conv(torch.cat([F.interpolate(d2, scale_factor=2, mode="nearest"), e1], 1), 8)
+    d1a = conv(torch.cat([rd(F.interpolate(d2, scale_factor=2, mode="nearest")), e1], 1), 8)
     d1 = conv(d1a, 9)
     out = conv(d1, 10, relu=False)
     pred = dose_low * s + out[0, 0]
@@ -146,20 +169,33 @@ def test_denoiser_gradients_match_a_float64_reference(sde_gpu):
     net.set_params(p)
     low, rho, high = _smooth_case(shape, 1)
     g, loss = net.gradients(low.float().cuda(), rho.float().cuda(), high.float().cuda())
-    ref_layers = [(torch.tensor(w, dtype=torch.float64, requires_grad=True),
-                   torch.tensor(b, dtype=torch.float64, requires_grad=True)) for w, b in net.split(p)]
-    ref_loss, _ = _ref_network(ref_layers, low, rho, high)
-    (ref_loss * low.numel()).backward()  # the library differentiates the summed loss
-    assert abs(loss - ref_loss.item()) <= 0.03 * ref_loss.item()
-    for i, ((gw, gb), (rw, rb)) in enumerate(zip(net.split(g), ref_layers)):
-        for a_, r_ in ((gw, rw.grad.numpy()), (gb, rb.grad.numpy())):
+    def ref_grads(bf16):
+        ref_layers = [(torch.tensor(w, dtype=torch.float64, requires_grad=True),
+                       torch.tensor(b, dtype=torch.float64, requires_grad=True)) for w, b in net.split(p)]
+        ref_loss, _ = _ref_network(ref_layers, low, rho, high, bf16=bf16)
+        (ref_loss * low.numel()).backward()  # the library differentiates the summed loss
+        return ref_loss.item(), ref_layers
+
+    # float64 throughout: the gradients agree in direction, with BF16-storage noise
+    ref_loss, ref_layers = ref_grads(False)
+    assert abs(loss - ref_loss) <= 0.03 * ref_loss
+    # the same network with BF16 storage where the library stores BF16: per layer (weights
+    # and biases) the gradients agree to 2 % in the L2 norm
+    q_loss, q_layers = ref_grads(True)
+    assert abs(loss - q_loss) <= 0.005 * q_loss, (loss, q_loss)
+    rels = []
+    for i, ((gw, gb), (rw, rb), (qw, qb)) in enumerate(zip(net.split(g), ref_layers, q_layers)):
+        for a_, r_, q_ in ((gw, rw.grad.numpy(), qw.grad.numpy()), (gb, rb.grad.numpy(), qb.grad.numpy())):
             a_ = a_.astype(np.float64).ravel()
-            r_ = r_.ravel()
+            r_, q_ = r_.ravel(), q_.ravel()
             if np.linalg.norm(r_) == 0:
                 continue
             cos = a_ @ r_ / (np.linalg.norm(a_) * np.linalg.norm(r_))
-            rel = np.linalg.norm(a_ - r_) / np.linalg.norm(r_)
-            assert cos > 0.99 and rel < 0.15, (i, cos, rel)
+            assert cos > 0.99, (i, cos)
+            rel = np.linalg.norm(a_ - q_) / np.linalg.norm(q_)
+            rels.append((i, rel))
+            assert rel <= 2e-2, (i, rel)
+    print("per-layer relative gradient error vs the BF16-storage reference:", rels)
     net.close()
 
 
