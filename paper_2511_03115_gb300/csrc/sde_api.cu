@@ -56,6 +56,9 @@ struct sde_dose {
     double* d_csda = nullptr;
     float4* d_table = nullptr;
     float4* d_cut = nullptr;  // [n_mats][N][2] Coulomb coefficients of the variable cut-off
+    float2* d_pick = nullptr;  // [n_mats][N][2*SDE_MAX_ELEMENTS] cumulative rates for the event pick
+    float4* d_mott_g = nullptr;  // [N] hydrogen primitive at the ends of the sampled range
+    float2* d_mott_r = nullptr;  // [N][kMottKnots] hydrogen inversion ratios
     unsigned long long* d_counters = nullptr;
     unsigned int* d_err = nullptr;
     sde_spot* d_raw_spots = nullptr;
@@ -131,7 +134,8 @@ static void free_all(sde_dose* d) {
     void* ptrs[] = {d->d_rho,   d->d_vox,      d->d_edep,   d->d_mats,        d->d_mj,
                     d->d_raw,   d->d_jrates,   d->d_csda,   d->d_table,       d->d_counters,
                     d->d_err,   d->d_raw_spots, d->d_spots, d->d_prefix,      d->d_dose,
-                    d->d_cut,   d->d_secq,      d->d_secctl};
+                    d->d_cut,   d->d_secq,      d->d_secctl, d->d_pick,       d->d_mott_g,
+                    d->d_mott_r};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
@@ -229,6 +233,9 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     d->table_bytes = (size_t)n_mats * N * kRowFloat4 * sizeof(float4);
     TRY(cudaMalloc(&d->d_table, d->table_bytes));
     TRY(cudaMalloc(&d->d_cut, (size_t)n_mats * N * 2 * sizeof(float4)));
+    TRY(cudaMalloc(&d->d_pick, (size_t)n_mats * N * 2 * SDE_MAX_ELEMENTS * sizeof(float2)));
+    TRY(cudaMalloc(&d->d_mott_g, (size_t)N * sizeof(float4)));
+    TRY(cudaMalloc(&d->d_mott_r, (size_t)N * kMottKnots * sizeof(float2)));
     TRY(cudaMalloc(&d->d_counters, kCntWords * sizeof(unsigned long long)));
     TRY(cudaMalloc(&d->d_err, sizeof(unsigned int)));
     TRY(cudaMallocHost(&d->h_counters, (kCntWords + 1) * sizeof(unsigned long long)));
@@ -273,6 +280,9 @@ extern "C" int sde_dose_create(sde_dose** out, int nx, int ny, int nz, const dou
     tb.d_csda = d->d_csda;
     tb.d_table = d->d_table;
     tb.d_cut = d->d_cut;
+    tb.d_pick = d->d_pick;
+    tb.d_mott_g = d->d_mott_g;
+    tb.d_mott_r = d->d_mott_r;
     TRY(build_tables(tb, nullptr));
     TRY(cudaDeviceSynchronize());
 #undef TRY
@@ -377,6 +387,11 @@ static KParams make_kparams(const sde_dose* d, int n_spots, uint64_t seed) {
     P.table = d->d_table;
     P.jrates = d->d_jrates;
     P.cut = d->d_cut;
+    P.pick = d->d_pick;
+    P.mott_g = d->d_mott_g;
+    P.mott_r = d->d_mott_r;
+    P.mott_lg2_lo = (float)mott_knot_lo(d->p.theta_cut_rad);
+    P.mott_inv_dj = (float)((kMottKnots - 1) / -mott_knot_lo(d->p.theta_cut_rad));
     // theta_c^2 = k^2 sigma^2 = k^2 (z / Delta) t, t the step's Brownian time
     P.cut_k2 = d->p.theta_cut_sigmas > 0.0
                    ? (float)(d->p.theta_cut_sigmas * d->p.theta_cut_sigmas * d->p.msc_z_cm / d->p.step_cm)

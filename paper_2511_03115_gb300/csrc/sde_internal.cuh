@@ -49,6 +49,9 @@ static_assert(sizeof(SecRec) == 48, "secondary record is 48 bytes");
 // ln E; the kernel multiplies the factors back from E.
 constexpr int kRowFloat4 = 3;
 constexpr int kRawFields = 5;
+// Hydrogen (Mott) inversion table of the fixed cut-off: knots in log2 of the no-sine root s0
+// from log2(1 - cos theta_cut) to 0.
+constexpr int kMottKnots = 64;
 
 // Element data of a material as seen by the jump sampler.
 struct MatJump {
@@ -99,6 +102,11 @@ struct KParams {
     const float4* __restrict__ table;  // [n_mats][N][kRowFloat4]
     const float* __restrict__ jrates;  // [n_mats][N][2*SDE_MAX_ELEMENTS] per unit density
     const float4* __restrict__ cut;    // [n_mats][N][2] Coulomb coefficients (variable cut-off)
+    const float2* __restrict__ pick;   // [n_mats][N][2*SDE_MAX_ELEMENTS] cumulative rates {value, slope}:
+                                       // elastic (x E^2 Delta / rho), then non-elastic (Delta / rho)
+    const float4* __restrict__ mott_g;  // [N] {G(s_cut), slope, -G(s_back), slope} of the hydrogen primitive
+    const float2* __restrict__ mott_r;  // [N][kMottKnots] {rho_j, rho_j+1}: exact root / no-sine root
+    float mott_lg2_lo, mott_inv_dj;     // knot position = (log2 s0 - lo) * inv_dj
     float cut_k2;                      // k^2 z / Delta, or 0: fixed cut-off s_cut
     const MatJump* __restrict__ mats;
     const SpotDev* __restrict__ spots;

@@ -163,6 +163,9 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     auto* table = (float4*)carve(table_bytes);
     auto* raw = (float*)carve((size_t)n_mats * N * kRawFields * sizeof(float));
     auto* jrates = (float*)carve((size_t)n_mats * N * 2 * SDE_MAX_ELEMENTS * sizeof(float));
+    auto* pick = (float2*)carve((size_t)n_mats * N * 2 * SDE_MAX_ELEMENTS * sizeof(float2));
+    auto* mott_g = (float4*)carve((size_t)N * sizeof(float4));
+    auto* mott_r = (float2*)carve((size_t)N * kMottKnots * sizeof(float2));
     auto* csda = (double*)carve((size_t)n_mats * N * sizeof(double));
     auto* spots = (SpotDev*)carve((size_t)n_spots * sizeof(SpotDev));
     auto* prefix = (unsigned long long*)carve(((size_t)n_spots + 1) * sizeof(unsigned long long));
@@ -202,6 +205,9 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     tb.d_jrates = jrates;
     tb.d_csda = csda;
     tb.d_table = table;
+    tb.d_pick = pick;
+    tb.d_mott_g = mott_g;
+    tb.d_mott_r = mott_r;
     NA_TRY(build_tables(tb, st));
     NA_TRY(launch_prep(d_spots, n_spots, spots, prefix, counters, err, origin_mm, voxel_mm, p.e_min_MeV,
                        p.e_max_MeV, st));
@@ -259,6 +265,11 @@ extern "C" int sde_transport_noalloc(int nx, int ny, int nz, const double voxel_
     P.edep = d_edep;
     P.table = table;
     P.jrates = jrates;
+    P.pick = pick;
+    P.mott_g = mott_g;
+    P.mott_r = mott_r;
+    P.mott_lg2_lo = (float)mott_knot_lo(p.theta_cut_rad);
+    P.mott_inv_dj = (float)((kMottKnots - 1) / -mott_knot_lo(p.theta_cut_rad));
     P.mats = d_mj;
     P.spots = spots;
     P.prefix = prefix;

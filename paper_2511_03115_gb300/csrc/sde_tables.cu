@@ -129,6 +129,10 @@ struct TableArgs {
     double* csda;   // [n_mats][N]
     float4* table;  // [n_mats][N][kRowFloat4]
     float4* cut;    // [n_mats][N][2] or null
+    float2* pick;   // [n_mats][N][2*SDE_MAX_ELEMENTS] cumulative rates {value, slope} or null
+    float4* mott_g; // [N] or null
+    float2* mott_r; // [N][kMottKnots] or null
+    double mott_lg2_lo, mott_dj;
 };
 
 __device__ double stopping_per_rho(const MatHost& m, double K, double E) {
@@ -255,6 +259,82 @@ __global__ void k_build_hot(TableArgs a) {
     row[2] = make_float4((float)v0[4], (float)(v1[4] - v0[4]), (float)v0[5], (float)v0[6]);
 }
 
+// Rows for picking the channel and element of a large-angle event (fixed cut-off): at each
+// grid point the cumulative elastic rates sum_{j<=i} sigma_e,j E^2 Delta / rho over the
+// elements in order, then the cumulative non-elastic rates sum_{j<=i} sigma_ne,j Delta / rho,
+// each as {value at E_k, difference to E_k+1} for linear interpolation in ln E.  Interpolated
+// cumulative sums are the cumulative sums of interpolated rates, so the pick follows the
+// same rule as summing the rates one by one: the first channel whose cumulative rate
+// exceeds the uniform target.
+__global__ void k_build_pick(TableArgs a) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.N * a.n_mats) return;
+    int mi = idx / a.N, kk = idx % a.N;
+    double c0[2 * SDE_MAX_ELEMENTS], c1[2 * SDE_MAX_ELEMENTS];
+    for (int side = 0; side < 2; ++side) {
+        const int kq = kk + side < a.N ? kk + side : kk;
+        const double E = exp(a.lnEmin + kq * a.dlnE);
+        Point o;
+        physics_point(a, a.mats[mi], E, o);
+        double* c = side ? c1 : c0;
+        double ae = 0.0, an = 0.0;
+        for (int i = 0; i < SDE_MAX_ELEMENTS; ++i) {
+            ae += o.se[i] * E * E * a.step;
+            an += o.sne[i] * a.step;
+            c[i] = ae;
+            c[SDE_MAX_ELEMENTS + i] = an;
+        }
+    }
+    float2* row = a.pick + ((size_t)mi * a.N + kk) * (2 * SDE_MAX_ELEMENTS);
+    for (int i = 0; i < 2 * SDE_MAX_ELEMENTS; ++i) row[i] = make_float2((float)c0[i], (float)(c1[i] - c0[i]));
+}
+
+// Hydrogen (identical-particle Coulomb) inversion for the fixed cut-off.  In the forward
+// variable s = 1 - |mu| the primitive is G(s) = 2(1-s)/(s(2-s)) - sin(eta ln((2-s)/s))/(2 eta),
+// decreasing from +inf to 0 on (0, 1]; without the sine term it is G0(s), whose inverse
+// s0(y) is closed-form.  For each energy point and each knot s0_j (uniform in log2 from
+// 1 - cos theta_cut to 1) the table holds rho = s / s0_j with G(s) = G0(s0_j), found by
+// bisection in FP64; the kernel interpolates rho bilinearly and takes one Newton step.
+// mott_g holds the primitive at the two ends of the sampled range per energy point.
+__device__ double mott_G(double s, double eta) {
+    return 2.0 * (1.0 - s) / (s * (2.0 - s)) - sin(eta * log((2.0 - s) / s)) / (2.0 * eta);
+}
+
+__device__ double mott_eta(double E) { return kFineStructure / sqrt(2.0 * E / kProtonMass); }
+
+__global__ void k_build_mott(TableArgs a) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.N * kMottKnots) return;
+    const int kk = idx / kMottKnots, j = idx % kMottKnots;
+    const double eta = mott_eta(exp(a.lnEmin + kk * a.dlnE));
+    double rho[2];
+    for (int q = 0; q < 2; ++q) {
+        const int jj = j + q < kMottKnots ? j + q : j;
+        const double s0 = exp2(a.mott_lg2_lo + jj * a.mott_dj);
+        const double y = 2.0 * (1.0 - s0) / (s0 * (2.0 - s0));
+        double lo = log(1e-12), hi = 0.0;  // bisection in ln s
+        for (int it = 0; it < 80; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mott_G(exp(mid), eta) > y)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        rho[q] = exp(0.5 * (lo + hi)) / s0;
+    }
+    a.mott_r[(size_t)kk * kMottKnots + j] = make_float2((float)rho[0], (float)rho[1]);
+    if (j == 0) {
+        double g[2][2];
+        for (int q = 0; q < 2; ++q) {
+            const double e2 = mott_eta(exp(a.lnEmin + (kk + q < a.N ? kk + q : kk) * a.dlnE));
+            g[q][0] = mott_G(1.0 - a.cos_cut, e2);
+            g[q][1] = -mott_G(1.0 - a.cos_back, e2);
+        }
+        a.mott_g[kk] = make_float4((float)g[0][0], (float)(g[1][0] - g[0][0]), (float)g[0][1],
+                                   (float)(g[1][1] - g[0][1]));
+    }
+}
+
 // Coefficients of the large-angle elastic rate with a variable cut-off, per unit density,
 // times E^2 Delta (flat in E like fe): the Rutherford sum over elements other than
 // hydrogen, R = sum n_i 2 pi (eta_i/k_i)^2, multiplies 1/(1 - mu_c) - 1/2; hydrogen's
@@ -324,6 +404,8 @@ __global__ void k_csda(TableArgs a) {
     }
 }
 
+double mott_knot_lo(double theta_cut) { return log2(1.0 - cos(theta_cut)); }
+
 cudaError_t build_tables(const TableBuild& tb, cudaStream_t st) {
     TableArgs a;
     a.N = tb.N;
@@ -343,12 +425,19 @@ cudaError_t build_tables(const TableBuild& tb, cudaStream_t st) {
     a.csda = tb.d_csda;
     a.table = tb.d_table;
     a.cut = tb.d_cut;
+    a.pick = tb.d_pick;
+    a.mott_g = tb.d_mott_g;
+    a.mott_r = tb.d_mott_r;
+    a.mott_lg2_lo = mott_knot_lo(tb.theta_cut);
+    a.mott_dj = -a.mott_lg2_lo / (kMottKnots - 1);
     int total = tb.N * tb.n_mats;
     int threads = 128, blocks = (total + threads - 1) / threads;
     k_build_raw<<<blocks, threads, 0, st>>>(a);
     k_build_hot<<<blocks, threads, 0, st>>>(a);
     k_csda<<<tb.n_mats, 256, 0, st>>>(a);
     if (a.cut) k_build_cut<<<blocks, threads, 0, st>>>(a);
+    if (a.pick) k_build_pick<<<blocks, threads, 0, st>>>(a);
+    if (a.mott_g && a.mott_r) k_build_mott<<<(tb.N * kMottKnots + 127) / 128, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

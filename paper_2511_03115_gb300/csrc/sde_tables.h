@@ -31,9 +31,14 @@ struct TableBuild {
     double* d_csda;
     float4* d_table;
     float4* d_cut = nullptr;  // optional [n_mats][N][2]: Coulomb coefficients (variable cut-off)
+    float2* d_pick = nullptr;  // optional [n_mats][N][2*SDE_MAX_ELEMENTS]: cumulative rates for the event pick
+    float4* d_mott_g = nullptr;  // optional [N]: hydrogen primitive at the cut-off and backscatter limits
+    float2* d_mott_r = nullptr;  // optional [N][kMottKnots]: hydrogen inversion ratios (fixed cut-off)
 };
 
 cudaError_t build_tables(const TableBuild& tb, cudaStream_t st);
+// log2 of the first knot of the hydrogen inversion table: log2(1 - cos theta_cut).
+double mott_knot_lo(double theta_cut);
 
 // Message for sde_last_error() (defined with the C ABI).
 void set_last_error(const char* msg);

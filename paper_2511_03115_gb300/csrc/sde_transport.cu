@@ -121,6 +121,41 @@ __device__ void mott_sample(float U, float eta, float s_cut, float s_back, float
     sn = step_sqrt(s * (2.f - s));
 }
 
+// The same law with the fixed cut-off, from tables: the primitive at the two ends of the
+// range is interpolated in ln E, the root starts from the closed-form root s0 of the
+// primitive without its sine term times the tabulated ratio rho(E, log2 s0) (bilinear,
+// ~1e-4 relative), and one Newton step brings it to FP32 precision (the error squares).
+__device__ __forceinline__ void mott_sample_tab(const KParams& P, float U, float eta, int k, float f, float& c,
+                                                float& sn) {
+    const float4 gt = __ldg(&P.mott_g[k]);
+    const float g_hi = fmaf(gt.y, f, gt.x), g_lo = fmaf(gt.w, f, gt.z);
+    const float target = g_lo + U * (g_hi - g_lo);
+    const float sg = target >= 0.f ? 1.f : -1.f;
+    const float y = fabsf(target);
+    const float q = step_sqrt(1.f + y * y);
+    const float s0 = __fdividef(1.f + __fdividef(1.f, q + y), 1.f + q);
+    float jf = (__log2f(s0) - P.mott_lg2_lo) * P.mott_inv_dj;
+    jf = fminf(fmaxf(jf, 0.f), (float)(kMottKnots - 1));
+    const int j = min((int)jf, kMottKnots - 2);
+    const float fj = jf - (float)j;
+    const float2 r0 = __ldg(&P.mott_r[(uint32_t)(k * kMottKnots + j)]);
+    const float2 r1 = __ldg(&P.mott_r[(uint32_t)((k + 1) * kMottKnots + j)]);
+    const float ra = fmaf(r0.y - r0.x, fj, r0.x), rb = fmaf(r1.y - r1.x, fj, r1.x);
+    const float s_min = sg > 0.f ? P.s_cut : P.s_back;
+    float s = fminf(fmaxf(s0 * fmaf(rb - ra, f, ra), s_min), 1.f);
+    {  // one Newton step on G(s) = y
+        const float mu = 1.f - s, rom2 = __fdividef(1.f, s * (2.f - s));
+        const float L = __logf(__fdividef(2.f - s, s));
+        float sl, cl;
+        __sincosf(eta * L, &sl, &cl);
+        const float G = 2.f * mu * rom2 - sl * __fdividef(0.5f, eta);
+        const float dG = (2.f * (1.f + mu * mu) * rom2 - cl) * rom2;
+        s = fminf(fmaxf(s + __fdividef(G - y, dG), s_min), 1.f);
+    }
+    c = sg * (1.f - s);
+    sn = step_sqrt(s * (2.f - s));
+}
+
 // Kalbach-Mann angular law a/(2 sinh a) (cosh(a mu) + r sinh(a mu)): the CDF
 // is quadratic in T = exp(a mu); the stable root is taken on either sign of C.
 __device__ float kalbach_mu(float U, float a, float r) {
@@ -200,29 +235,56 @@ __device__ __forceinline__ JumpOut do_jump(const KParams& P, int m, float E, int
         float glo = -mott_prim(P.s_back, eta_h);
         scale_H *= (mott_prim(s_c, eta_h) - glo) / (mott_prim(P.s_cut, eta_h) - glo);
     }
-    float target = u01(J.x) * (sj * P.inv_delta_cm), acc = 0.f;
-    int pick = -1, last = -1;
-    for (int ch = 0; ch < 2 && pick < 0; ++ch)
-        for (int i = 0; i < mj.n_el; ++i) {
-            int o = ch * SDE_MAX_ELEMENTS + i;
-            float rate = fmaf(r1[o] - r0[o], f, r0[o]) * (ch == 0 ? (mj.Z[i] == 1 ? scale_H : scale_R) : 1.f);
-            if (rate <= 0.f) continue;
-            last = o;
-            acc += rate;
-            if (target < acc) {
-                pick = o;
-                break;
-            }
+    int pick = -1;
+    if (!CUT) {
+        // Cumulative rows (per unit density, x Delta): the first channel whose cumulative rate
+        // exceeds the target U sj.  Elastic rows are stored x E^2, so they are compared with
+        // the target x E^2; the non-elastic rows with what remains of it.
+        const float2* c = P.pick + (uint32_t)(m * P.N + k) * (uint32_t)(2 * SDE_MAX_ELEMENTS);
+        const int ne = mj.n_el;
+        const float t = u01(J.x) * sj;
+        const float tE = t * (E * E);
+        const float2 ce = c[ne - 1], cn = c[SDE_MAX_ELEMENTS + ne - 1];
+        const float etot = fmaf(ce.y, f, ce.x), ntot = fmaf(cn.y, f, cn.x);
+        if ((tE < etot && etot > 0.f) || !(ntot > 0.f)) {
+            if (!(etot > 0.f)) return o;  // no channel open (cannot happen when the clock fired)
+            int i = 0;
+            while (i < ne - 1 && fmaf(c[i].y, f, c[i].x) <= tE) ++i;
+            pick = i;
+        } else {
+            const float tn = fmaf(-etot, rE2, t);
+            int i = 0;
+            while (i < ne - 1 && fmaf(c[SDE_MAX_ELEMENTS + i].y, f, c[SDE_MAX_ELEMENTS + i].x) <= tn) ++i;
+            pick = SDE_MAX_ELEMENTS + i;
         }
-    if (pick < 0) pick = last;
-    if (pick < 0) return o;  // no channel open (cannot happen when the clock fired)
+    } else {
+        float target = u01(J.x) * (sj * P.inv_delta_cm), acc = 0.f;
+        int last = -1;
+        for (int ch = 0; ch < 2 && pick < 0; ++ch)
+            for (int i = 0; i < mj.n_el; ++i) {
+                int o = ch * SDE_MAX_ELEMENTS + i;
+                float rate = fmaf(r1[o] - r0[o], f, r0[o]) * (ch == 0 ? (mj.Z[i] == 1 ? scale_H : scale_R) : 1.f);
+                if (rate <= 0.f) continue;
+                last = o;
+                acc += rate;
+                if (target < acc) {
+                    pick = o;
+                    break;
+                }
+            }
+        if (pick < 0) pick = last;
+        if (pick < 0) return o;  // no channel open (cannot happen when the clock fired)
+    }
     int el = pick % SDE_MAX_ELEMENTS;
     bool elastic = pick < SDE_MAX_ELEMENTS;
     float m2 = mj.m2[el];
     float cc, sc, cl, sl;
     if (elastic) {
         if (mj.Z[el] == 1) {
-            mott_sample(u01(J.y), eta_h, CUT ? s_c : P.s_cut, P.s_back, cc, sc);
+            if (CUT)
+                mott_sample(u01(J.y), eta_h, s_c, P.s_back, cc, sc);
+            else
+                mott_sample_tab(P, u01(J.y), eta_h, k, f, cc, sc);
         } else {
             float span = CUT ? __fdividef(1.f, s_c) - 0.5f : P.ruth_span;
             float s = __fdividef(1.f, 0.5f + u01(J.y) * span);
