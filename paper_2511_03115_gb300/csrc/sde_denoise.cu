@@ -219,19 +219,26 @@ __device__ __forceinline__ bool pipe_wait(uint64_t* m, uint32_t parity, volatile
     return true;
 }
 
-// AND of a predicate over the 128 worker threads (warps 0-3), named barrier 1.
+// Worker warps of the brick convolution (loads and epilogue); the MMA warp follows them.
+// Two workers share each tensor-memory lane quarter (warp & 3) in the epilogue.
+constexpr int kConvWorkers = 8;
+constexpr int kConvWorkerThreads = 32 * kConvWorkers;
+
+// AND of a predicate over the NT worker threads of a kernel (its warps 0 .. NT/32 - 1),
+// named barrier 1.
+template <int NT>
 __device__ __forceinline__ bool workers_all(bool v) {
     uint32_t r;
     asm volatile(
-        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, 1, 128, pi;\n\t"
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, 1, %2, pi;\n\t"
         "selp.u32 %0, 1, 0, po;\n\t}\n"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(NT)
         : "memory");
     return r != 0;
 }
 
-__global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b) {
+__global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(ConvArgs a, BrickPlan b) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Cin = a.Cin, Cp = b.Cp, W = a.W, H = a.H, D = a.D;
@@ -250,14 +257,14 @@ __global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b
     }
     if (tid == 0) {
         for (int s = 0; s < kPipeStages; ++s) {
-            umma::mbar_init(&full[s], 128);
+            umma::mbar_init(&full[s], kConvWorkerThreads);
             umma::mbar_init(&empty[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             umma::mbar_init(&tfull[s], 1);
-            umma::mbar_init(&tempty[s], 128);
+            umma::mbar_init(&tempty[s], kConvWorkerThreads);
         }
-        umma::mbar_init(wfull, 128);
+        umma::mbar_init(wfull, kConvWorkerThreads);
         *abort_flag = 0;
     }
     umma::fence_before_sync();
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b
     const int fA = (Yb + 1) * P;  // brick position of output (y0, x = -1): row 0 of M tile 0
     const int acc_cols = b.tiles * Cp;
 
-    if (warp == 4) {
+    if (warp == kConvWorkers) {
         if (lane == 0) {
             const uint32_t idesc = umma::idesc_bf16_f32(128, Cp);
             int k = 0;
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b
         auto worker_wait = [&](uint64_t* m, uint32_t parity) {
             bool done = true;
             if (tid == 0) done = pipe_wait(m, parity, abort_flag);
-            return workers_all(done);
+            return workers_all<kConvWorkerThreads>(done);
         };
         auto epilogue = [&](int pj, int pitem) {
             const int acc = pj % b.nacc, v = pj / b.nacc;
@@ -346,9 +353,11 @@ __global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b
             const int part = r % b.nsplit;
             const int n = r / b.nsplit;
             const int cbase = part * Cp;
-            const uint32_t trow = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(acc * acc_cols);
-            for (int m = 0; m < b.tiles; ++m) {
-                const int q = fA + 128 * m + 32 * warp + lane - Yb * P;  // position in plane zb = 1
+            // warp w reads lane quarter w & 3; the two warps of a quarter take alternate tiles
+            const int quarter = warp & 3;
+            const uint32_t trow = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * acc_cols);
+            for (int m = warp >> 2; m < b.tiles; m += kConvWorkers / 4) {
+                const int q = fA + 128 * m + 32 * quarter + lane - Yb * P;  // position in plane zb = 1
                 const int yb = q / P, xp = q - (q / P) * P;
                 const int yy = y0 + yb - 1, xx = xp - 1;
                 const bool valid = yb >= 1 && yb <= b.Ty && xp >= 1 && xp <= W && yy < H;
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b
                     const int co = q >> 1, g = q & 1;
                     umma::cp_async16(s_wres + (uint32_t)((c * 27 + tap) * Cp * 32) + umma::core_offset(co, g * 8, 16),
                                      a.w + ((size_t)co * 27 + tap) * Cin + c * 16 + g * 8, 16u);
-                    q += 128;
+                    q += kConvWorkerThreads;
                     while (q >= 2 * Cp) {
                         q -= 2 * Cp;
                         ++tap;
@@ -437,8 +446,8 @@ __global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b
                                 (unsigned)zz < (unsigned)D && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
                             const __nv_bfloat16* src = in ? src_c + ((size_t)(zz * H + yy) * W + xx) * Cin : src_c;
                             umma::cp_async16(dst + (uint32_t)f * 16u, src, in ? 16u : 0u);
-                            f += 64;
-                            xp += 64;
+                            f += kConvWorkerThreads / 2;
+                            xp += kConvWorkerThreads / 2;
                             while (xp >= P) {
                                 xp -= P;
                                 if (++yb == Yb) {
@@ -459,7 +468,7 @@ __global__ void __launch_bounds__(160, 1) k_conv3d_brick(ConvArgs a, BrickPlan b
                             const int co = q >> 1, g = q & 1;
                             umma::cp_async16(s_w + (uint32_t)(tap * Cp * 32) + umma::core_offset(co, g * 8, 16),
                                              win + ((size_t)co * 27 + tap) * Cin + c * 16 + g * 8, 16u);
-                            q += 128;
+                            q += kConvWorkerThreads;
                             while (q >= 2 * Cp) {
                                 q -= 2 * Cp;
                                 ++tap;
@@ -574,7 +583,7 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
         auto worker_wait = [&](uint64_t* m, uint32_t parity) {
             bool done = true;
             if (tid == 0) done = pipe_wait(m, parity, abort_flag);
-            return workers_all(done);
+            return workers_all<128>(done);
         };
         for (int j = 0; j < my_items && ok; ++j) {
             const int s = j % kPipeStages, u = j / kPipeStages;
@@ -715,7 +724,7 @@ cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int ctas = bp.items < sms ? bp.items : sms;
-    k_conv3d_brick<<<ctas, 160, bsmem, st>>>(a, bp);
+    k_conv3d_brick<<<ctas, kConvWorkerThreads + 32, bsmem, st>>>(a, bp);
     return cudaGetLastError();
 }
 
