@@ -278,23 +278,32 @@ int sde_dose_probe_steps(sde_dose* d, int m, double rho, double E, uint64_t seed
  * multiple of 16.  stream: cudaStream_t or NULL. */
 int sde_gemm_bf16(const void* d_A, const void* d_B, float* d_D, int M, int N, int K, void* stream);
 
-/* 3x3x3 convolution, stride 1, zero padding 1, channels-last BF16:
+/* Activation layout of the convolutions, "padded channel-group-major" BF16: a tensor of
+ * C channels (C a multiple of 8) on a D x H x W grid is [batch][C/8][D+2][H+2][W+2][8],
+ * channel 8 g + e of voxel (z, y, x) at ((((n C/8 + g)(D+2) + z+1)(H+2) + y+1)(W+2) + x+1) 8 + e.
+ * The one-voxel border holds zeros (the convolution's zero padding): the caller zeroes
+ * it once and these calls never write it.
+ *
+ * 3x3x3 convolution, stride 1, zero padding 1:
  * y[n][v][y_coffset + co] = (relu?) (bias[co] + sum_{tap,ci} x[n][v + off(tap)][ci] w[co][tap][ci]),
- * v = (z*H + y)*W + x, tap = 9 kz + 3 ky + kx, off = (kz-1, ky-1, kx-1).  d_x [batch][D*H*W][Cin],
- * d_w [Cout][27][Cin] BF16, d_bias [Cout] FP32 or NULL; y rows have y_cstride channels
- * (BF16, or FP32 when y_fp32 != 0), written at channel offset y_coffset (so two
- * producers can fill the halves of a concatenation).  Requires W <= 256, D*H*W a
- * multiple of 128, Cin a multiple of 16 in [16, 192], Cout a multiple of 16 in
- * [16, 256] (SDE_EINVAL otherwise).  The data gradient of the convolution is this call
- * on dy with the weights of sde_conv3d_flip_weights.  Asynchronous;
- * sde_denoise_status reports a timed-out wait. */
+ * tap = 9 kz + 3 ky + kx, off = (kz-1, ky-1, kx-1).  d_x padded channel-group-major with Cin
+ * channels; d_w [Cout][27][Cin] BF16 (the call packs it for the tensor core in
+ * stream-ordered scratch memory); d_bias [Cout] FP32 or NULL.  The output has y_cstride
+ * channels written from channel y_coffset on (so two producers can fill the parts of a
+ * concatenation): padded channel-group-major BF16, or with y_fp32 != 0 plain
+ * channels-last FP32 [batch][D*H*W][y_cstride].  Requires W <= 256, Cin a multiple of
+ * 16 in [16, 192], Cout a multiple of 16 in [16, 256], 16-byte aligned d_x and d_y
+ * (SDE_EINVAL otherwise).  The data gradient of the convolution is this call on dy with
+ * the weights of sde_conv3d_flip_weights.  Asynchronous; sde_denoise_status reports a
+ * timed-out wait. */
 int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int W, int Cin, const void* d_w,
                        const float* d_bias, int Cout, void* d_y, int y_cstride, int y_coffset, int y_fp32,
                        int relu, void* stream);
 
 /* Weight gradient of sde_conv3d_forward: d_dw[co][tap][ci] += sum over voxels of
- * dy[v][co] x[v + off(tap)][ci] (FP32 accumulation into d_dw; BF16 d_x, d_dy; Cout <= 128;
- * shape limits as sde_conv3d_forward).  Asynchronous. */
+ * dy[v][co] x[v + off(tap)][ci] (FP32 accumulation into d_dw; d_x and d_dy padded
+ * channel-group-major BF16 with Cin and Cout channels; Cout <= 128; shape limits as
+ * sde_conv3d_forward).  Asynchronous. */
 int sde_conv3d_wgrad(const void* d_x, const void* d_dy, float* d_dw, int batch, int D, int H, int W, int Cin,
                      int Cout, void* stream);
 

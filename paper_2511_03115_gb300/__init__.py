@@ -384,22 +384,54 @@ def _sp(stream):
     return None if stream is None else C.c_void_p(stream.cuda_stream)
 
 
-def conv3d(x, w, bias=None, relu=False, y=None, y_coffset=0, fp32=False, stream=None):
-    """3x3x3 convolution: x [n, D, H, W, Cin] bf16, w [Cout, 27, Cin] bf16 -> y [n, D, H, W, C]."""
+def pcg_zeros(n, C, D, H, W, device="cuda"):
+    """A zeroed BF16 tensor in the convolutions' padded channel-group-major layout:
+    [n, C/8, D+2, H+2, W+2, 8] (see include/sde_dose.h)."""
     import torch
-    n, D, H, W, Cin = x.shape
+    return torch.zeros(n, C // 8, D + 2, H + 2, W + 2, 8, dtype=torch.bfloat16, device=device)
+
+
+def to_pcg(x):
+    """Channels-last [n, D, H, W, C] -> padded channel-group-major [n, C/8, D+2, H+2, W+2, 8]."""
+    n, D, H, W, Cc = x.shape
+    y = pcg_zeros(n, Cc, D, H, W, device=x.device)
+    y[:, :, 1:-1, 1:-1, 1:-1, :] = x.to(y.dtype).reshape(n, D, H, W, Cc // 8, 8).permute(0, 4, 1, 2, 3, 5)
+    return y
+
+
+def from_pcg(y):
+    """Padded channel-group-major [n, G, D+2, H+2, W+2, 8] -> channels-last [n, D, H, W, 8 G]."""
+    n, G, Dp, Hp, Wp, _ = y.shape
+    return y[:, :, 1:-1, 1:-1, 1:-1, :].permute(0, 2, 3, 4, 1, 5).reshape(n, Dp - 2, Hp - 2, Wp - 2, 8 * G)
+
+
+def _pcg_shape(x):
+    n, G, Dp, Hp, Wp, e = x.shape
+    if e != 8:
+        raise ValueError("expected a padded channel-group-major tensor [n, C/8, D+2, H+2, W+2, 8]")
+    return n, Dp - 2, Hp - 2, Wp - 2, 8 * G
+
+
+def conv3d(x, w, bias=None, relu=False, y=None, y_coffset=0, fp32=False, stream=None):
+    """3x3x3 convolution: x padded channel-group-major with Cin channels, w [Cout, 27, Cin]
+    bf16 -> y padded channel-group-major bf16, or with fp32 channels-last [n, D, H, W, C]."""
+    import torch
+    n, D, H, W, Cin = _pcg_shape(x)
     Cout = w.shape[0]
     if y is None:
-        y = torch.empty(n, D, H, W, Cout, dtype=torch.float32 if fp32 else torch.bfloat16, device=x.device)
+        y = (torch.empty(n, D, H, W, Cout, dtype=torch.float32, device=x.device) if fp32
+             else pcg_zeros(n, Cout, D, H, W, device=x.device))
+    cstride = y.shape[-1] if fp32 else 8 * y.shape[1]
     _check(lib().sde_conv3d_forward(x.data_ptr(), n, D, H, W, Cin, w.data_ptr(),
                                     None if bias is None else bias.data_ptr(), Cout, y.data_ptr(),
-                                    y.shape[-1], y_coffset, int(fp32), int(relu), _sp(stream)))
+                                    cstride, y_coffset, int(fp32), int(relu), _sp(stream)))
     return y
 
 
 def conv3d_wgrad(x, dy, dw, stream=None):
-    n, D, H, W, Cin = x.shape
-    _check(lib().sde_conv3d_wgrad(x.data_ptr(), dy.data_ptr(), dw.data_ptr(), n, D, H, W, Cin, dy.shape[-1],
+    """dw [Cout, 27, Cin] fp32 += weight gradient; x, dy padded channel-group-major."""
+    n, D, H, W, Cin = _pcg_shape(x)
+    _check(lib().sde_conv3d_wgrad(x.data_ptr(), dy.data_ptr(), dw.data_ptr(), n, D, H, W, Cin, 8 * dy.shape[1],
                                   _sp(stream)))
     return dw
 

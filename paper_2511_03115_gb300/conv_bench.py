@@ -3,7 +3,8 @@
 ``python -m paper_2511_03115_gb300.conv_bench`` times the forward convolution (and the
 weight gradient) of every layer shape of the 128 x 128 x 192 denoiser on random BF16
 data, then a full inference and a training step, and prints one line per layer with
-the achieved TFLOP/s (2 x voxels x 27 x Cin x Cout per forward).  ``--shape D H W Cin
+the achieved TFLOP/s (2 x voxels x 27 x Cin x Cout per forward; each call also packs its
+weights for the tensor core, which the network does once per weight update).  ``--shape D H W Cin
 Cout`` runs only that convolution ``--reps`` times (a small case for a profiler), or with
 ``--wgrad`` its weight gradient.
 """
@@ -37,12 +38,13 @@ def _time(fn, reps, stream):
 
 
 def _tensors(D, H, W, ci, co, seed=0):
+    """Random input and weights, zeroed output; activations padded channel-group-major."""
     import torch
     g = torch.Generator(device="cuda").manual_seed(seed)
-    x = (0.5 * torch.randn(1, D, H, W, ci, device="cuda", generator=g)).to(torch.bfloat16)
+    x = S.to_pcg((0.5 * torch.randn(1, D, H, W, ci, device="cuda", generator=g)).to(torch.bfloat16))
     w = (0.05 * torch.randn(co, 27, ci, device="cuda", generator=g)).to(torch.bfloat16)
     b = torch.zeros(co, device="cuda")
-    y = torch.empty(1, D, H, W, co, device="cuda", dtype=torch.bfloat16)
+    y = S.pcg_zeros(1, co, D, H, W)
     return x, w, b, y
 
 
@@ -60,7 +62,7 @@ def main():
         x, w, b, y = _tensors(D, H, W, ci, co)
         if args.wgrad:
             dw = torch.zeros(co, 27, ci, device="cuda")
-            dy = (0.5 * torch.randn(1, D, H, W, co, device="cuda")).to(torch.bfloat16)
+            dy = S.to_pcg((0.5 * torch.randn(1, D, H, W, co, device="cuda")).to(torch.bfloat16))
         for _ in range(args.reps):
             if args.wgrad:
                 S.conv3d_wgrad(x, dy, dw)
@@ -79,7 +81,7 @@ def main():
         row = {"shape": [D, H, W, ci, co], "fwd_ms": ms, "fwd_tflops": flop / ms / 1e9}
         if co <= 128:
             dw = torch.zeros(co, 27, ci, device="cuda")
-            dy = torch.randn(1, D, H, W, co, device="cuda").to(torch.bfloat16)
+            dy = S.to_pcg(torch.randn(1, D, H, W, co, device="cuda").to(torch.bfloat16))
             ms_w = _time(lambda: S.conv3d_wgrad(x, dy, dw), max(1, args.reps // 3), st)
             S.denoise_status()
             row.update({"wgrad_ms": ms_w, "wgrad_tflops": flop / ms_w / 1e9})

@@ -191,18 +191,24 @@ namespace {
 // planes z-1..z+1, rows y0-1..y0+Ty, columns -1..W -- is staged in shared memory once,
 // as two 8-channel planes in which brick position f = (zb Yb + yb) P + xp (P = W + 2,
 // Yb = Ty + 2) holds 16 bytes.  In that layout 8 consecutive positions form a K-major
-// core matrix, so the A operand of tap (dz, dy, dx) for the M tile starting at brick
+// core matrix, so the A operand of tap (dz, dy, dx) for an M tile starting at brick
 // position f0 is the same buffer read from f0 + (dz Yb + dy) P + dx: the 27 taps are 27
-// descriptor offsets, not 27 copies.  M tiles of 128 rows cover the positions of the Ty
-// output rows including their two padding columns; the epilogue drops the rows that are
-// not output voxels.
+// descriptor offsets, not 27 copies.  The input is padded channel-group-major, so each
+// (channel group, plane) part of the brick is one contiguous run of Yb P x 16 bytes in
+// global memory and a chunk arrives in six bulk copies.  When W is a multiple of 128 an M
+// tile is 128 consecutive x of one output row and no padding column is computed;
+// otherwise M tiles of 128 consecutive positions cover the Ty rows including their
+// padding columns and the epilogue drops the rows that are not output voxels.
 //
-// Persistent and warp-specialised: warps 0-3 stream (brick, weight) chunks into a ring of
-// shared-memory stages with cp.async (each stage's "full" barrier completes when the
-// copies land) and run the epilogue of the previous item while the tensor core works on
-// the current one; one thread of warp 4 issues the MMAs into one of two tensor-memory
-// accumulators and releases stages and accumulators through tcgen05.commit.  Every wait
-// is bounded; a timeout sets a shared abort flag that ends all roles' loops.
+// Persistent and warp-specialised: one thread of the producer warp streams (brick,
+// weight) chunks into a ring of shared-memory stages (each stage's "full" barrier
+// completes when the bytes of its copies have landed); one thread of the MMA warp issues
+// tcgen05.mma into one of two tensor-memory accumulators and releases stages and
+// accumulators through tcgen05.commit; the kConvWorkers epilogue warps turn a finished
+// accumulator into output (bias, leaky ReLU, BF16 or FP32 store) while the tensor core
+// works on the next item.  Every wait is bounded; a timeout sets a shared abort flag that
+// ends all roles' loops, and the producer waits for its copies in flight before the CTA
+// exits.
 // ----------------------------------------------------------------------------
 constexpr int kPipeStages = 2;
 constexpr int kPipeHeader = 1024;  // barriers, tensor-memory slot, abort flag
@@ -219,10 +225,11 @@ __device__ __forceinline__ bool pipe_wait(uint64_t* m, uint32_t parity, volatile
     return true;
 }
 
-// Worker warps of the brick convolution (loads and epilogue); the MMA warp follows them.
-// Two workers share each tensor-memory lane quarter (warp & 3) in the epilogue.
+// Epilogue warps of the brick convolution; two share each tensor-memory lane quarter
+// (warp & 3).  The MMA warp and the producer warp follow them.
 constexpr int kConvWorkers = 8;
 constexpr int kConvWorkerThreads = 32 * kConvWorkers;
+constexpr int kConvThreads = kConvWorkerThreads + 64;
 
 // AND of a predicate over the NT worker threads of a kernel (its warps 0 .. NT/32 - 1),
 // named barrier 1.
@@ -238,7 +245,51 @@ __device__ __forceinline__ bool workers_all(bool v) {
     return r != 0;
 }
 
-__global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(ConvArgs a, BrickPlan b) {
+// Brick position of output row 0's first M-tile row, shifted to tile m (tap offsets are
+// added to it): row tiles are 128 x of one output row, flat tiles 128 consecutive positions
+// starting at output (y0, x = -1).
+__device__ __forceinline__ int tile_base(int m, bool rowtile, int P, int Yb, int tpr) {
+    return rowtile ? (Yb + 1) * P + 1 + (m / tpr) * P + (m % tpr) * 128 : (Yb + 1) * P + 128 * m;
+}
+
+// The 27 x TILES MMAs of one channel chunk, fully unrolled so that the issuing thread spends
+// one integer add per instruction: A's start field is the stage's plus (tile base + tap
+// offset), B's steps by one tap tile (Cp x 16 BF16 = 2 Cp units of 16 bytes).  The start
+// fields stay within 14 bits (shared addresses below 256 KB, lowest start one position
+// into the stage), so adding to the low word never carries or borrows into the others.
+template <int TILES>
+__device__ __forceinline__ void conv_chunk_mma(uint32_t dacc, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
+                                               uint32_t b_hi, uint32_t idesc, int Cp, const int (&toff)[27],
+                                               bool rowtile, int P, int Yb, int tpr, uint32_t first_accum) {
+    int tb[TILES];
+#pragma unroll
+    for (int m = 0; m < TILES; ++m) tb[m] = tile_base(m, rowtile, P, Yb, tpr);
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        const uint32_t bl = b_lo + (uint32_t)(2 * Cp * t);
+#pragma unroll
+        for (int m = 0; m < TILES; ++m)
+            umma::mma_bf16_lohi(dacc + (uint32_t)(m * Cp), a_lo + (uint32_t)(tb[m] + toff[t]), a_hi, bl, b_hi, idesc,
+                                t > 0 ? 1u : first_accum);
+    }
+}
+
+// Work item of the brick convolution: (sample, Cout part, row block, z plane).
+struct BrickItem {
+    int n, part, y0, z;
+};
+__device__ __forceinline__ BrickItem brick_item(const BrickPlan& b, int D, int item) {
+    BrickItem t;
+    t.z = item % D;
+    item /= D;
+    t.y0 = (item % b.nyb) * b.Ty;
+    item /= b.nyb;
+    t.part = item % b.nsplit;
+    t.n = item / b.nsplit;
+    return t;
+}
+
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, BrickPlan b) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Cin = a.Cin, Cp = b.Cp, W = a.W, H = a.H, D = a.D;
@@ -257,14 +308,14 @@ __global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(Con
     }
     if (tid == 0) {
         for (int s = 0; s < kPipeStages; ++s) {
-            umma::mbar_init(&full[s], kConvWorkerThreads);
+            umma::mbar_init(&full[s], 1);
             umma::mbar_init(&empty[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             umma::mbar_init(&tfull[s], 1);
             umma::mbar_init(&tempty[s], kConvWorkerThreads);
         }
-        umma::mbar_init(wfull, kConvWorkerThreads);
+        umma::mbar_init(wfull, 1);
         *abort_flag = 0;
     }
     umma::fence_before_sync();
@@ -272,16 +323,57 @@ __global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(Con
     umma::fence_after_sync();
     const uint32_t tbase = *slot;
     const int nchunk = Cin >> 4;
-    const int npos = 3 * Yb * P;
-    const int fA = (Yb + 1) * P;  // brick position of output (y0, x = -1): row 0 of M tile 0
     const int acc_cols = b.tiles * Cp;
+    const int tpr = W >> 7;                          // row tiles: M tiles per output row
+    const uint32_t w_chunk = (uint32_t)(27 * Cp * 32);  // bytes of one chunk's weights
+    const uint32_t s_wres = s_stage0 + (uint32_t)(kPipeStages * b.stage);
+    const Pcg pg{D, H, W};
 
-    if (warp == kConvWorkers) {
+    if (warp == kConvWorkers + 1) {
+        if (lane == 0) {  // producer
+            const int Gin = Cin >> 3;
+            const uint32_t run = (uint32_t)(Yb * P * 16);  // one (channel group, plane) part of a brick
+            int k = 0;
+            if (b.wres) {
+                umma::mbar_arrive_expect_tx(wfull, (uint32_t)nchunk * w_chunk);
+                umma::bulk_g2s(s_wres, a.wpk, (uint32_t)nchunk * w_chunk, wfull);
+            }
+            bool ok = true;
+            for (int item = blockIdx.x; ok && item < b.items; item += gridDim.x) {
+                const BrickItem t = brick_item(b, D, item);
+                const __nv_bfloat16* wpart = a.wpk + (size_t)t.part * nchunk * 27 * Cp * 16;
+                for (int c = 0; c < nchunk; ++c, ++k) {
+                    const int s = k % kPipeStages, u = k / kPipeStages;
+                    if (u >= 1 && !pipe_wait(&empty[s], (uint32_t)(u - 1) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
+                    umma::mbar_arrive_expect_tx(&full[s], 6u * run + (b.wres ? 0u : w_chunk));
+                    for (int gg = 0; gg < 2; ++gg)
+                        for (int zb = 0; zb < 3; ++zb)  // rows y0-1 .. y0+Ty of plane z+zb-1, columns -1 .. W
+                            umma::bulk_g2s(st + 128u + (uint32_t)(gg * b.plane) + (uint32_t)zb * run,
+                                           a.x + 8 * pg.unit(t.n, Gin, 2 * c + gg, t.z + zb - 1, t.y0 - 1, -1), run,
+                                           &full[s]);
+                    if (!b.wres)
+                        umma::bulk_g2s(st + (uint32_t)b.w_off, wpart + (size_t)c * 27 * Cp * 16, w_chunk, &full[s]);
+                }
+            }
+            // no copy may still be writing shared memory when the CTA exits: wait for the
+            // last kPipeStages chunks (earlier ones were consumed before their stage was reused)
+            for (int kk = k > kPipeStages ? k - kPipeStages : 0; kk < k; ++kk)
+                umma::mbar_wait(&full[kk % kPipeStages], (uint32_t)(kk / kPipeStages) & 1u, kWaitCycles);
+            if (b.wres) umma::mbar_wait(wfull, 0u, kWaitCycles);
+        }
+        __syncwarp();
+    } else if (warp == kConvWorkers) {
         if (lane == 0) {
             const uint32_t idesc = umma::idesc_bf16_f32(128, Cp);
+            int toff[27];  // tap (dz, dy, dx) -> brick position offset (dz Yb + dy) P + dx
+#pragma unroll
+            for (int t = 0; t < 27; ++t) toff[t] = ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P + (t % 3 - 1);
             int k = 0;
             bool ok = !b.wres || pipe_wait(wfull, 0u, abort_flag);
-            const uint32_t s_wres = s_stage0 + (uint32_t)(kPipeStages * b.stage);
             for (int item = blockIdx.x, j = 0; ok && item < b.items; item += gridDim.x, ++j) {
                 const int acc = j % b.nacc, v = j / b.nacc;
                 if (v >= 1 && !pipe_wait(&tempty[acc], (uint32_t)(v - 1) & 1u, abort_flag)) break;
@@ -294,31 +386,38 @@ __global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(Con
                         break;
                     }
                     umma::fence_after_sync();
-                    umma::fence_async_smem();  // cp.async (generic proxy) data -> tensor core
                     const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
-                    // Only the start-address field (16-byte units, low bits) differs between
-                    // the descriptors of one stage, so they are the base descriptors plus a
-                    // position index (A) or a tap offset (B).  Shared addresses stay below
-                    // 256 KB, so the field never carries into the next one.
                     const uint64_t a0 = umma::smem_desc(st + 128u, (uint32_t)b.plane, 128);
-                    uint64_t bd = umma::smem_desc(
-                        b.wres ? s_wres + (uint32_t)(c * 27 * Cp * 32) : st + (uint32_t)b.w_off, 128, 256);
-                    uint32_t accum = c > 0 ? 1u : 0u;
-                    for (int dz = -1; dz <= 1; ++dz)
-                        for (int dy = -1; dy <= 1; ++dy)
-                            for (int dx = -1; dx <= 1; ++dx) {
-                                // fA + tap offset >= -1: the lowest start is one position before
-                                // the plane (a padding row whose result is dropped), inside the stage
-                                uint64_t ad = a0 + (uint64_t)(int64_t)(fA + (dz * Yb + dy) * P + dx);
-                                uint32_t dcol = dacc;
-                                for (int m = 0; m < b.tiles; ++m) {
-                                    umma::mma_bf16(dcol, ad, bd, idesc, accum);
-                                    ad += 128;  // next 128 positions
-                                    dcol += (uint32_t)Cp;
-                                }
-                                accum = 1u;
-                                bd += (uint64_t)(2 * Cp);  // next tap: Cp x 16 BF16 = 2 Cp units
-                            }
+                    const uint64_t b0 = umma::smem_desc(
+                        b.wres ? s_wres + (uint32_t)c * w_chunk : st + (uint32_t)b.w_off, 128, 256);
+                    const uint32_t a_lo = (uint32_t)a0, a_hi = (uint32_t)(a0 >> 32);
+                    const uint32_t b_lo = (uint32_t)b0, b_hi = (uint32_t)(b0 >> 32);
+                    const uint32_t first = c > 0 ? 1u : 0u;
+                    const bool rt = b.rowtile != 0;
+                    switch (b.tiles) {
+#define SDE_CONV_TILES(T)                                                                          \
+    case T:                                                                                        \
+        conv_chunk_mma<T>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, rt, P, Yb, tpr, first); \
+        break;
+                        SDE_CONV_TILES(1)
+                        SDE_CONV_TILES(2)
+                        SDE_CONV_TILES(3)
+                        SDE_CONV_TILES(4)
+                        SDE_CONV_TILES(5)
+                        SDE_CONV_TILES(6)
+                        SDE_CONV_TILES(7)
+                        SDE_CONV_TILES(8)
+#undef SDE_CONV_TILES
+                        default:
+                            for (int t = 0; t < 27; ++t)
+                                for (int m = 0; m < b.tiles; ++m)
+                                    umma::mma_bf16_lohi(dacc + (uint32_t)(m * Cp),
+                                                        a_lo + (uint32_t)(tile_base(m, rt, P, Yb, tpr) +
+                                                                          ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P +
+                                                                          (t % 3 - 1)),
+                                                        a_hi, b_lo + (uint32_t)(2 * Cp * t), b_hi, idesc,
+                                                        t > 0 ? 1u : first);
+                    }
                     umma::mma_commit(&empty[s]);
                 }
                 if (ok) umma::mma_commit(&tfull[acc]);
@@ -326,42 +425,39 @@ __global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(Con
         }
         __syncwarp();
     } else {
-        // workers: loads of item j, then the epilogue of item j - 1.  With one accumulator
-        // the MMAs of item j wait for that epilogue, so it runs once the first
-        // kPipeStages chunks of item j (which need no MMA of item j) are issued.  Worker
-        // control flow is uniform: thread 0 polls each barrier and the outcome is shared
-        // through a named-barrier vote, so a timeout ends all four warps together.
-        int k = 0;
+        // epilogue: thread 0 polls each barrier and the outcome is shared through a
+        // named-barrier vote, so control flow stays uniform and a timeout ends all warps
         bool ok = true;
         auto worker_wait = [&](uint64_t* m, uint32_t parity) {
             bool done = true;
             if (tid == 0) done = pipe_wait(m, parity, abort_flag);
             return workers_all<kConvWorkerThreads>(done);
         };
-        auto epilogue = [&](int pj, int pitem) {
-            const int acc = pj % b.nacc, v = pj / b.nacc;
+        const int quarter = warp & 3;  // tensor-memory lanes 32 quarter .. + 31
+        const int Gy = a.y_cstride >> 3;
+        for (int item = blockIdx.x, j = 0; ok && item < b.items; item += gridDim.x, ++j) {
+            const int acc = j % b.nacc, v = j / b.nacc;
             if (!worker_wait(&tfull[acc], (uint32_t)v & 1u)) {
                 ok = false;
-                return;
+                break;
             }
             umma::fence_after_sync();
-            int r = pitem;
-            const int z = r % D;
-            r /= D;
-            const int y0 = (r % b.nyb) * b.Ty;
-            r /= b.nyb;
-            const int part = r % b.nsplit;
-            const int n = r / b.nsplit;
-            const int cbase = part * Cp;
-            // warp w reads lane quarter w & 3; the two warps of a quarter take alternate tiles
-            const int quarter = warp & 3;
+            const BrickItem t = brick_item(b, D, item);
+            const int cbase = t.part * Cp;
             const uint32_t trow = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * acc_cols);
             for (int m = warp >> 2; m < b.tiles; m += kConvWorkers / 4) {
-                const int q = fA + 128 * m + 32 * quarter + lane - Yb * P;  // position in plane zb = 1
-                const int yb = q / P, xp = q - (q / P) * P;
-                const int yy = y0 + yb - 1, xx = xp - 1;
-                const bool valid = yb >= 1 && yb <= b.Ty && xp >= 1 && xp <= W && yy < H;
-                const size_t vox = (size_t)n * a.nvox + ((size_t)z * H + (valid ? yy : 0)) * W + (valid ? xx : 0);
+                int yy, xx;
+                bool valid = true;
+                if (b.rowtile) {
+                    yy = t.y0 + m / tpr;
+                    xx = 128 * (m % tpr) + 32 * quarter + lane;
+                } else {
+                    const int q = P + 128 * m + 32 * quarter + lane;  // position in brick plane zb = 1
+                    const int yb = q / P, xp = q - yb * P;
+                    yy = t.y0 + yb - 1;
+                    xx = xp - 1;
+                    valid = yb >= 1 && yb <= b.Ty && xp >= 1 && xp <= W;
+                }
                 for (int c = 0; c < Cp; c += 8) {
                     float rr[8];
                     __syncwarp();
@@ -372,14 +468,15 @@ __global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(Con
                             if (a.relu) rr[e] = rr[e] > 0.f ? rr[e] : a.slope * rr[e];
                         }
                         if (a.y_fp32) {
+                            const size_t vox = (size_t)t.n * a.nvox + ((size_t)t.z * H + yy) * W + xx;
                             float* yo = static_cast<float*>(a.y) + vox * a.y_cstride + a.y_coffset + cbase + c;
                             reinterpret_cast<float4*>(yo)[0] = make_float4(rr[0], rr[1], rr[2], rr[3]);
                             reinterpret_cast<float4*>(yo)[1] = make_float4(rr[4], rr[5], rr[6], rr[7]);
                         } else {
                             __nv_bfloat162 pk[4];
                             for (int e = 0; e < 4; ++e) pk[e] = __floats2bfloat162_rn(rr[2 * e], rr[2 * e + 1]);
-                            __nv_bfloat16* yo =
-                                static_cast<__nv_bfloat16*>(a.y) + vox * a.y_cstride + a.y_coffset + cbase + c;
+                            const int gy = (a.y_coffset + cbase + c) >> 3;
+                            __nv_bfloat16* yo = static_cast<__nv_bfloat16*>(a.y) + 8 * pg.unit(t.n, Gy, gy, t.z, yy, xx);
                             *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<uint4*>(pk);
                         }
                     }
@@ -387,101 +484,7 @@ __global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(Con
             }
             umma::fence_before_sync();
             umma::mbar_arrive(&tempty[acc]);
-        };
-        if (b.wres) {  // all chunks' weights, once: [chunk][tap][Cp x 16 K-major]
-            const uint32_t s_wres = s_stage0 + (uint32_t)(kPipeStages * b.stage);
-            for (int c = 0; c < nchunk; ++c) {
-                int tap = 0, q = tid;
-                while (q >= 2 * Cp) {
-                    q -= 2 * Cp;
-                    ++tap;
-                }
-                for (; tap < 27;) {
-                    const int co = q >> 1, g = q & 1;
-                    umma::cp_async16(s_wres + (uint32_t)((c * 27 + tap) * Cp * 32) + umma::core_offset(co, g * 8, 16),
-                                     a.w + ((size_t)co * 27 + tap) * Cin + c * 16 + g * 8, 16u);
-                    q += kConvWorkerThreads;
-                    while (q >= 2 * Cp) {
-                        q -= 2 * Cp;
-                        ++tap;
-                    }
-                }
-            }
-            umma::cp_async_mbar_arrive(wfull);
         }
-        for (int item = blockIdx.x, j = 0;; item += gridDim.x, ++j) {
-            bool epi_done = j == 0;
-            if (item < b.items) {
-                int r = item;
-                const int z = r % D;
-                r /= D;
-                const int y0 = (r % b.nyb) * b.Ty;
-                r /= b.nyb;
-                const int part = r % b.nsplit;
-                const int n = r / b.nsplit;
-                const __nv_bfloat16* xin = a.x + (size_t)n * a.nvox * Cin;
-                const __nv_bfloat16* win = a.w + (size_t)part * Cp * 27 * Cin;
-                for (int c = 0; c < nchunk && ok; ++c, ++k) {
-                    if (b.nacc == 1 && c == kPipeStages && !epi_done) {
-                        epilogue(j - 1, item - (int)gridDim.x);
-                        epi_done = true;
-                        if (!ok) break;
-                    }
-                    const int s = k % kPipeStages, u = k / kPipeStages;
-                    if (u >= 1 && !worker_wait(&empty[s], (uint32_t)(u - 1) & 1u)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
-                    {  // brick: lane pairs copy both 8-channel halves (one 32-byte sector) of a position
-                        const int g = tid & 1;
-                        int f = tid >> 1;
-                        int row = f / P, xp = f - row * P;
-                        int zb = row / Yb, yb = row - zb * Yb;
-                        const uint32_t dst = st + 128u + (uint32_t)(g * b.plane);
-                        const __nv_bfloat16* src_c = xin + c * 16 + g * 8;
-                        while (f < npos) {
-                            const int zz = z + zb - 1, yy = y0 + yb - 1, xx = xp - 1;
-                            const bool in =
-                                (unsigned)zz < (unsigned)D && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
-                            const __nv_bfloat16* src = in ? src_c + ((size_t)(zz * H + yy) * W + xx) * Cin : src_c;
-                            umma::cp_async16(dst + (uint32_t)f * 16u, src, in ? 16u : 0u);
-                            f += kConvWorkerThreads / 2;
-                            xp += kConvWorkerThreads / 2;
-                            while (xp >= P) {
-                                xp -= P;
-                                if (++yb == Yb) {
-                                    yb = 0;
-                                    ++zb;
-                                }
-                            }
-                        }
-                    }
-                    if (!b.wres) {  // weights of this chunk and part: per tap a Cp x 16 K-major tile
-                        const uint32_t s_w = st + (uint32_t)b.w_off;
-                        int tap = 0, q = tid;
-                        while (q >= 2 * Cp) {
-                            q -= 2 * Cp;
-                            ++tap;
-                        }
-                        for (; tap < 27;) {
-                            const int co = q >> 1, g = q & 1;
-                            umma::cp_async16(s_w + (uint32_t)(tap * Cp * 32) + umma::core_offset(co, g * 8, 16),
-                                             win + ((size_t)co * 27 + tap) * Cin + c * 16 + g * 8, 16u);
-                            q += kConvWorkerThreads;
-                            while (q >= 2 * Cp) {
-                                q -= 2 * Cp;
-                                ++tap;
-                            }
-                        }
-                    }
-                    umma::cp_async_mbar_arrive(&full[s]);
-                }
-            }
-            if (!epi_done && ok) epilogue(j - 1, item - (int)gridDim.x);
-            if (item >= b.items || !ok) break;
-        }
-        umma::cp_async_wait_all();
     }
     umma::fence_before_sync();
     __syncthreads();
@@ -495,7 +498,8 @@ __global__ void __launch_bounds__(kConvWorkerThreads + 32, 1) k_conv3d_brick(Con
 // dy[v][co] x[v + off(tap)][ci].  Per work item (Ty output rows of one z plane) the
 // output-gradient rows and the zero-padded input brick are staged once, both as 8-channel
 // planes with 16 bytes per position, i.e. M/N-major core matrices (8 positions x 8
-// channels).  The MMA's A operand is dy (M = co, padded to 128: rows past Cout read
+// channels); both tensors are padded channel-group-major, so each 8-channel plane of the
+// rows, and each (8-channel plane, z plane) part of the brick, is one bulk copy.  The MMA's A operand is dy (M = co, padded to 128: rows past Cout read
 // whatever follows and are never stored), K = 16 positions; B is the brick read from the
 // tap's offset (N = Nc input channels).  All taps of the pass use the same A, so the
 // tensor core fetches it once per K step.  dW accumulates in tensor memory over all the
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
     }
     if (tid == 0) {
         for (int s = 0; s < kPipeStages; ++s) {
-            umma::mbar_init(&full[s], 128);
+            umma::mbar_init(&full[s], 1);
             umma::mbar_init(&empty[s], 1);
         }
         umma::mbar_init(dfull, 1);
@@ -557,7 +561,6 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
                     break;
                 }
                 umma::fence_after_sync();
-                umma::fence_async_smem();  // cp.async (generic proxy) data -> tensor core
                 const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
                 // M/N-major: leading byte offset = next 8 positions (K), stride = next 8 channels
                 const uint64_t a0 = umma::smem_desc(st, 128, (uint32_t)b.plane_dy);
@@ -585,45 +588,40 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
             if (tid == 0) done = pipe_wait(m, parity, abort_flag);
             return workers_all<128>(done);
         };
-        for (int j = 0; j < my_items && ok; ++j) {
-            const int s = j % kPipeStages, u = j / kPipeStages;
-            if (u >= 1 && !worker_wait(&empty[s], (uint32_t)(u - 1) & 1u)) {
-                ok = false;
-                break;
-            }
-            int r = (int)blockIdx.x + j * (int)gridDim.x;
-            const int z = r % D;
-            r /= D;
-            const int y0 = (r % b.nyb) * b.Ty;
-            const int n = r / b.nyb;
-            const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
-            {  // output-gradient rows: Cout/8 planes of kst*16 positions (zero at padding and past the rows)
-                const int groups = Cout >> 3, npos = b.kst * 16;
-                const __nv_bfloat16* dyn = a.dy + (size_t)n * a.nvox * Cout;
-                for (int i = tid; i < groups * npos; i += 128) {
-                    const int q = i / npos, f = i - q * npos;
-                    const int rr = f / P, xp = f - rr * P, yy = y0 + rr, xx = xp - 1;
-                    const bool in = rr < b.Ty && yy < H && (unsigned)xx < (unsigned)W;
-                    const __nv_bfloat16* src = in ? dyn + ((size_t)(z * H + yy) * W + xx) * Cout + 8 * q : dyn;
-                    umma::cp_async16(st + (uint32_t)(q * b.plane_dy + f * 16), src, in ? 16u : 0u);
+        if (tid == 0) {  // producer: per item Cout/8 runs of dy rows and Nc/8 x 3 runs of the input brick
+            const Pcg pg{D, H, W};
+            const uint32_t run_dy = (uint32_t)(b.Ty * P * 16), run_x = (uint32_t)(Yb * P * 16);
+            const int gdy = Cout >> 3, gx = Nc >> 3;
+            int j = 0;
+            for (; j < my_items; ++j) {
+                const int s = j % kPipeStages, u = j / kPipeStages;
+                if (u >= 1 && !pipe_wait(&empty[s], (uint32_t)(u - 1) & 1u, abort_flag)) {
+                    ok = false;
+                    break;
                 }
+                int r = (int)blockIdx.x + j * (int)gridDim.x;
+                const int z = r % D;
+                r /= D;
+                const int y0 = (r % b.nyb) * b.Ty;
+                const int n = r / b.nyb;
+                const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
+                umma::mbar_arrive_expect_tx(&full[s], (uint32_t)gdy * run_dy + (uint32_t)(3 * gx) * run_x);
+                // output-gradient rows y0 .. y0+Ty-1 with their zero padding columns; the
+                // positions up to kst*16 past them stay zero from the start
+                for (int q = 0; q < gdy; ++q)
+                    umma::bulk_g2s(st + (uint32_t)(q * b.plane_dy), a.dy + 8 * pg.unit(n, gdy, q, z, y0, -1), run_dy,
+                                   &full[s]);
+                for (int g = 0; g < gx; ++g)
+                    for (int zb = 0; zb < 3; ++zb)
+                        umma::bulk_g2s(st + (uint32_t)(b.x_off + g * b.plane_x) + (uint32_t)zb * run_x,
+                                       a.x + 8 * pg.unit(n, Cin >> 3, c * gx + g, z + zb - 1, y0 - 1, -1), run_x,
+                                       &full[s]);
             }
-            {  // input brick of this chunk: Nc/8 planes (as the forward kernel)
-                const int groups = Nc >> 3;
-                const __nv_bfloat16* xin = a.x + (size_t)n * a.nvox * Cin + c * Nc;
-                for (int i = tid; i < groups * npos_x; i += 128) {
-                    const int g = i / npos_x, f = i - g * npos_x;
-                    const int row = f / P, xp = f - row * P, zb = row / Yb, yb = row - zb * Yb;
-                    const int zz = z + zb - 1, yy = y0 + yb - 1, xx = xp - 1;
-                    const bool in =
-                        (unsigned)zz < (unsigned)D && (unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W;
-                    const __nv_bfloat16* src = in ? xin + ((size_t)(zz * H + yy) * W + xx) * Cin + 8 * g : xin;
-                    umma::cp_async16(st + (uint32_t)(b.x_off + g * b.plane_x + f * 16), src, in ? 16u : 0u);
-                }
-            }
-            umma::cp_async_mbar_arrive(&full[s]);
+            // no copy may still be writing shared memory when the CTA exits
+            for (int jj = j > kPipeStages ? j - kPipeStages : 0; jj < j; ++jj)
+                umma::mbar_wait(&full[jj % kPipeStages], (uint32_t)(jj / kPipeStages) & 1u, kWaitCycles);
         }
-        umma::cp_async_wait_all();
+        ok = workers_all<128>(ok);
         if (ok && my_items > 0 && worker_wait(dfull, 0u)) {
             umma::fence_after_sync();
             const int co = 32 * warp + lane;
@@ -665,47 +663,51 @@ cudaError_t flip_weights_launch(const __nv_bfloat16* w, __nv_bfloat16* wd, int C
 }
 
 // Work decomposition of the pipelined brick kernel for one layer shape: output channels
-// split into parts of Cp, weights resident or streamed, and rows per item Ty, chosen by a
-// cost model measured on GB300: an MMA (M = 128, K = 16) whose A operand is not the
-// previous one's costs ~100 cycles up to N = 192 and N / 2 beyond; staging moves ~11 bytes
-// per cycle per SM; with one accumulator the epilogue (~20 cycles per 8 columns of a
-// tile) does not overlap the MMAs.
-static bool brick_plan(const ConvArgs& a, int batch, BrickPlan* out, size_t* smem_out) {
-    const int P = a.W + 2;
+// split into parts of Cp, weights resident or streamed, and rows per item Ty (a divisor of
+// H), chosen by a cost model measured on GB300: a tcgen05.mma (M = 128, K = 16) costs ~56
+// cycles up to N = 64, 64 at N = 128 and N / 2 beyond; bulk copies of brick runs move
+// ~64 bytes per cycle per SM; the epilogue (~20 cycles per 8 columns of a tile, two warps
+// per lane quarter) overlaps the MMAs only with two accumulators.
+static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickPlan* out, size_t* smem_out) {
+    const int P = W + 2;
     const size_t smem_cap = 227 * 1024;
+    const bool rowtile = W % 128 == 0;
     double best = 1e300;
     bool found = false;
-    const int nchunk = a.Cin / 16;
-    for (int nsplit = 1; nsplit <= a.Cout / 16; ++nsplit) {
-        if (a.Cout % nsplit || (a.Cout / nsplit) % 16) continue;
-        const int Cp = a.Cout / nsplit;
+    const int nchunk = Cin / 16;
+    for (int nsplit = 1; nsplit <= Cout / 16; ++nsplit) {
+        if (Cout % nsplit || (Cout / nsplit) % 16) continue;
+        const int Cp = Cout / nsplit;
         if (Cp > 256) continue;
         const size_t w_bytes = (size_t)27 * Cp * 32;
+        const double mma_cyc = Cp <= 64 ? 56.0 : (Cp <= 128 ? 64.0 : Cp / 2.0);
         for (int wres = 0; wres <= (nsplit == 1 ? 1 : 0); ++wres)
-            for (int Ty = 1; Ty <= a.H; ++Ty) {
-                const int tiles = (Ty * P + 127) / 128;
+            for (int Ty = 1; Ty <= H; ++Ty) {
+                if (H % Ty) continue;
+                const int tiles = rowtile ? Ty * (W / 128) : (Ty * P + 127) / 128;
                 if (tiles * Cp > 512) break;
                 const int nacc = 2 * tiles * Cp <= 512 ? 2 : 1;
-                const size_t npos = (size_t)3 * (Ty + 2) * P;
-                const size_t plane = (npos * 16 + 127) / 128 * 128;
-                // M tiles read up to 128 positions past the end of the second plane
-                const size_t w_off = (128 + 2 * plane + 2048 + 127) / 128 * 128;
+                const size_t run = (size_t)(Ty + 2) * P * 16;
+                const size_t plane = (3 * run + 127) / 128 * 128;
+                // flat tiles read up to 128 positions past the end of the second plane
+                const size_t w_off = (128 + 2 * plane + (rowtile ? 0 : 2048) + 127) / 128 * 128;
                 const size_t stage = wres ? w_off : (w_off + w_bytes + 127) / 128 * 128;
                 const size_t smem = kPipeHeader + kPipeStages * stage + (wres ? nchunk * w_bytes : 0);
                 if (smem > smem_cap || plane >= (1u << 18)) break;
-                const double mma = (double)nchunk * 27 * tiles * (Cp > 192 ? Cp / 2.0 : 100.0);
-                const double load = (double)nchunk * (stage - 2176) / 11.0;
-                const double epi = tiles * (Cp / 8.0) * 20.0;
-                const double item = (mma > load ? mma : load) + (nacc == 1 ? epi : 0.0);
-                const double cost = item / ((double)Ty * a.W) * nsplit;  // per output voxel, all parts
+                const double mma = (double)nchunk * 27 * tiles * mma_cyc;
+                const double load = (double)nchunk * (6 * run + (wres ? 0 : w_bytes)) / 64.0;
+                const double epi = tiles * (Cp / 8.0) * 10.0;
+                // copies and MMAs overlap, but not perfectly: a quarter of the shorter one shows
+                double item = (mma > load ? mma : load) + 0.25 * (mma > load ? load : mma);
+                item = nacc == 2 ? (item > epi ? item : epi) : item + epi;
+                const double cost = item / ((double)Ty * W) * nsplit;  // per output voxel, all parts
                 if (cost < best) {
                     best = cost;
                     found = true;
                     int tcols = 32;
                     while (tcols < nacc * tiles * Cp) tcols <<= 1;
-                    const int nyb = (a.H + Ty - 1) / Ty;
-                    *out = BrickPlan{Ty,         tiles,      nyb,  P,     Ty + 2, Cp,   nsplit, (int)plane,
-                                     (int)w_off, wres,       (int)stage, nacc, tcols, batch * nsplit * nyb * a.D};
+                    *out = BrickPlan{Ty,   tiles, rowtile ? 1 : 0, H / Ty, P,     Ty + 2,     Cp,    nsplit,
+                                     (int)plane, (int)w_off, wres, (int)stage, nacc, tcols, batch * nsplit * (H / Ty) * D};
                     *smem_out = smem;
                 }
             }
@@ -713,10 +715,36 @@ static bool brick_plan(const ConvArgs& a, int batch, BrickPlan* out, size_t* sme
     return found;
 }
 
+// wpk[part][chunk][tap][core-matrix image of the Cp x 16 tile] = w[part Cp + r][tap][16 chunk + k]
+static __global__ void k_pack_weights(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wpk, int Cin,
+                               int Cout, int Cp) {
+    const int n = Cout * 27 * Cin, nchunk = Cin >> 4;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = i % Cin, tap = (i / Cin) % 27, co = i / (27 * Cin);
+        const int part = co / Cp, r = co - part * Cp, c = ci >> 4, k = ci & 15;
+        const size_t tile = (((size_t)part * nchunk + c) * 27 + tap) * Cp * 16;
+        wpk[tile + umma::core_offset(r, k, 16) / 2] = w[i];
+    }
+}
+
+int conv_plan_cp(int D, int H, int W, int Cin, int Cout) {
+    BrickPlan bp{};
+    size_t smem = 0;
+    return brick_plan(D, H, W, Cin, Cout, 1, &bp, &smem) ? bp.Cp : 0;
+}
+
+cudaError_t conv_pack_weights(const __nv_bfloat16* w, __nv_bfloat16* wpk, int Cin, int Cout, int Cp,
+                              cudaStream_t st) {
+    if (Cp <= 0 || Cout % Cp || Cin % 16) return cudaErrorInvalidValue;
+    k_pack_weights<<<256, 256, 0, st>>>(w, wpk, Cin, Cout, Cp);
+    return cudaGetLastError();
+}
+
 cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st) {
     BrickPlan bp{};
     size_t bsmem = 0;
-    if (!brick_plan(a, batch, &bp, &bsmem)) return cudaErrorInvalidValue;
+    if (!brick_plan(a.D, a.H, a.W, a.Cin, a.Cout, batch, &bp, &bsmem) || bp.Cp != a.wpk_cp)
+        return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_conv3d_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -724,14 +752,14 @@ cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int ctas = bp.items < sms ? bp.items : sms;
-    k_conv3d_brick<<<ctas, kConvWorkerThreads + 32, bsmem, st>>>(a, bp);
+    k_conv3d_brick<<<ctas, kConvThreads, bsmem, st>>>(a, bp);
     return cudaGetLastError();
 }
 
 // Plan of the brick weight gradient: Nc in {16, 32} input channels per pass, as many
-// taps per pass as 512 tensor-memory columns hold, and the largest Ty whose two stages
-// fit; the cost model (~46 cycles per MMA with a reused A; staging ~11 bytes per cycle per
-// SM) picks between the Nc options.  Measured alternative, slower on the denoiser's
+// taps per pass as 512 tensor-memory columns hold, and Ty a divisor of H whose two stages
+// fit; the cost model (~56 cycles per MMA; bulk copies ~64 bytes per cycle per SM) picks
+// among them.  Measured alternative, slower on the denoiser's
 // layers: one input plane per pass with the nine taps of one dz (more rows per item).
 static bool wgrad_plan(const WgradArgs& a, WgradPlan* out, size_t* smem_out) {
     const int P = a.W + 2;
@@ -742,6 +770,7 @@ static bool wgrad_plan(const WgradArgs& a, WgradPlan* out, size_t* smem_out) {
         const int ntap = Nc == 16 ? 27 : 14;
         const int ngroups = (27 + ntap - 1) / ntap;
         for (int Ty = 1; Ty <= a.H; ++Ty) {
+            if (a.H % Ty) continue;
             const int kst = (Ty * P + 15) / 16;
             const size_t plane_dy = (size_t)kst * 256;
             const size_t dy_bytes = (size_t)(a.Cout / 8) * plane_dy;
@@ -752,13 +781,14 @@ static bool wgrad_plan(const WgradArgs& a, WgradPlan* out, size_t* smem_out) {
             const size_t smem = kPipeHeader + kPipeStages * stage;
             if (smem > 227 * 1024 || plane_x >= (1u << 18) || plane_dy >= (1u << 18)) break;
             const double pos = (double)Ty * a.W;  // output voxels per item
-            const double mma = (double)kst * 27 * 46.0 * (a.Cin / Nc);
-            const double load = (double)(stage - 512) / 11.0 * (a.Cin / Nc) * ngroups;
+            const double mma = (double)kst * 27 * 56.0 * (a.Cin / Nc);
+            const double bytes = (double)(a.Cout / 8) * Ty * P * 16 + (double)(Nc / 8) * 3 * (Ty + 2) * P * 16;
+            const double load = bytes / 64.0 * (a.Cin / Nc) * ngroups;
             const double cost = (mma > load ? mma : load) / pos;
             if (cost < best) {
                 best = cost;
                 found = true;
-                const int nyb = (a.H + Ty - 1) / Ty;
+                const int nyb = a.H / Ty;
                 const int items = a.batch * nyb * a.D;
                 const int passes = (a.Cin / Nc) * ngroups;
                 int G = (152 + passes - 1) / passes;
@@ -786,26 +816,37 @@ cudaError_t wgrad_launch(const WgradArgs& a, cudaStream_t st) {
 }  // namespace sde
 
 static bool conv_shape_ok(int D, int H, int W, int Cin, int Cout, int batch) {
-    long long nvox = (long long)D * H * W;
-    return batch >= 1 && D >= 1 && H >= 1 && W >= 1 && W <= 256 && nvox % 128 == 0 && nvox * batch < (1ll << 31) &&
-           Cin >= 16 && Cin <= 192 && Cin % 16 == 0 && Cout >= 16 && Cout <= 256 && Cout % 16 == 0;
+    const long long vp = (long long)(D + 2) * (H + 2) * (W + 2);
+    return batch >= 1 && D >= 1 && H >= 1 && W >= 1 && W <= 256 && vp * batch * 256 < (1ll << 40) && Cin >= 16 &&
+           Cin <= 192 && Cin % 16 == 0 && Cout >= 16 && Cout <= 256 && Cout % 16 == 0;
 }
 
 extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int W, int Cin, const void* d_w,
                                   const float* d_bias, int Cout, void* d_y, int y_cstride, int y_coffset,
                                   int y_fp32, int relu, void* stream) {
     if (!d_x || !d_w || !d_y || !conv_shape_ok(D, H, W, Cin, Cout, batch) || y_cstride < Cout + y_coffset ||
-        y_coffset < 0 || (y_coffset % 8) || (y_cstride % 8)) {
-        set_last_error("sde_conv3d_forward: need W <= 256, D*H*W a multiple of 128, Cin in 16..192 and Cout in 16..256 "
-                       "(multiples of 16), y_cstride >= Cout + y_coffset, both multiples of 8");
+        y_coffset < 0 || (y_coffset % 8) || (y_cstride % 8) || (((uintptr_t)d_x | (uintptr_t)d_y) & 15)) {
+        set_last_error("sde_conv3d_forward: need W <= 256, Cin in 16..192 and Cout in 16..256 (multiples of 16), "
+                       "y_cstride >= Cout + y_coffset, both multiples of 8, 16-byte aligned x and y");
         return SDE_EINVAL;
     }
     unsigned int* d_status = nullptr;
     int rc = report(status_word(&d_status), "status word");
     if (rc) return rc;
+    const int Cp = conv_plan_cp(D, H, W, Cin, Cout);
+    if (!Cp) {
+        set_last_error("sde_conv3d_forward: no tile plan fits shared memory for this shape");
+        return SDE_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    __nv_bfloat16* wpk = nullptr;  // weights in the tensor core's layout, stream-ordered scratch
+    rc = report(cudaMallocAsync(reinterpret_cast<void**>(&wpk), (size_t)Cout * 27 * Cin * 2, st), "cudaMallocAsync");
+    if (rc) return rc;
+    rc = report(conv_pack_weights(static_cast<const __nv_bfloat16*>(d_w), wpk, Cin, Cout, Cp, st), "pack weights");
     ConvArgs a;
     a.x = static_cast<const __nv_bfloat16*>(d_x);
-    a.w = static_cast<const __nv_bfloat16*>(d_w);
+    a.wpk = wpk;
+    a.wpk_cp = Cp;
     a.bias = d_bias;
     a.y = d_y;
     a.D = D;
@@ -820,14 +861,17 @@ extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int 
     a.relu = relu;
     a.slope = 0.f;
     a.status = d_status;
-    return report(conv3d_launch(a, batch, (cudaStream_t)stream), "conv3d launch");
+    if (!rc) rc = report(conv3d_launch(a, batch, st), "conv3d launch");
+    const int rf = report(cudaFreeAsync(wpk, st), "cudaFreeAsync");
+    return rc ? rc : rf;
 }
 
 extern "C" int sde_conv3d_wgrad(const void* d_x, const void* d_dy, float* d_dw, int batch, int D, int H, int W,
                                 int Cin, int Cout, void* stream) {
-    if (!d_x || !d_dy || !d_dw || !conv_shape_ok(D, H, W, Cin, Cout, batch) || Cout > 128) {
-        set_last_error("sde_conv3d_wgrad: need W <= 256, D*H*W a multiple of 128, Cin in 16..192, Cout in 16..128 "
-                       "(multiples of 16)");
+    if (!d_x || !d_dy || !d_dw || !conv_shape_ok(D, H, W, Cin, Cout, batch) || Cout > 128 ||
+        (((uintptr_t)d_x | (uintptr_t)d_dy) & 15)) {
+        set_last_error("sde_conv3d_wgrad: need W <= 256, Cin in 16..192, Cout in 16..128 (multiples of 16), "
+                       "16-byte aligned x and dy");
         return SDE_EINVAL;
     }
     unsigned int* d_status = nullptr;

@@ -54,37 +54,21 @@ __device__ __forceinline__ float scale_of(const unsigned int* maxbits, int b) {
     return m > 0.f ? 1.f / m : 1.f;
 }
 
-// in0[b][v][16] = (dose * s_b, density / 2, 0, ...)
-__global__ void k_prepare_input(const float* __restrict__ dose, const float* __restrict__ rho, size_t V, int batch,
+// Input channels (padded channel-group-major, two groups): group 0 of voxel v of sample b
+// holds (dose * s_b, density / 2, 0, ...); group 1 stays zero.
+__global__ void k_prepare_input(const float* __restrict__ dose, const float* __restrict__ rho, Pcg g, int batch,
                                 const unsigned int* maxbits, bf16* __restrict__ in0) {
-    const size_t n = V * batch;
+    const size_t V = (size_t)g.D * g.H * g.W, n = V * batch;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(i / V);
-        __nv_bfloat162 p[8];
-        p[0] = __floats2bfloat162_rn(dose[i] * scale_of(maxbits, b), 0.5f * rho[i % V]);
-        for (int j = 1; j < 8; ++j) p[j] = __floats2bfloat162_rn(0.f, 0.f);
-        uint4* o = reinterpret_cast<uint4*>(in0 + i * 16);
-        o[0] = reinterpret_cast<uint4*>(p)[0];
-        o[1] = reinterpret_cast<uint4*>(p)[1];
+        const int v = (int)(i - (size_t)b * V);
+        const int x = v % g.W, y = (v / g.W) % g.H, z = v / (g.W * g.H);
+        __nv_bfloat162 p[4];
+        p[0] = __floats2bfloat162_rn(dose[i] * scale_of(maxbits, b), 0.5f * rho[v]);
+        for (int j = 1; j < 4; ++j) p[j] = __floats2bfloat162_rn(0.f, 0.f);
+        *reinterpret_cast<uint4*>(in0 + 8 * g.unit(b, 2, 0, z, y, x)) = *reinterpret_cast<uint4*>(p);
     }
 }
-
-// Fine grid (D, H, W) even in each dimension; coarse = half.  The resampling kernels move
-// eight channels (16 bytes) per thread with 32-bit index arithmetic; every channel count,
-// stride and offset is a multiple of 8 and every index range is below 2^31 (checked at
-// creation).
-struct Grid2 {
-    int D, H, W;
-    __device__ __forceinline__ int coarse_of(int v) const {
-        const int x = v % W, y = (v / W) % H, z = v / (W * H);
-        return ((z >> 1) * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1);
-    }
-    __device__ __forceinline__ int child(int vc, int d) const {  // d-th of the 8 fine children
-        const int Wc = W >> 1, Hc = H >> 1;
-        const int xc = vc % Wc, yc = (vc / Wc) % Hc, zc = vc / (Wc * Hc);
-        return ((2 * zc + (d >> 2)) * H + 2 * yc + ((d >> 1) & 1)) * W + 2 * xc + (d & 1);
-    }
-};
 
 __device__ __forceinline__ void ld8(const bf16* p, float (&f)[8]) {
     const uint4 u = *reinterpret_cast<const uint4*>(p);
@@ -102,121 +86,136 @@ __device__ __forceinline__ void st8(bf16* p, const float (&f)[8]) {
     *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(h);
 }
 
-#define SDE_GRID_LOOP(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+// Two resolutions: the fine grid F (D, H, W even) and the coarse grid C = F / 2.  The
+// resampling kernels run one thread per (coarse voxel, 8-channel group) on the launch grid
+// (ceil(Wc G / 256), Hc, Dc batch) with 256 threads, G = C/8 a power of two, and move 16
+// bytes per access: no integer division per element.  Channel counts, strides and offsets
+// are multiples of 8 (offsets and strides below are in channels).
+struct Grid2 {
+    Pcg F, C;
+};
+__host__ __device__ inline Grid2 grid2(int D, int H, int W) { return Grid2{Pcg{D, H, W}, Pcg{D / 2, H / 2, W / 2}}; }
 
-// Coarse-voxel kernels (pooling, upsampling) run one thread per (coarse voxel, 8-channel
-// group) on the grid (ceil(Wc G / 256), Hc, Dc batch) with 256 threads, G = C/8 a power of
-// two: no integer division per element.
 struct CoarseIdx {
     int q, xc, yc, zc, b;
-    size_t vc;  // b Vc + (zc Hc + yc) Wc + xc
 };
 __device__ __forceinline__ bool coarse_idx(const Grid2& g, int G, CoarseIdx& c) {
-    const int Wc = g.W >> 1, Hc = g.H >> 1, Dc = g.D >> 1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= Wc * G) return false;
+    if (t >= g.C.W * G) return false;
     c.q = t & (G - 1);
     c.xc = t >> (__ffs(G) - 1);
     c.yc = blockIdx.y;
-    c.zc = blockIdx.z % Dc;
-    c.b = blockIdx.z / Dc;
-    c.vc = (((size_t)c.b * Dc + c.zc) * Hc + c.yc) * Wc + c.xc;
+    c.zc = blockIdx.z % g.C.D;
+    c.b = blockIdx.z / g.C.D;
     return true;
 }
-// fine voxel (with batch) of child d of c: (2 zc + d/4, 2 yc + (d/2)%2, 2 xc + d%2)
-__device__ __forceinline__ size_t fine_of(const Grid2& g, const CoarseIdx& c, int d) {
-    return (((size_t)c.b * g.D + 2 * c.zc + (d >> 2)) * g.H + 2 * c.yc + ((d >> 1) & 1)) * g.W + 2 * c.xc + (d & 1);
+// 16-byte unit of fine child d = (dz, dy, dx) bits (4, 2, 1) of coarse voxel c, group gq of Gt
+__device__ __forceinline__ size_t fine_unit(const Grid2& g, const CoarseIdx& c, int Gt, int gq, int d) {
+    return g.F.unit(c.b, Gt, gq, 2 * c.zc + (d >> 2), 2 * c.yc + ((d >> 1) & 1), 2 * c.xc + (d & 1));
+}
+__device__ __forceinline__ size_t coarse_unit(const Grid2& g, const CoarseIdx& c, int Gt, int gq) {
+    return g.C.unit(c.b, Gt, gq, c.zc, c.yc, c.xc);
 }
 
-// out[b][vc][c] = mean of the 8 children of vc in in[b][v][ico + c] (row stride ics)
+// out (C channels, coarse) = mean of the 8 children in in (channels ico .. ico+C of ics)
 __global__ void k_avgpool2(const bf16* __restrict__ in, int ics, int ico, int C, Grid2 g, bf16* __restrict__ out) {
     CoarseIdx c;
     if (!coarse_idx(g, C >> 3, c)) return;
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int d = 0; d < 8; ++d) {
         float f[8];
-        ld8(in + fine_of(g, c, d) * ics + ico + 8 * c.q, f);
+        ld8(in + 8 * fine_unit(g, c, ics >> 3, (ico >> 3) + c.q, d), f);
         for (int e = 0; e < 8; ++e) acc[e] += f[e];
     }
     for (int e = 0; e < 8; ++e) acc[e] *= 0.125f;
-    st8(out + c.vc * C + 8 * c.q, acc);
+    st8(out + 8 * coarse_unit(g, c, C >> 3, c.q), acc);
 }
 
-// din[b][v][c] = dout[b][parent(v)][c] / 8 + add[b][v][aco + c]   (add may be NULL)
+// din (C channels, fine) = dout[parent] / 8 + add (channels aco .. aco+C of acs; may be NULL)
 __global__ void k_avgpool2_bwd(const bf16* __restrict__ dout, const bf16* __restrict__ add, int acs, int aco, int C,
-                               Grid2 g, int batch, bf16* __restrict__ din) {
-    const int G = C >> 3, Vf = g.D * g.H * g.W, Vc = Vf >> 3;
-    SDE_GRID_LOOP(i, Vf * batch * G) {
-        const int q = i % G, r = i / G, v = r % Vf, b = r / Vf;
-        float f[8];
-        ld8(dout + ((size_t)b * Vc + g.coarse_of(v)) * C + 8 * q, f);
-        for (int e = 0; e < 8; ++e) f[e] *= 0.125f;
+                               Grid2 g, bf16* __restrict__ din) {
+    CoarseIdx c;
+    if (!coarse_idx(g, C >> 3, c)) return;
+    float f[8];
+    ld8(dout + 8 * coarse_unit(g, c, C >> 3, c.q), f);
+    for (int e = 0; e < 8; ++e) f[e] *= 0.125f;
+    for (int d = 0; d < 8; ++d) {
+        float o[8];
+        for (int e = 0; e < 8; ++e) o[e] = f[e];
         if (add) {
             float a[8];
-            ld8(add + ((size_t)b * Vf + v) * acs + aco + 8 * q, a);
-            for (int e = 0; e < 8; ++e) f[e] += a[e];
+            ld8(add + 8 * fine_unit(g, c, acs >> 3, (aco >> 3) + c.q, d), a);
+            for (int e = 0; e < 8; ++e) o[e] += a[e];
         }
-        st8(din + ((size_t)b * Vf + v) * C + 8 * q, f);
+        st8(din + 8 * fine_unit(g, c, C >> 3, c.q, d), o);
     }
 }
 
-// out[b][v][oco + c] = in[b][parent(v)][c]   (nearest-neighbour upsampling): each coarse
-// 8-channel group is read once and written to its 8 children.
+// out (channels oco .. oco+C of ocs, fine) = in[parent] (C channels, coarse): nearest-
+// neighbour upsampling; each coarse group is read once and written to its 8 children.
 __global__ void k_upsample2(const bf16* __restrict__ in, int C, Grid2 g, bf16* __restrict__ out, int ocs, int oco) {
     CoarseIdx c;
     if (!coarse_idx(g, C >> 3, c)) return;
-    const uint4 val = *reinterpret_cast<const uint4*>(in + c.vc * C + 8 * c.q);
-    for (int d = 0; d < 8; ++d) *reinterpret_cast<uint4*>(out + fine_of(g, c, d) * ocs + oco + 8 * c.q) = val;
+    const uint4 val = *reinterpret_cast<const uint4*>(in + 8 * coarse_unit(g, c, C >> 3, c.q));
+    for (int d = 0; d < 8; ++d)
+        *reinterpret_cast<uint4*>(out + 8 * fine_unit(g, c, ocs >> 3, (oco >> 3) + c.q, d)) = val;
+}
+
+// dout (C channels, coarse) = sum over the 8 children of din (channels ico .. ico+C of ics)
+__global__ void k_upsample2_bwd(const bf16* __restrict__ din, int ics, int ico, int C, Grid2 g,
+                                bf16* __restrict__ dout) {
+    CoarseIdx c;
+    if (!coarse_idx(g, C >> 3, c)) return;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int d = 0; d < 8; ++d) {
+        float f[8];
+        ld8(din + 8 * fine_unit(g, c, ics >> 3, (ico >> 3) + c.q, d), f);
+        for (int e = 0; e < 8; ++e) acc[e] += f[e];
+    }
+    st8(dout + 8 * coarse_unit(g, c, C >> 3, c.q), acc);
 }
 
 // Launch geometry of the coarse-voxel kernels (C/8 must be a power of two).
 static bool coarse_grid(const Grid2& g, int C, int batch, dim3& grid) {
     const int G = C >> 3;
-    if (C % 8 || G <= 0 || (G & (G - 1)) || (g.D | g.H | g.W) & 1) return false;
-    const long long z = (long long)(g.D >> 1) * batch;
-    if (z > 65535 || (g.H >> 1) > 65535) return false;
-    grid = dim3((unsigned)(((g.W >> 1) * G + 255) / 256), (unsigned)(g.H >> 1), (unsigned)z);
+    if (C % 8 || G <= 0 || (G & (G - 1)) || (g.F.D | g.F.H | g.F.W) & 1) return false;
+    const long long z = (long long)g.C.D * batch;
+    if (z > 65535 || g.C.H > 65535) return false;
+    grid = dim3((unsigned)((g.C.W * G + 255) / 256), (unsigned)g.C.H, (unsigned)z);
     return true;
 }
 
-// dout[b][vc][c] = sum over the 8 children of din[b][v][ico + c]
-__global__ void k_upsample2_bwd(const bf16* __restrict__ din, int ics, int ico, int C, Grid2 g, int batch,
-                                bf16* __restrict__ dout) {
-    const int G = C >> 3, Vf = g.D * g.H * g.W, Vc = Vf >> 3;
-    SDE_GRID_LOOP(i, Vc * batch * G) {
-        const int q = i % G, r = i / G, vc = r % Vc, b = r / Vc;
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int d = 0; d < 8; ++d) {
-            float f[8];
-            ld8(din + ((size_t)b * Vf + g.child(vc, d)) * ics + ico + 8 * q, f);
-            for (int e = 0; e < 8; ++e) acc[e] += f[e];
-        }
-        st8(dout + ((size_t)b * Vc + vc) * C + 8 * q, acc);
-    }
-}
-
-// Leaky ReLU backward: dy[r][c] *= (y[r][yco + c] > 0 ? 1 : slope)  (y has the sign of x)
-__global__ void k_relu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y, int ycs, int yco, int C, int N,
-                           float slope) {
+// Leaky ReLU backward over the whole padded tensors (the border is zero in both and stays
+// zero): dy[u] *= (y > 0 ? 1 : slope), y the matching group of channels yco .. of ycs
+// (y has the sign of the pre-activation).  units = batch x C/8 x padded voxels.
+__global__ void k_relu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y, int ycs, int yco, int C, int units,
+                           int vp, float slope) {
     const int G = C >> 3;
-    SDE_GRID_LOOP(i, N * G) {
-        const int q = i % G, r = i / G;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < units; i += gridDim.x * blockDim.x) {
+        const int r = i / vp, v = i - r * vp, q = r % G, b = r / G;
         float f[8], t[8];
-        ld8(dy + (size_t)r * C + 8 * q, f);
-        ld8(y + (size_t)r * ycs + yco + 8 * q, t);
+        ld8(dy + (size_t)8 * i, f);
+        ld8(y + 8 * (((size_t)b * (ycs >> 3) + (yco >> 3) + q) * vp + v), t);
         for (int e = 0; e < 8; ++e)
             if (!(t[e] > 0.f)) f[e] *= slope;
-        st8(dy + (size_t)r * C + 8 * q, f);
+        st8(dy + (size_t)8 * i, f);
     }
 }
 
-// db[c] += sum over rows of dy[r][c]
-__global__ void k_bias_grad(const bf16* __restrict__ dy, size_t N, int C, float* __restrict__ db) {
+// db[c] += sum over voxels of dy (padded channel-group-major, C channels; the border is
+// zero and adds nothing); units = batch x C/8 x padded voxels
+__global__ void k_bias_grad(const bf16* __restrict__ dy, int units, int vp, int C, float* __restrict__ db) {
     extern __shared__ float s_acc[];
     for (int c = threadIdx.x; c < C; c += blockDim.x) s_acc[c] = 0.f;
     __syncthreads();
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N * C; i += (size_t)gridDim.x * blockDim.x)
-        atomicAdd(&s_acc[i % C], __bfloat162float(dy[i]));
+    const int G = C >> 3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < units; i += gridDim.x * blockDim.x) {
+        const int q = (i / vp) % G;
+        float f[8];
+        ld8(dy + (size_t)8 * i, f);
+        for (int e = 0; e < 8; ++e)
+            if (f[e] != 0.f) atomicAdd(&s_acc[8 * q + e], f[e]);
+    }
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&db[c], s_acc[c]);
 }
@@ -225,27 +224,28 @@ __global__ void k_bias_grad(const bf16* __restrict__ dy, size_t N, int C, float*
 // (c the target scale, e.g. the ratio of history counts of the two runs).  The squared
 // error is weighted by 1/(t + kappa): the gamma index compares doses with local
 // normalisation, so relative errors in low-dose voxels matter as much as absolute
-// errors at the peak.  loss_acc += w diff^2; dout[b][v][0] = 2 w diff.  The gradient
+// errors at the peak.  loss_acc += w diff^2; channel 0 of dout at (b, v) = 2 w diff.  The gradient
 // is that of the summed loss (the reported loss is its mean): averaging over millions
 // of voxels would push the gradients far below Adam's epsilon.
 __global__ void k_loss(const float* __restrict__ dose_low, const float* __restrict__ out, const float* __restrict__ target,
-                       float target_scale, const unsigned int* maxbits, size_t V, int batch, bf16* __restrict__ dout,
+                       float target_scale, const unsigned int* maxbits, Pcg g, int batch, bf16* __restrict__ dout,
                        float* loss_acc) {
-    const size_t n = V * batch;
+    const size_t V = (size_t)g.D * g.H * g.W, n = V * batch;
     const float gscale = 2.f;
     float local = 0.f;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float s = scale_of(maxbits, (int)(i / V));
+        const int b = (int)(i / V);
+        const int v = (int)(i - (size_t)b * V);
+        const float s = scale_of(maxbits, b);
         const float t = target[i] * target_scale * s;
         const float diff = dose_low[i] * s + out[i * 16] - t;
         const float w = 1.f / (fabsf(t) + kLossKappa);
         local += w * diff * diff;
-        __nv_bfloat162 p[8];
+        __nv_bfloat162 p[4];
         p[0] = __floats2bfloat162_rn(gscale * w * diff, 0.f);
-        for (int j = 1; j < 8; ++j) p[j] = __floats2bfloat162_rn(0.f, 0.f);
-        uint4* o = reinterpret_cast<uint4*>(dout + i * 16);
-        o[0] = reinterpret_cast<uint4*>(p)[0];
-        o[1] = reinterpret_cast<uint4*>(p)[1];
+        for (int j = 1; j < 4; ++j) p[j] = __floats2bfloat162_rn(0.f, 0.f);
+        const int x = v % g.W, y = (v / g.W) % g.H, z = v / (g.W * g.H);
+        *reinterpret_cast<uint4*>(dout + 8 * g.unit(b, 2, 0, z, y, x)) = *reinterpret_cast<uint4*>(p);
     }
     for (int off = 16; off > 0; off >>= 1) local += __shfl_down_sync(0xffffffffu, local, off);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, local);
@@ -370,9 +370,12 @@ namespace {
 struct Layer {
     int Cin, Cout;
     bool relu;
+    int lvl;  // resolution level: grid / 2^lvl
     size_t nw;
     float *w32, *b32, *gw, *gb, *mw, *vw, *mb, *vb;
     bf16 *w16, *wflip;
+    bf16 *wpk, *wpkf;  // w16 and wflip packed for the tensor core (conv_pack_weights)
+    int cp, cpf;       // their output channels per part
 };
 
 // Each grid-stride kernel uses this many blocks.
@@ -429,20 +432,23 @@ struct HostRng {
     double normal() { return sqrt(-2.0 * log(uniform())) * cos(6.283185307179586 * uniform()); }
 };
 
-int conv(sde_denoiser* d, const bf16* x, int batch, int D, int H, int W, const Layer& l, const bf16* w, int Cout,
+// One convolution of layer l at grid D x H x W: the forward one, or with flip the data
+// gradient (dy convolved with the flipped weights, Cin and Cout exchanged).
+int conv(sde_denoiser* d, const bf16* x, int batch, int D, int H, int W, const Layer& l, bool flip, int Cout,
          void* y, int cstride, int coffset, bool fp32, bool relu, const float* bias) {
     unsigned int* status = nullptr;
     int rc = fail(denoise_status_word(&status), "status word");
     if (rc) return rc;
     ConvArgs a;
     a.x = x;
-    a.w = w;
+    a.wpk = flip ? l.wpkf : l.wpk;
+    a.wpk_cp = flip ? l.cpf : l.cp;
     a.bias = bias;
     a.y = y;
     a.D = D;
     a.H = H;
     a.W = W;
-    a.Cin = (w == l.wflip) ? l.Cout : l.Cin;
+    a.Cin = flip ? l.Cout : l.Cin;
     a.Cout = Cout;
     a.nvox = D * H * W;
     a.y_cstride = cstride;
@@ -472,13 +478,14 @@ int wgrad(sde_denoiser* d, const bf16* x, const bf16* dy, const Layer& l, int ba
     a.status = status;
     rc = fail(wgrad_launch(a, d->st), "wgrad launch");
     if (rc) return rc;
-    const size_t N = (size_t)batch * a.nvox;
-    k_bias_grad<<<kBlocks, 256, l.Cout * sizeof(float), d->st>>>(dy, N, l.Cout, l.gb);
+    const int vp = (int)Pcg{D, H, W}.vp();
+    k_bias_grad<<<kBlocks, 256, l.Cout * sizeof(float), d->st>>>(dy, batch * (l.Cout >> 3) * vp, vp, l.Cout, l.gb);
     return fail(cudaGetLastError(), "bias grad launch");
 }
 
-int relu_bwd(sde_denoiser* d, bf16* dy, const bf16* y, int ycs, int yco, int C, size_t N) {
-    k_relu_bwd<<<kBlocks, 256, 0, d->st>>>(dy, y, ycs, yco, C, (int)N, kLeak);
+int relu_bwd(sde_denoiser* d, bf16* dy, const bf16* y, int ycs, int yco, int C, int batch, const Pcg& g) {
+    const int vp = (int)g.vp();
+    k_relu_bwd<<<kBlocks, 256, 0, d->st>>>(dy, y, ycs, yco, C, batch * (C >> 3) * vp, vp, kLeak);
     return fail(cudaGetLastError(), "relu bwd launch");
 }
 
@@ -491,95 +498,109 @@ int relu_bwd(sde_denoiser* d, bf16* dy, const bf16* y, int ycs, int yco, int C, 
 int forward(sde_denoiser* d, const float* dose_low, const float* rho, int batch) {
     const int D = d->D, H = d->H, W = d->W;
     const int D2 = D / 2, H2 = H / 2, W2 = W / 2, D3 = D / 4, H3 = H / 4, W3 = W / 4;
-    Grid2 g1{D, H, W}, g2{D2, H2, W2};
+    const Grid2 g1 = grid2(D, H, W), g2 = grid2(D2, H2, W2);
     DN_TRY(fail(cudaMemsetAsync(d->maxbits, 0, sizeof(unsigned int) * d->batch_max, d->st), "memset"));
     k_absmax<<<kBlocks, 256, 0, d->st>>>(dose_low, d->V1, batch, d->maxbits);
-    k_prepare_input<<<kBlocks, 256, 0, d->st>>>(dose_low, rho, d->V1, batch, d->maxbits, d->in0);
+    k_prepare_input<<<kBlocks, 256, 0, d->st>>>(dose_low, rho, g1.F, batch, d->maxbits, d->in0);
     DN_TRY(fail(cudaGetLastError(), "input launch"));
     Layer* L = d->L;
-    DN_TRY(conv(d, d->in0, batch, D, H, W, L[0], L[0].w16, 32, d->e1a, 32, 0, false, true, L[0].b32));
-    DN_TRY(conv(d, d->e1a, batch, D, H, W, L[1], L[1].w16, 32, d->cat1, 96, 64, false, true, L[1].b32));
+    DN_TRY(conv(d, d->in0, batch, D, H, W, L[0], false, 32, d->e1a, 32, 0, false, true, L[0].b32));
+    DN_TRY(conv(d, d->e1a, batch, D, H, W, L[1], false, 32, d->cat1, 96, 64, false, true, L[1].b32));
     dim3 grid;
     if (!coarse_grid(g1, 64, batch, grid) || !coarse_grid(g2, 128, batch, grid))
         return fail(cudaErrorInvalidValue, "pooling grid");
     coarse_grid(g1, 32, batch, grid);
     k_avgpool2<<<grid, 256, 0, d->st>>>(d->cat1, 96, 64, 32, g1, d->p1);
-    DN_TRY(conv(d, d->p1, batch, D2, H2, W2, L[2], L[2].w16, 64, d->e2a, 64, 0, false, true, L[2].b32));
-    DN_TRY(conv(d, d->e2a, batch, D2, H2, W2, L[3], L[3].w16, 64, d->cat2, 192, 128, false, true, L[3].b32));
+    DN_TRY(conv(d, d->p1, batch, D2, H2, W2, L[2], false, 64, d->e2a, 64, 0, false, true, L[2].b32));
+    DN_TRY(conv(d, d->e2a, batch, D2, H2, W2, L[3], false, 64, d->cat2, 192, 128, false, true, L[3].b32));
     coarse_grid(g2, 64, batch, grid);
     k_avgpool2<<<grid, 256, 0, d->st>>>(d->cat2, 192, 128, 64, g2, d->p2);
-    DN_TRY(conv(d, d->p2, batch, D3, H3, W3, L[4], L[4].w16, 128, d->b1, 128, 0, false, true, L[4].b32));
-    DN_TRY(conv(d, d->b1, batch, D3, H3, W3, L[5], L[5].w16, 128, d->b2, 128, 0, false, true, L[5].b32));
+    DN_TRY(conv(d, d->p2, batch, D3, H3, W3, L[4], false, 128, d->b1, 128, 0, false, true, L[4].b32));
+    DN_TRY(conv(d, d->b1, batch, D3, H3, W3, L[5], false, 128, d->b2, 128, 0, false, true, L[5].b32));
     coarse_grid(g2, 128, batch, grid);
     k_upsample2<<<grid, 256, 0, d->st>>>(d->b2, 128, g2, d->cat2, 192, 0);
-    DN_TRY(conv(d, d->cat2, batch, D2, H2, W2, L[6], L[6].w16, 64, d->d2a, 64, 0, false, true, L[6].b32));
-    DN_TRY(conv(d, d->d2a, batch, D2, H2, W2, L[7], L[7].w16, 64, d->d2, 64, 0, false, true, L[7].b32));
+    DN_TRY(conv(d, d->cat2, batch, D2, H2, W2, L[6], false, 64, d->d2a, 64, 0, false, true, L[6].b32));
+    DN_TRY(conv(d, d->d2a, batch, D2, H2, W2, L[7], false, 64, d->d2, 64, 0, false, true, L[7].b32));
     coarse_grid(g1, 64, batch, grid);
     k_upsample2<<<grid, 256, 0, d->st>>>(d->d2, 64, g1, d->cat1, 96, 0);
-    DN_TRY(conv(d, d->cat1, batch, D, H, W, L[8], L[8].w16, 32, d->d1a, 32, 0, false, true, L[8].b32));
-    DN_TRY(conv(d, d->d1a, batch, D, H, W, L[9], L[9].w16, 32, d->d1, 32, 0, false, true, L[9].b32));
-    DN_TRY(conv(d, d->d1, batch, D, H, W, L[10], L[10].w16, 16, d->out, 16, 0, true, false, L[10].b32));
+    DN_TRY(conv(d, d->cat1, batch, D, H, W, L[8], false, 32, d->d1a, 32, 0, false, true, L[8].b32));
+    DN_TRY(conv(d, d->d1a, batch, D, H, W, L[9], false, 32, d->d1, 32, 0, false, true, L[9].b32));
+    DN_TRY(conv(d, d->d1, batch, D, H, W, L[10], false, 16, d->out, 16, 0, true, false, L[10].b32));
     return fail(cudaGetLastError(), "forward launch");
 }
 
 int backward(sde_denoiser* d, int batch) {
     const int D = d->D, H = d->H, W = d->W;
     const int D2 = D / 2, H2 = H / 2, W2 = W / 2, D3 = D / 4, H3 = H / 4, W3 = W / 4;
-    Grid2 g1{D, H, W}, g2{D2, H2, W2};
-    const size_t N1 = d->V1 * batch, N2 = d->V2 * batch, N3 = d->V3 * batch;
+    const Grid2 g1 = grid2(D, H, W), g2 = grid2(D2, H2, W2);
+    const Pcg& P1 = g1.F;
+    const Pcg& P2 = g2.F;
+    const Pcg& P3 = g2.C;
     Layer* L = d->L;
+    dim3 grid;
     // out layer
     DN_TRY(wgrad(d, d->d1, d->g_out, L[10], batch, D, H, W));
-    DN_TRY(conv(d, d->g_out, batch, D, H, W, L[10], L[10].wflip, 32, d->g_d1, 32, 0, false, false, nullptr));
-    DN_TRY(relu_bwd(d, d->g_d1, d->d1, 32, 0, 32, N1));
+    DN_TRY(conv(d, d->g_out, batch, D, H, W, L[10], true, 32, d->g_d1, 32, 0, false, false, nullptr));
+    DN_TRY(relu_bwd(d, d->g_d1, d->d1, 32, 0, 32, batch, P1));
     DN_TRY(wgrad(d, d->d1a, d->g_d1, L[9], batch, D, H, W));
-    DN_TRY(conv(d, d->g_d1, batch, D, H, W, L[9], L[9].wflip, 32, d->g_d1a, 32, 0, false, false, nullptr));
-    DN_TRY(relu_bwd(d, d->g_d1a, d->d1a, 32, 0, 32, N1));
+    DN_TRY(conv(d, d->g_d1, batch, D, H, W, L[9], true, 32, d->g_d1a, 32, 0, false, false, nullptr));
+    DN_TRY(relu_bwd(d, d->g_d1a, d->d1a, 32, 0, 32, batch, P1));
     DN_TRY(wgrad(d, d->cat1, d->g_d1a, L[8], batch, D, H, W));
-    DN_TRY(conv(d, d->g_d1a, batch, D, H, W, L[8], L[8].wflip, 96, d->g_cat1, 96, 0, false, false, nullptr));
-    k_upsample2_bwd<<<kBlocks, 256, 0, d->st>>>(d->g_cat1, 96, 0, 64, g1, batch, d->g_d2);
-    DN_TRY(relu_bwd(d, d->g_d2, d->d2, 64, 0, 64, N2));
+    DN_TRY(conv(d, d->g_d1a, batch, D, H, W, L[8], true, 96, d->g_cat1, 96, 0, false, false, nullptr));
+    coarse_grid(g1, 64, batch, grid);
+    k_upsample2_bwd<<<grid, 256, 0, d->st>>>(d->g_cat1, 96, 0, 64, g1, d->g_d2);
+    DN_TRY(relu_bwd(d, d->g_d2, d->d2, 64, 0, 64, batch, P2));
     DN_TRY(wgrad(d, d->d2a, d->g_d2, L[7], batch, D2, H2, W2));
-    DN_TRY(conv(d, d->g_d2, batch, D2, H2, W2, L[7], L[7].wflip, 64, d->g_d2a, 64, 0, false, false, nullptr));
-    DN_TRY(relu_bwd(d, d->g_d2a, d->d2a, 64, 0, 64, N2));
+    DN_TRY(conv(d, d->g_d2, batch, D2, H2, W2, L[7], true, 64, d->g_d2a, 64, 0, false, false, nullptr));
+    DN_TRY(relu_bwd(d, d->g_d2a, d->d2a, 64, 0, 64, batch, P2));
     DN_TRY(wgrad(d, d->cat2, d->g_d2a, L[6], batch, D2, H2, W2));
-    DN_TRY(conv(d, d->g_d2a, batch, D2, H2, W2, L[6], L[6].wflip, 192, d->g_cat2, 192, 0, false, false, nullptr));
-    k_upsample2_bwd<<<kBlocks, 256, 0, d->st>>>(d->g_cat2, 192, 0, 128, g2, batch, d->g_b2);
-    DN_TRY(relu_bwd(d, d->g_b2, d->b2, 128, 0, 128, N3));
+    DN_TRY(conv(d, d->g_d2a, batch, D2, H2, W2, L[6], true, 192, d->g_cat2, 192, 0, false, false, nullptr));
+    coarse_grid(g2, 128, batch, grid);
+    k_upsample2_bwd<<<grid, 256, 0, d->st>>>(d->g_cat2, 192, 0, 128, g2, d->g_b2);
+    DN_TRY(relu_bwd(d, d->g_b2, d->b2, 128, 0, 128, batch, P3));
     DN_TRY(wgrad(d, d->b1, d->g_b2, L[5], batch, D3, H3, W3));
-    DN_TRY(conv(d, d->g_b2, batch, D3, H3, W3, L[5], L[5].wflip, 128, d->g_b1, 128, 0, false, false, nullptr));
-    DN_TRY(relu_bwd(d, d->g_b1, d->b1, 128, 0, 128, N3));
+    DN_TRY(conv(d, d->g_b2, batch, D3, H3, W3, L[5], true, 128, d->g_b1, 128, 0, false, false, nullptr));
+    DN_TRY(relu_bwd(d, d->g_b1, d->b1, 128, 0, 128, batch, P3));
     DN_TRY(wgrad(d, d->p2, d->g_b1, L[4], batch, D3, H3, W3));
-    DN_TRY(conv(d, d->g_b1, batch, D3, H3, W3, L[4], L[4].wflip, 64, d->g_p2, 64, 0, false, false, nullptr));
-    k_avgpool2_bwd<<<kBlocks, 256, 0, d->st>>>(d->g_p2, d->g_cat2, 192, 128, 64, g2, batch, d->g_e2);
-    DN_TRY(relu_bwd(d, d->g_e2, d->cat2, 192, 128, 64, N2));
+    DN_TRY(conv(d, d->g_b1, batch, D3, H3, W3, L[4], true, 64, d->g_p2, 64, 0, false, false, nullptr));
+    coarse_grid(g2, 64, batch, grid);
+    k_avgpool2_bwd<<<grid, 256, 0, d->st>>>(d->g_p2, d->g_cat2, 192, 128, 64, g2, d->g_e2);
+    DN_TRY(relu_bwd(d, d->g_e2, d->cat2, 192, 128, 64, batch, P2));
     DN_TRY(wgrad(d, d->e2a, d->g_e2, L[3], batch, D2, H2, W2));
-    DN_TRY(conv(d, d->g_e2, batch, D2, H2, W2, L[3], L[3].wflip, 64, d->g_e2a, 64, 0, false, false, nullptr));
-    DN_TRY(relu_bwd(d, d->g_e2a, d->e2a, 64, 0, 64, N2));
+    DN_TRY(conv(d, d->g_e2, batch, D2, H2, W2, L[3], true, 64, d->g_e2a, 64, 0, false, false, nullptr));
+    DN_TRY(relu_bwd(d, d->g_e2a, d->e2a, 64, 0, 64, batch, P2));
     DN_TRY(wgrad(d, d->p1, d->g_e2a, L[2], batch, D2, H2, W2));
-    DN_TRY(conv(d, d->g_e2a, batch, D2, H2, W2, L[2], L[2].wflip, 32, d->g_p1, 32, 0, false, false, nullptr));
-    k_avgpool2_bwd<<<kBlocks, 256, 0, d->st>>>(d->g_p1, d->g_cat1, 96, 64, 32, g1, batch, d->g_e1);
-    DN_TRY(relu_bwd(d, d->g_e1, d->cat1, 96, 64, 32, N1));
+    DN_TRY(conv(d, d->g_e2a, batch, D2, H2, W2, L[2], true, 32, d->g_p1, 32, 0, false, false, nullptr));
+    coarse_grid(g1, 32, batch, grid);
+    k_avgpool2_bwd<<<grid, 256, 0, d->st>>>(d->g_p1, d->g_cat1, 96, 64, 32, g1, d->g_e1);
+    DN_TRY(relu_bwd(d, d->g_e1, d->cat1, 96, 64, 32, batch, P1));
     DN_TRY(wgrad(d, d->e1a, d->g_e1, L[1], batch, D, H, W));
-    DN_TRY(conv(d, d->g_e1, batch, D, H, W, L[1], L[1].wflip, 32, d->g_e1a, 32, 0, false, false, nullptr));
-    DN_TRY(relu_bwd(d, d->g_e1a, d->e1a, 32, 0, 32, N1));
+    DN_TRY(conv(d, d->g_e1, batch, D, H, W, L[1], true, 32, d->g_e1a, 32, 0, false, false, nullptr));
+    DN_TRY(relu_bwd(d, d->g_e1a, d->e1a, 32, 0, 32, batch, P1));
     DN_TRY(wgrad(d, d->in0, d->g_e1a, L[0], batch, D, H, W));
     return fail(cudaGetLastError(), "backward launch");
 }
 
-int refresh_flips(sde_denoiser* d) {
-    for (int i = 1; i < 11; ++i)
-        DN_TRY(fail(flip_weights_launch(d->L[i].w16, d->L[i].wflip, d->L[i].Cin, d->L[i].Cout, d->st), "flip"));
+// After every change of the BF16 weights: the flipped copies and both packed images.
+int refresh_weights(sde_denoiser* d) {
+    for (int i = 0; i < 11; ++i) {
+        Layer& l = d->L[i];
+        DN_TRY(fail(conv_pack_weights(l.w16, l.wpk, l.Cin, l.Cout, l.cp, d->st), "pack"));
+        if (i == 0) continue;  // the input layer needs no data gradient
+        DN_TRY(fail(flip_weights_launch(l.w16, l.wflip, l.Cin, l.Cout, d->st), "flip"));
+        DN_TRY(fail(conv_pack_weights(l.wflip, l.wpkf, l.Cout, l.Cin, l.cpf, d->st), "pack"));
+    }
     return SDE_OK;
 }
+
 
 }  // namespace
 
 extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int batch_max, uint64_t seed) {
-    if (!out || D < 4 || H < 4 || W < 4 || (D % 4) || (H % 4) || (W % 4) || batch_max < 1 ||
-        ((long long)(D / 4) * (H / 4) * (W / 4)) % 128 || (long long)D * H * W * batch_max * 24 >= (1ll << 31)) {
-        set_last_error("sde_denoiser_create: D, H, W must be multiples of 4 with (D/4)(H/4)(W/4) a multiple of 128 "
-                       "and D H W batch_max below 2^31 / 24");
+    if (!out || D < 4 || H < 4 || W < 4 || (D % 4) || (H % 4) || (W % 4) || W > 256 || batch_max < 1 ||
+        (long long)(D + 2) * (H + 2) * (W + 2) * batch_max * 24 >= (1ll << 31)) {
+        set_last_error("sde_denoiser_create: D, H, W must be multiples of 4, W <= 256, and (D+2)(H+2)(W+2) batch_max "
+                       "below 2^31 / 24");
         return SDE_EINVAL;
     }
     sde_denoiser* d = new (std::nothrow) sde_denoiser();
@@ -596,6 +617,7 @@ extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int 
     d->V3 = d->V2 / 8;
     const int cin[11] = {16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 32};
     const int cout[11] = {32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16};
+    const int lvl[11] = {0, 0, 1, 1, 2, 2, 1, 1, 0, 0, 0};
     HostRng rng{seed ^ 0xD1B54A32D192ED03ull};
     int rc = SDE_OK;
     for (int i = 0; i < 11 && rc == SDE_OK; ++i) {
@@ -603,7 +625,16 @@ extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int 
         l.Cin = cin[i];
         l.Cout = cout[i];
         l.relu = i < 10;
+        l.lvl = lvl[i];
         l.nw = (size_t)l.Cout * 27 * l.Cin;
+        const int Dl = D >> l.lvl, Hl = H >> l.lvl, Wl = W >> l.lvl;
+        l.cp = conv_plan_cp(Dl, Hl, Wl, l.Cin, l.Cout);
+        l.cpf = conv_plan_cp(Dl, Hl, Wl, l.Cout, l.Cin);
+        if (!l.cp || !l.cpf) {
+            set_last_error("sde_denoiser_create: no convolution tile plan for this grid");
+            rc = SDE_EINVAL;
+            break;
+        }
         rc = dalloc(d, &l.w32, l.nw);
         if (!rc) rc = dalloc(d, &l.gw, l.nw);
         if (!rc) rc = dalloc(d, &l.mw, l.nw);
@@ -614,6 +645,8 @@ extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int 
         if (!rc) rc = dalloc(d, &l.vb, (size_t)l.Cout);
         if (!rc) rc = dalloc(d, &l.w16, l.nw);
         if (!rc) rc = dalloc(d, &l.wflip, l.nw);
+        if (!rc) rc = dalloc(d, &l.wpk, l.nw);
+        if (!rc) rc = dalloc(d, &l.wpkf, l.nw);
         if (rc) break;
         // He initialisation; the input layer sees two live channels; the output layer
         // starts at zero, so that the untrained network is the identity on the dose
@@ -633,8 +666,10 @@ extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int 
             rc = fail(cudaGetLastError(), "to bf16");
         }
     }
+    // activations and their gradients: padded channel-group-major, borders zero for good
     const size_t B = (size_t)batch_max;
-    const size_t V1 = d->V1 * B, V2 = d->V2 * B, V3 = d->V3 * B;
+    const size_t V1 = Pcg{D, H, W}.vp() * B, V2 = Pcg{D / 2, H / 2, W / 2}.vp() * B,
+                 V3 = Pcg{D / 4, H / 4, W / 4}.vp() * B;
     struct {
         bf16** p;
         size_t n;
@@ -645,14 +680,16 @@ extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int 
                 {&d->g_cat1, V1 * 96}, {&d->g_d2, V2 * 64}, {&d->g_d2a, V2 * 64}, {&d->g_cat2, V2 * 192},
                 {&d->g_b2, V3 * 128}, {&d->g_b1, V3 * 128}, {&d->g_p2, V3 * 64}, {&d->g_e2, V2 * 64},
                 {&d->g_e2a, V2 * 64}, {&d->g_p1, V2 * 32}, {&d->g_e1, V1 * 32}, {&d->g_e1a, V1 * 32}};
-    for (auto& a : acts)
+    for (auto& a : acts) {
         if (!rc) rc = dalloc(d, a.p, a.n);
-    if (!rc) rc = dalloc(d, &d->out, V1 * 16);
+        if (!rc) rc = fail(cudaMemset(*a.p, 0, a.n * sizeof(bf16)), "memset");
+    }
+    if (!rc) rc = dalloc(d, &d->out, d->V1 * B * 16);  // FP32 output, plain channels-last
     if (!rc) rc = dalloc(d, &d->maxbits, B);
     if (!rc) rc = dalloc(d, &d->loss_acc, (size_t)1);
     if (!rc) rc = dalloc(d, &d->gcounts, (size_t)2);
     if (!rc) rc = dalloc(d, &d->gmax, (size_t)1);
-    if (!rc) rc = refresh_flips(d);
+    if (!rc) rc = refresh_weights(d);
     if (!rc) rc = fail(cudaDeviceSynchronize(), "create sync");
     if (rc) {
         free_denoiser(d);
@@ -710,8 +747,8 @@ extern "C" int sde_denoiser_train_step(sde_denoiser* d, const float* d_dose_low,
     }
     DN_TRY(forward(d, d_dose_low, d_density, batch));
     DN_TRY(fail(cudaMemsetAsync(d->loss_acc, 0, sizeof(float), d->st), "memset"));
-    k_loss<<<kBlocks, 256, 0, d->st>>>(d_dose_low, d->out, d_dose_high, target_scale, d->maxbits, d->V1, batch,
-                                       d->g_out, d->loss_acc);
+    k_loss<<<kBlocks, 256, 0, d->st>>>(d_dose_low, d->out, d_dose_high, target_scale, d->maxbits,
+                                       Pcg{d->D, d->H, d->W}, batch, d->g_out, d->loss_acc);
     DN_TRY(fail(cudaGetLastError(), "loss launch"));
     for (Layer& l : d->L) {
         DN_TRY(fail(cudaMemsetAsync(l.gw, 0, l.nw * sizeof(float), d->st), "memset"));
@@ -726,7 +763,7 @@ extern "C" int sde_denoiser_train_step(sde_denoiser* d, const float* d_dose_low,
         k_adam<<<8, 256, 0, d->st>>>(l.b32, l.gb, l.mb, l.vb, nullptr, (size_t)l.Cout, lr, b1, b2, 1e-8f, bc1, bc2);
     }
     DN_TRY(fail(cudaGetLastError(), "adam launch"));
-    DN_TRY(refresh_flips(d));
+    DN_TRY(refresh_weights(d));
     if (loss_out) {
         float h = 0.f;
         DN_TRY(fail(cudaMemcpyAsync(&h, d->loss_acc, sizeof h, cudaMemcpyDeviceToHost, d->st), "loss copy"));
@@ -767,9 +804,9 @@ extern "C" int sde_denoiser_set_params(sde_denoiser* d, const float* host, uint6
         o += l.nw;
         DN_TRY(fail(cudaMemcpy(l.b32, host + o, l.Cout * sizeof(float), cudaMemcpyHostToDevice), "params copy"));
         o += l.Cout;
-        k_to_bf16<<<kBlocks, 256>>>(l.w32, l.w16, l.nw);
+        k_to_bf16<<<kBlocks, 256, 0, d->st>>>(l.w32, l.w16, l.nw);
     }
-    DN_TRY(refresh_flips(d));
+    DN_TRY(refresh_weights(d));
     return fail(cudaDeviceSynchronize(), "set params sync");
 }
 
@@ -786,8 +823,8 @@ extern "C" int sde_denoiser_gradients(sde_denoiser* d, const float* d_dose_low, 
     }
     DN_TRY(forward(d, d_dose_low, d_density, batch));
     DN_TRY(fail(cudaMemsetAsync(d->loss_acc, 0, sizeof(float), d->st), "memset"));
-    k_loss<<<kBlocks, 256, 0, d->st>>>(d_dose_low, d->out, d_dose_high, target_scale, d->maxbits, d->V1, batch,
-                                       d->g_out, d->loss_acc);
+    k_loss<<<kBlocks, 256, 0, d->st>>>(d_dose_low, d->out, d_dose_high, target_scale, d->maxbits,
+                                       Pcg{d->D, d->H, d->W}, batch, d->g_out, d->loss_acc);
     for (Layer& l : d->L) {
         DN_TRY(fail(cudaMemsetAsync(l.gw, 0, l.nw * sizeof(float), d->st), "memset"));
         DN_TRY(fail(cudaMemsetAsync(l.gb, 0, l.Cout * sizeof(float), d->st), "memset"));

@@ -60,6 +60,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// As mma_bf16 with each descriptor given as its low and high 32-bit words (callers that
+// step only the start-address field keep the high words fixed and add to the low ones).
+__device__ __forceinline__ void mma_bf16_lohi(uint32_t d_tmem, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
+                                              uint32_t b_hi, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+        "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // The mbarrier arrives once all MMAs issued so far by this thread have completed.
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -105,6 +117,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* m) {
 // landed (the arrival is not pre-counted: the barrier's count includes it).
 __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* m) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(m)) : "memory");
+}
+
+// Arrive on the mbarrier (count 1) and add tx_bytes to the bytes its current phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, uint32_t tx_bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(tx_bytes)
+                 : "memory");
+}
+
+// Bulk copy of `bytes` contiguous bytes global -> shared by the tensor memory accelerator;
+// completion is counted in bytes on the mbarrier.  Both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* m) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(smem_addr(m))
+                 : "memory");
 }
 
 // Eight consecutive FP32 columns of this thread's tensor-memory lane.

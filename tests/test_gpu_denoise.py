@@ -27,10 +27,22 @@ def _torch_conv_ref(x, w, bias=None):
     return y.permute(0, 2, 3, 4, 1)
 
 
+def _border_is_zero(y):
+    """The one-voxel border of a padded channel-group-major tensor."""
+    inner = y.clone()
+    inner[:, :, 1:-1, 1:-1, 1:-1, :] = 0
+    return int(inner.abs().sum()) == 0
+
+
 @pytest.mark.parametrize("Cin,Cout,shape", [(16, 32, (4, 8, 8)), (32, 64, (3, 8, 16)), (96, 32, (2, 8, 8)),
                                             (192, 64, (2, 4, 16)), (64, 128, (4, 4, 8)),
-                                            (32, 32, (3, 5, 128)), (32, 96, (2, 9, 64)), (32, 16, (4, 7, 32))])
+                                            (32, 32, (3, 5, 128)), (32, 96, (2, 9, 64)), (32, 16, (4, 7, 32)),
+                                            (16, 32, (2, 3, 256))])
 def test_conv3d_forward_dgrad_wgrad_match_torch(sde_gpu, Cin, Cout, shape):
+    """Forward (FP32 and BF16 + ReLU output), data gradient (forward on dy with flipped
+    weights) and weight gradient against float64 PyTorch.  Shapes cover odd H (rows per
+    item a divisor of H), W = 128 and 256 (one and two row tiles per output row) and
+    narrower rows (tiles spanning rows and padding columns)."""
     import torch
     g = torch.Generator().manual_seed(Cin * 1000 + Cout)
     n = 2
@@ -40,12 +52,20 @@ def test_conv3d_forward_dgrad_wgrad_match_torch(sde_gpu, Cin, Cout, shape):
     b = torch.randn(Cout, generator=g).float()
     ref = _torch_conv_ref(x, w, b)
     S = sde_gpu
-    y = S.conv3d(x.cuda(), w.cuda(), b.cuda(), fp32=True)
+    xp = S.to_pcg(x.cuda())
+    y = S.conv3d(xp, w.cuda(), b.cuda(), fp32=True)
     S.denoise_status()
     assert (y.cpu().double() - ref).abs().max().item() <= 1e-5 * ref.abs().max().item() + 1e-5
-    yr = S.conv3d(x.cuda(), w.cuda(), b.cuda(), relu=True)  # BF16 output with ReLU
+    yr = S.conv3d(xp, w.cuda(), b.cuda(), relu=True)  # BF16 output with ReLU
     S.denoise_status()
-    assert (yr.cpu().double() - ref.clamp(min=0)).abs().max().item() <= 1e-2 * ref.abs().max().item()
+    assert _border_is_zero(yr)
+    assert (S.from_pcg(yr).cpu().double() - ref.clamp(min=0)).abs().max().item() <= 1e-2 * ref.abs().max().item()
+    # into channels 16 .. 16 + Cout of a wider tensor (one part of a concatenation)
+    yc = S.pcg_zeros(n, Cout + 16, D, H, W)
+    S.conv3d(xp, w.cuda(), b.cuda(), relu=True, y=yc, y_coffset=16)
+    S.denoise_status()
+    assert _border_is_zero(yc) and int(yc[:, :2].abs().sum()) == 0
+    assert torch.equal(yc[:, 2:], yr)
     # gradients by autograd in float64
     xr = x.double().permute(0, 4, 1, 2, 3).clone().requires_grad_(True)
     wt = w.double().reshape(Cout, 3, 3, 3, Cin).permute(0, 4, 1, 2, 3).clone().requires_grad_(True)
@@ -54,15 +74,15 @@ def test_conv3d_forward_dgrad_wgrad_match_torch(sde_gpu, Cin, Cout, shape):
     yt.backward(dy.double())
     dx_ref = xr.grad.permute(0, 2, 3, 4, 1)
     dw_ref = wt.grad.permute(0, 2, 3, 4, 1).reshape(Cout, 27, Cin)
-    dy_cl = dy.permute(0, 2, 3, 4, 1).contiguous().cuda()
+    dy_p = S.to_pcg(dy.permute(0, 2, 3, 4, 1).contiguous().cuda())
     if Cin <= 256:
         wd = S.conv3d_flip_weights(w.cuda())
-        dx = S.conv3d(dy_cl, wd, fp32=True)
+        dx = S.conv3d(dy_p, wd, fp32=True)
         S.denoise_status()
         assert (dx.cpu().double() - dx_ref).abs().max().item() <= 1e-5 * dx_ref.abs().max().item() + 1e-5
     if Cout <= 128:
         dw = torch.zeros(Cout, 27, Cin, dtype=torch.float32, device="cuda")
-        S.conv3d_wgrad(x.cuda(), dy_cl, dw)
+        S.conv3d_wgrad(xp, dy_p, dw)
         S.denoise_status()
         assert (dw.cpu().double() - dw_ref).abs().max().item() <= 1e-4 * dw_ref.abs().max().item() + 1e-4
 
@@ -74,13 +94,14 @@ def test_conv3d_wgrad_at_full_width_matches_float64(sde_gpu, Cin, Cout):
     Its padding positions multiply staged memory around the data by zero, so that memory
     must be zero rather than leftover bits; a leftover NaN would show here."""
     import torch
+    S = sde_gpu
     g = torch.Generator(device="cuda").manual_seed(Cin + Cout)
     D, H, W = 6, 128, 128
     x = (0.5 * torch.randn(1, D, H, W, Cin, device="cuda", generator=g)).to(torch.bfloat16)
     dy = (0.5 * torch.randn(1, D, H, W, Cout, device="cuda", generator=g)).to(torch.bfloat16)
     dw = torch.zeros(Cout, 27, Cin, device="cuda")
-    sde_gpu.conv3d_wgrad(x, dy, dw)
-    sde_gpu.denoise_status()
+    S.conv3d_wgrad(S.to_pcg(x), S.to_pcg(dy), dw)
+    S.denoise_status()
     ref = torch.nn.grad.conv3d_weight(x.double().permute(0, 4, 1, 2, 3), (Cout, Cin, 3, 3, 3),
                                       dy.double().permute(0, 4, 1, 2, 3), padding=1)
     ref = ref.permute(0, 2, 3, 4, 1).reshape(Cout, 27, Cin)
