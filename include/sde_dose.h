@@ -292,8 +292,8 @@ int sde_gemm_bf16(const void* d_A, const void* d_B, float* d_D, int M, int N, in
  * channels written from channel y_coffset on (so two producers can fill the parts of a
  * concatenation): padded channel-group-major BF16, or with y_fp32 != 0 plain
  * channels-last FP32 [batch][D*H*W][y_cstride].  Requires W <= 256, Cin a multiple of
- * 16 in [16, 192], Cout a multiple of 16 in [16, 256], 16-byte aligned d_x and d_y
- * (SDE_EINVAL otherwise).  The data gradient of the convolution is this call on dy with
+ * 16 in [16, 192], Cout a multiple of 16 in [16, 256], 16-byte aligned d_x, d_y and
+ * d_bias (SDE_EINVAL otherwise).  The data gradient of the convolution is this call on dy with
  * the weights of sde_conv3d_flip_weights.  Asynchronous; sde_denoise_status reports a
  * timed-out wait. */
 int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int W, int Cin, const void* d_w,

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
                                                    const __nv_bfloat16* __restrict__ B, float* __restrict__ D,
                                                    int M, int N, int K, unsigned int* status) {
     constexpr int KC = 64;
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
     unsigned char* sB = smem + 128 * KC * 2;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 256 * KC * 2);
@@ -274,6 +274,30 @@ __device__ __forceinline__ void conv_chunk_mma(uint32_t dacc, uint32_t a_lo, uin
     }
 }
 
+// Folded variant (one 128-voxel row per tile): per (z, y) tap pair q one MMA of N = 3 Cp whose
+// B is the three consecutive x-tap tiles of the pair and whose A is the pair's dx = 0
+// window; accumulator column block j then holds the window's product with the dx = j - 1
+// weights, and the epilogue adds the blocks shifted by one position.
+template <int TILES>
+__device__ __forceinline__ void conv_chunk_mma_fold(uint32_t dacc, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
+                                                    uint32_t b_hi, uint32_t idesc, int Cp, const int (&toff)[27],
+                                                    int P, int Yb, uint32_t first_accum) {
+    int tb[TILES];
+#pragma unroll
+    for (int m = 0; m < TILES; ++m) tb[m] = tile_base(m, true, P, Yb, 1);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const uint32_t bl = b_lo + (uint32_t)(6 * Cp * q);  // taps 3q .. 3q+2
+#pragma unroll
+        for (int m = 0; m < TILES; ++m)
+            umma::mma_bf16_lohi(dacc + (uint32_t)(3 * m * Cp), a_lo + (uint32_t)(tb[m] + toff[3 * q + 1]), a_hi, bl,
+                                b_hi, idesc, q > 0 ? 1u : first_accum);
+    }
+}
+
+// Named barrier over the 128 threads of one group of four epilogue warps.
+__device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
 // Work item of the brick convolution: (sample, Cout part, row block, z plane).
 struct BrickItem {
     int n, part, y0, z;
@@ -323,7 +347,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
     umma::fence_after_sync();
     const uint32_t tbase = *slot;
     const int nchunk = Cin >> 4;
-    const int acc_cols = b.tiles * Cp;
+    const int acc_cols = b.tiles * Cp * (b.fold ? 3 : 1);
     const int tpr = W >> 7;                          // row tiles: M tiles per output row
     const uint32_t w_chunk = (uint32_t)(27 * Cp * 32);  // bytes of one chunk's weights
     const uint32_t s_wres = s_stage0 + (uint32_t)(kPipeStages * b.stage);
@@ -368,7 +392,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
         __syncwarp();
     } else if (warp == kConvWorkers) {
         if (lane == 0) {
-            const uint32_t idesc = umma::idesc_bf16_f32(128, Cp);
+            const uint32_t idesc = umma::idesc_bf16_f32(128, b.fold ? 3 * Cp : Cp);
             int toff[27];  // tap (dz, dy, dx) -> brick position offset (dz Yb + dy) P + dx
 #pragma unroll
             for (int t = 0; t < 27; ++t) toff[t] = ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P + (t % 3 - 1);
@@ -394,29 +418,51 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                     const uint32_t b_lo = (uint32_t)b0, b_hi = (uint32_t)(b0 >> 32);
                     const uint32_t first = c > 0 ? 1u : 0u;
                     const bool rt = b.rowtile != 0;
-                    switch (b.tiles) {
+                    if (b.fold) {
+                        switch (b.tiles) {
+#define SDE_CONV_FOLD(T)                                                                             \
+    case T:                                                                                          \
+        conv_chunk_mma_fold<T>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, P, Yb, first); \
+        break;
+                            SDE_CONV_FOLD(1)
+                            SDE_CONV_FOLD(2)
+                            SDE_CONV_FOLD(3)
+                            SDE_CONV_FOLD(4)
+#undef SDE_CONV_FOLD
+                            default:
+                                for (int q = 0; q < 9; ++q)
+                                    for (int m = 0; m < b.tiles; ++m)
+                                        umma::mma_bf16_lohi(dacc + (uint32_t)(3 * m * Cp),
+                                                            a_lo + (uint32_t)(tile_base(m, true, P, Yb, 1) +
+                                                                              ((q / 3 - 1) * Yb + (q % 3 - 1)) * P),
+                                                            a_hi, b_lo + (uint32_t)(6 * Cp * q), b_hi, idesc,
+                                                            q > 0 ? 1u : first);
+                        }
+                    } else {
+                        switch (b.tiles) {
 #define SDE_CONV_TILES(T)                                                                          \
     case T:                                                                                        \
         conv_chunk_mma<T>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, rt, P, Yb, tpr, first); \
         break;
-                        SDE_CONV_TILES(1)
-                        SDE_CONV_TILES(2)
-                        SDE_CONV_TILES(3)
-                        SDE_CONV_TILES(4)
-                        SDE_CONV_TILES(5)
-                        SDE_CONV_TILES(6)
-                        SDE_CONV_TILES(7)
-                        SDE_CONV_TILES(8)
+                            SDE_CONV_TILES(1)
+                            SDE_CONV_TILES(2)
+                            SDE_CONV_TILES(3)
+                            SDE_CONV_TILES(4)
+                            SDE_CONV_TILES(5)
+                            SDE_CONV_TILES(6)
+                            SDE_CONV_TILES(7)
+                            SDE_CONV_TILES(8)
 #undef SDE_CONV_TILES
-                        default:
-                            for (int t = 0; t < 27; ++t)
-                                for (int m = 0; m < b.tiles; ++m)
-                                    umma::mma_bf16_lohi(dacc + (uint32_t)(m * Cp),
-                                                        a_lo + (uint32_t)(tile_base(m, rt, P, Yb, tpr) +
-                                                                          ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P +
-                                                                          (t % 3 - 1)),
-                                                        a_hi, b_lo + (uint32_t)(2 * Cp * t), b_hi, idesc,
-                                                        t > 0 ? 1u : first);
+                            default:
+                                for (int t = 0; t < 27; ++t)
+                                    for (int m = 0; m < b.tiles; ++m)
+                                        umma::mma_bf16_lohi(dacc + (uint32_t)(m * Cp),
+                                                            a_lo + (uint32_t)(tile_base(m, rt, P, Yb, tpr) +
+                                                                              ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P +
+                                                                              (t % 3 - 1)),
+                                                            a_hi, b_lo + (uint32_t)(2 * Cp * t), b_hi, idesc,
+                                                            t > 0 ? 1u : first);
+                        }
                     }
                     umma::mma_commit(&empty[s]);
                 }
@@ -434,7 +480,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
             return workers_all<kConvWorkerThreads>(done);
         };
         const int quarter = warp & 3;  // tensor-memory lanes 32 quarter .. + 31
+        const int grp = warp >> 2;     // warps 0-3 take the even tiles of an item, 4-7 the odd ones
         const int Gy = a.y_cstride >> 3;
+        // fold: per group two buffers (alternate tiles) of [lane quarter][Cp] column values at
+        // the quarter's edges: D[x = 32 quarter + 31][co] and D[x = 32 quarter][2 Cp + co]
+        float* xbuf = reinterpret_cast<float*>(smem + b.xch);
+        int par = 0;
         for (int item = blockIdx.x, j = 0; ok && item < b.items; item += gridDim.x, ++j) {
             const int acc = j % b.nacc, v = j / b.nacc;
             if (!worker_wait(&tfull[acc], (uint32_t)v & 1u)) {
@@ -458,29 +509,99 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                     xx = xp - 1;
                     valid = yb >= 1 && yb <= b.Ty && xp >= 1 && xp <= W;
                 }
-                for (int c = 0; c < Cp; c += 8) {
-                    float rr[8];
+                // fold: out[x] = D[x-1][co] + D[x][Cp + co] + D[x+1][2 Cp + co]; x - 1 and x + 1 of the
+                // quarter's edge lanes belong to the neighbouring quarter (another warp of the group),
+                // x = -1 and x = 128 are padding (their D is zero).  Columns move 16 at a time, all
+                // loads of a chunk in flight before one wait.
+                const uint32_t tcol = trow + (uint32_t)(m * Cp * (b.fold ? 3 : 1));
+                float* xlo = xbuf + (size_t)((grp * 2 + par) * 2) * 4 * Cp;
+                float* xhi = xlo + 4 * Cp;
+                for (int c = 0; c < Cp; c += 16) {
+                    uint32_t v[16];
                     __syncwarp();
-                    umma::tmem_ld8(trow + (uint32_t)(m * Cp + c), rr);
-                    if (valid) {
-                        for (int e = 0; e < 8; ++e) {
-                            if (a.bias) rr[e] += a.bias[cbase + c + e];
-                            if (a.relu) rr[e] = rr[e] > 0.f ? rr[e] : a.slope * rr[e];
+                    if (b.fold) {
+                        uint32_t lo[16], hi[16];
+                        umma::tmem_ld16_nowait(tcol + (uint32_t)c, lo);
+                        umma::tmem_ld16_nowait(tcol + (uint32_t)(Cp + c), v);
+                        umma::tmem_ld16_nowait(tcol + (uint32_t)(2 * Cp + c), hi);
+                        umma::tmem_wait_ld16(lo);
+                        umma::tmem_touch16(v);
+                        umma::tmem_touch16(hi);
+                        // edge lanes publish their 16 values with four 16-byte stores
+                        if (lane == 31 || lane == 0) {
+                            uint4* dst = reinterpret_cast<uint4*>((lane == 31 ? xlo : xhi) + quarter * Cp + c);
+                            const uint32_t* src = lane == 31 ? lo : hi;
+#pragma unroll
+                            for (int q4 = 0; q4 < 4; ++q4)
+                                dst[q4] = make_uint4(src[4 * q4], src[4 * q4 + 1], src[4 * q4 + 2], src[4 * q4 + 3]);
                         }
+                        uint32_t l[16], r[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            l[e] = __shfl_up_sync(0xffffffffu, lo[e], 1);
+                            r[e] = __shfl_down_sync(0xffffffffu, hi[e], 1);
+                        }
+                        group_sync(2 + grp);
+                        if (lane == 0 || lane == 31) {
+                            const bool left = lane == 0;
+                            const bool edge = left ? quarter == 0 : quarter == 3;  // padding column
+                            const int nq = left ? (quarter > 0 ? quarter - 1 : 0) : (quarter < 3 ? quarter + 1 : 3);
+                            const uint4* src = reinterpret_cast<const uint4*>((left ? xlo : xhi) + nq * Cp + c);
+                            uint32_t* dst = left ? l : r;
+#pragma unroll
+                            for (int q4 = 0; q4 < 4; ++q4) {
+                                const uint4 w = edge ? make_uint4(0u, 0u, 0u, 0u) : src[q4];
+                                dst[4 * q4] = w.x;
+                                dst[4 * q4 + 1] = w.y;
+                                dst[4 * q4 + 2] = w.z;
+                                dst[4 * q4 + 3] = w.w;
+                            }
+                        }
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            v[e] = __float_as_uint(__uint_as_float(v[e]) + (__uint_as_float(l[e]) + __uint_as_float(r[e])));
+                    } else {
+                        umma::tmem_ld16_nowait(tcol + (uint32_t)c, v);
+                        umma::tmem_wait_ld16(v);
+                    }
+                    if (valid) {
+                        float rr[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) rr[e] = __uint_as_float(v[e]);
+                        if (a.bias) {
+                            const float4* bq = reinterpret_cast<const float4*>(a.bias + cbase + c);
+#pragma unroll
+                            for (int q4 = 0; q4 < 4; ++q4) {
+                                const float4 bb = __ldg(bq + q4);
+                                rr[4 * q4] += bb.x;
+                                rr[4 * q4 + 1] += bb.y;
+                                rr[4 * q4 + 2] += bb.z;
+                                rr[4 * q4 + 3] += bb.w;
+                            }
+                        }
+                        if (a.relu)
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) rr[e] = rr[e] > 0.f ? rr[e] : a.slope * rr[e];
                         if (a.y_fp32) {
                             const size_t vox = (size_t)t.n * a.nvox + ((size_t)t.z * H + yy) * W + xx;
-                            float* yo = static_cast<float*>(a.y) + vox * a.y_cstride + a.y_coffset + cbase + c;
-                            reinterpret_cast<float4*>(yo)[0] = make_float4(rr[0], rr[1], rr[2], rr[3]);
-                            reinterpret_cast<float4*>(yo)[1] = make_float4(rr[4], rr[5], rr[6], rr[7]);
+                            float4* yo = reinterpret_cast<float4*>(static_cast<float*>(a.y) + vox * a.y_cstride +
+                                                                   a.y_coffset + cbase + c);
+                            for (int q4 = 0; q4 < 4; ++q4)
+                                yo[q4] = make_float4(rr[4 * q4], rr[4 * q4 + 1], rr[4 * q4 + 2], rr[4 * q4 + 3]);
                         } else {
-                            __nv_bfloat162 pk[4];
-                            for (int e = 0; e < 4; ++e) pk[e] = __floats2bfloat162_rn(rr[2 * e], rr[2 * e + 1]);
-                            const int gy = (a.y_coffset + cbase + c) >> 3;
-                            __nv_bfloat16* yo = static_cast<__nv_bfloat16*>(a.y) + 8 * pg.unit(t.n, Gy, gy, t.z, yy, xx);
-                            *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<uint4*>(pk);
+                            for (int h = 0; h < 2; ++h) {
+                                __nv_bfloat162 pk[4];
+                                for (int e = 0; e < 4; ++e)
+                                    pk[e] = __floats2bfloat162_rn(rr[8 * h + 2 * e], rr[8 * h + 2 * e + 1]);
+                                const int gy = (a.y_coffset + cbase + c + 8 * h) >> 3;
+                                __nv_bfloat16* yo =
+                                    static_cast<__nv_bfloat16*>(a.y) + 8 * pg.unit(t.n, Gy, gy, t.z, yy, xx);
+                                *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<uint4*>(pk);
+                            }
                         }
                     }
                 }
+                par ^= 1;
             }
             umma::fence_before_sync();
             umma::mbar_arrive(&tempty[acc]);
@@ -547,12 +668,14 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tbase = *slot;
-    const int npos_x = 3 * Yb * P;
     const int fB = (Yb + 1) * P;  // brick position under output position 0 of the item
 
     if (warp == 4) {
         if (lane == 0) {
             const uint32_t idesc = umma::idesc_bf16_f32(128, Nc, 1, 1);
+            int toff[27];  // tap (dz, dy, dx) -> brick position offset (dz Yb + dy) P + dx
+#pragma unroll
+            for (int t = 0; t < 27; ++t) toff[t] = ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P + (t % 3 - 1);
             bool ok = true;
             for (int j = 0; j < my_items && ok; ++j) {
                 const int s = j % kPipeStages, u = j / kPipeStages;
@@ -565,16 +688,20 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
                 // M/N-major: leading byte offset = next 8 positions (K), stride = next 8 channels
                 const uint64_t a0 = umma::smem_desc(st, 128, (uint32_t)b.plane_dy);
                 const uint64_t b0 = umma::smem_desc(st + (uint32_t)b.x_off, 128, (uint32_t)b.plane_x);
+                const uint32_t a_hi = (uint32_t)(a0 >> 32), b_hi = (uint32_t)(b0 >> 32);
                 for (int ks = 0; ks < b.kst; ++ks) {
-                    const uint64_t ad = a0 + (uint64_t)(16 * ks);  // 16 positions of 16 bytes
+                    const uint32_t a_lo = (uint32_t)a0 + (uint32_t)(16 * ks);  // 16 positions of 16 bytes
+                    const uint32_t b_lo = (uint32_t)b0 + (uint32_t)(fB + 16 * ks);
                     // each tap's accumulator starts at its first MMA: item 0, K step 0
                     const uint32_t accum = (j > 0 || ks > 0) ? 1u : 0u;
-                    for (int t = t0; t < t1; ++t) {
-                        const int d = ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P + (t % 3 - 1);
-                        // fB + d >= -1: one position before the brick at most (dy is zero there)
-                        const uint64_t bd = b0 + (uint64_t)(int64_t)(fB + 16 * ks + d);
-                        umma::mma_bf16(tbase + (uint32_t)((t - t0) * Nc), ad, bd, idesc, accum);
-                    }
+                    // unrolled over all taps (this pass's range selected by a uniform predicate):
+                    // one add per instruction; fB + offset >= -1, one position before the brick
+                    // at most (dy is zero there), so the start field never borrows
+#pragma unroll
+                    for (int t = 0; t < 27; ++t)
+                        if (t >= t0 && t < t1)
+                            umma::mma_bf16_lohi(tbase + (uint32_t)((t - t0) * Nc), a_lo, a_hi,
+                                                b_lo + (uint32_t)toff[t], b_hi, idesc, accum);
                 }
                 umma::mma_commit(&empty[s]);
             }
@@ -663,11 +790,15 @@ cudaError_t flip_weights_launch(const __nv_bfloat16* w, __nv_bfloat16* wd, int C
 }
 
 // Work decomposition of the pipelined brick kernel for one layer shape: output channels
-// split into parts of Cp, weights resident or streamed, and rows per item Ty (a divisor of
-// H), chosen by a cost model measured on GB300: a tcgen05.mma (M = 128, K = 16) costs ~56
-// cycles up to N = 64, 64 at N = 128 and N / 2 beyond; bulk copies of brick runs move
-// ~64 bytes per cycle per SM; the epilogue (~20 cycles per 8 columns of a tile, two warps
-// per lane quarter) overlaps the MMAs only with two accumulators.
+// split into parts of Cp, weights resident or streamed, rows per item Ty (a divisor of H),
+// and for 128-voxel rows the x-tap fold, chosen by a cost model measured on GB300: a
+// tcgen05.mma (M = 128, K = 16) costs ~56 cycles up to N = 64, 64 at N = 128 and N / 2
+// beyond, whatever its operands; bulk copies of brick runs move ~64 bytes per cycle per SM;
+// the epilogue (~20 cycles per 8 columns of a tile and lane quarter, about 2.5 times that
+// folded, two warps per quarter) overlaps the MMAs only with two accumulators; copies and
+// MMAs overlap, but not perfectly (a quarter of the shorter one shows).
+static double mma_cycles(int N) { return N <= 64 ? 56.0 : (N <= 128 ? 64.0 : N / 2.0); }
+
 static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickPlan* out, size_t* smem_out) {
     const int P = W + 2;
     const size_t smem_cap = 227 * 1024;
@@ -680,37 +811,55 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
         const int Cp = Cout / nsplit;
         if (Cp > 256) continue;
         const size_t w_bytes = (size_t)27 * Cp * 32;
-        const double mma_cyc = Cp <= 64 ? 56.0 : (Cp <= 128 ? 64.0 : Cp / 2.0);
-        for (int wres = 0; wres <= (nsplit == 1 ? 1 : 0); ++wres)
-            for (int Ty = 1; Ty <= H; ++Ty) {
-                if (H % Ty) continue;
-                const int tiles = rowtile ? Ty * (W / 128) : (Ty * P + 127) / 128;
-                if (tiles * Cp > 512) break;
-                const int nacc = 2 * tiles * Cp <= 512 ? 2 : 1;
-                const size_t run = (size_t)(Ty + 2) * P * 16;
-                const size_t plane = (3 * run + 127) / 128 * 128;
-                // flat tiles read up to 128 positions past the end of the second plane
-                const size_t w_off = (128 + 2 * plane + (rowtile ? 0 : 2048) + 127) / 128 * 128;
-                const size_t stage = wres ? w_off : (w_off + w_bytes + 127) / 128 * 128;
-                const size_t smem = kPipeHeader + kPipeStages * stage + (wres ? nchunk * w_bytes : 0);
-                if (smem > smem_cap || plane >= (1u << 18)) break;
-                const double mma = (double)nchunk * 27 * tiles * mma_cyc;
-                const double load = (double)nchunk * (6 * run + (wres ? 0 : w_bytes)) / 64.0;
-                const double epi = tiles * (Cp / 8.0) * 10.0;
-                // copies and MMAs overlap, but not perfectly: a quarter of the shorter one shows
-                double item = (mma > load ? mma : load) + 0.25 * (mma > load ? load : mma);
-                item = nacc == 2 ? (item > epi ? item : epi) : item + epi;
-                const double cost = item / ((double)Ty * W) * nsplit;  // per output voxel, all parts
-                if (cost < best) {
-                    best = cost;
-                    found = true;
-                    int tcols = 32;
-                    while (tcols < nacc * tiles * Cp) tcols <<= 1;
-                    *out = BrickPlan{Ty,   tiles, rowtile ? 1 : 0, H / Ty, P,     Ty + 2,     Cp,    nsplit,
-                                     (int)plane, (int)w_off, wres, (int)stage, nacc, tcols, batch * nsplit * (H / Ty) * D};
-                    *smem_out = smem;
+        for (int fold = 0; fold <= (W == 128 && 3 * Cp <= 256 ? 1 : 0); ++fold)
+            for (int wres = 0; wres <= (nsplit == 1 ? 1 : 0); ++wres)
+                for (int Ty = 1; Ty <= H; ++Ty) {
+                    if (H % Ty) continue;
+                    const int tiles = rowtile ? Ty * (W / 128) : (Ty * P + 127) / 128;
+                    const int cols = tiles * Cp * (fold ? 3 : 1);  // accumulator columns per item
+                    if (cols > 512) break;
+                    const int nacc = 2 * cols <= 512 ? 2 : 1;
+                    const size_t run = (size_t)(Ty + 2) * P * 16;
+                    const size_t plane = (3 * run + 127) / 128 * 128;
+                    // flat tiles read up to 128 positions past the end of the second plane
+                    const size_t w_off = (128 + 2 * plane + (rowtile ? 0 : 2048) + 127) / 128 * 128;
+                    const size_t stage = wres ? w_off : (w_off + w_bytes + 127) / 128 * 128;
+                    const size_t xch = kPipeHeader + kPipeStages * stage + (wres ? nchunk * w_bytes : 0);
+                    const size_t smem = xch + (fold ? (size_t)128 * Cp : 0);
+                    if (smem > smem_cap || plane >= (1u << 18)) break;
+                    const double mma = (double)nchunk * tiles * (fold ? 9 * mma_cycles(3 * Cp) : 27 * mma_cycles(Cp));
+                    const double load = (double)nchunk * (6 * run + (wres ? 0 : w_bytes)) / 64.0;
+                    const double epi = tiles * (Cp / 8.0) * (fold ? 25.0 : 10.0);
+                    double item = (mma > load ? mma : load) + 0.25 * (mma > load ? load : mma);
+                    item = nacc == 2 ? (item > epi ? item : epi) : item + epi;
+                    const double cost = item / ((double)Ty * W) * nsplit;  // per output voxel, all parts
+                    if (cost < best) {
+                        best = cost;
+                        found = true;
+                        int tcols = 32;
+                        while (tcols < nacc * cols) tcols <<= 1;
+                        BrickPlan bp{};
+                        bp.Ty = Ty;
+                        bp.tiles = tiles;
+                        bp.rowtile = rowtile ? 1 : 0;
+                        bp.fold = fold;
+                        bp.nyb = H / Ty;
+                        bp.P = P;
+                        bp.Yb = Ty + 2;
+                        bp.Cp = Cp;
+                        bp.nsplit = nsplit;
+                        bp.plane = (int)plane;
+                        bp.w_off = (int)w_off;
+                        bp.wres = wres;
+                        bp.stage = (int)stage;
+                        bp.nacc = nacc;
+                        bp.xch = (int)xch;
+                        bp.tcols = tcols;
+                        bp.items = batch * nsplit * (H / Ty) * D;
+                        *out = bp;
+                        *smem_out = smem;
+                    }
                 }
-            }
     }
     return found;
 }
@@ -825,9 +974,10 @@ extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int 
                                   const float* d_bias, int Cout, void* d_y, int y_cstride, int y_coffset,
                                   int y_fp32, int relu, void* stream) {
     if (!d_x || !d_w || !d_y || !conv_shape_ok(D, H, W, Cin, Cout, batch) || y_cstride < Cout + y_coffset ||
-        y_coffset < 0 || (y_coffset % 8) || (y_cstride % 8) || (((uintptr_t)d_x | (uintptr_t)d_y) & 15)) {
+        y_coffset < 0 || (y_coffset % 8) || (y_cstride % 8) ||
+        (((uintptr_t)d_x | (uintptr_t)d_y | (uintptr_t)d_bias) & 15)) {
         set_last_error("sde_conv3d_forward: need W <= 256, Cin in 16..192 and Cout in 16..256 (multiples of 16), "
-                       "y_cstride >= Cout + y_coffset, both multiples of 8, 16-byte aligned x and y");
+                       "y_cstride >= Cout + y_coffset, both multiples of 8, 16-byte aligned x, y and bias");
         return SDE_EINVAL;
     }
     unsigned int* d_status = nullptr;

@@ -47,6 +47,7 @@ struct BrickPlan {
     int Ty;       // output rows (y) per work item, all x of one z plane; divides H
     int tiles;    // M tiles of 128 positions per work item
     int rowtile;  // 1: W is a multiple of 128 and each tile is 128 x of one output row
+    int fold;     // 1 (row tiles only): the three x taps of a (z, y) tap pair in one MMA of N = 3 Cp
     int nyb;      // H / Ty
     int P;        // W + 2: brick row pitch in positions
     int Yb;       // Ty + 2: brick rows per plane
@@ -57,7 +58,8 @@ struct BrickPlan {
     int wres;     // 1: all chunks' weights stay resident after the stages (loaded once per CTA)
     int stage;    // bytes per pipeline stage (brick chunk + weight chunk)
     int nacc;     // tensor-memory accumulators (2: epilogue overlaps the next item)
-    int tcols;    // tensor-memory columns allocated (power of two >= nacc x tiles x Cp)
+    int xch;      // fold: offset of the epilogue's boundary-exchange buffer in shared memory
+    int tcols;    // tensor-memory columns allocated (power of two >= nacc x tiles x Cp x (fold ? 3 : 1))
     int items;    // batch x nsplit x nyb x D
 };
 

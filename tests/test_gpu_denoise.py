@@ -37,11 +37,13 @@ def _border_is_zero(y):
 @pytest.mark.parametrize("Cin,Cout,shape", [(16, 32, (4, 8, 8)), (32, 64, (3, 8, 16)), (96, 32, (2, 8, 8)),
                                             (192, 64, (2, 4, 16)), (64, 128, (4, 4, 8)),
                                             (32, 32, (3, 5, 128)), (32, 96, (2, 9, 64)), (32, 16, (4, 7, 32)),
-                                            (16, 32, (2, 3, 256))])
+                                            (16, 32, (2, 3, 256)), (32, 96, (2, 4, 128)), (16, 32, (2, 6, 128)),
+                                            (32, 16, (3, 4, 128))])
 def test_conv3d_forward_dgrad_wgrad_match_torch(sde_gpu, Cin, Cout, shape):
     """Forward (FP32 and BF16 + ReLU output), data gradient (forward on dy with flipped
     weights) and weight gradient against float64 PyTorch.  Shapes cover odd H (rows per
-    item a divisor of H), W = 128 and 256 (one and two row tiles per output row) and
+    item a divisor of H), W = 128 (row tiles with the three x taps folded into one MMA, at
+    16, 32 and 48 output channels per part) and 256 (two row tiles per output row) and
     narrower rows (tiles spanning rows and padding columns)."""
     import torch
     g = torch.Generator().manual_seed(Cin * 1000 + Cout)
