@@ -584,10 +584,17 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                             for (int e = 0; e < 16; ++e) rr[e] = rr[e] > 0.f ? rr[e] : a.slope * rr[e];
                         if (a.y_fp32) {
                             const size_t vox = (size_t)t.n * a.nvox + ((size_t)t.z * H + yy) * W + xx;
-                            float4* yo = reinterpret_cast<float4*>(static_cast<float*>(a.y) + vox * a.y_cstride +
-                                                                   a.y_coffset + cbase + c);
-                            for (int q4 = 0; q4 < 4; ++q4)
-                                yo[q4] = make_float4(rr[4 * q4], rr[4 * q4 + 1], rr[4 * q4 + 2], rr[4 * q4 + 3]);
+                            if (a.y_keep) {  // leading channels only (the first chunk of part 0)
+                                if (cbase + c == 0)
+#pragma unroll
+                                    for (int e = 0; e < 16; ++e)  // constant indices keep rr in registers
+                                        if (e < a.y_keep) static_cast<float*>(a.y)[vox * a.y_keep + e] = rr[e];
+                            } else {
+                                float4* yo = reinterpret_cast<float4*>(static_cast<float*>(a.y) + vox * a.y_cstride +
+                                                                       a.y_coffset + cbase + c);
+                                for (int q4 = 0; q4 < 4; ++q4)
+                                    yo[q4] = make_float4(rr[4 * q4], rr[4 * q4 + 1], rr[4 * q4 + 2], rr[4 * q4 + 3]);
+                            }
                         } else {
                             for (int h = 0; h < 2; ++h) {
                                 __nv_bfloat162 pk[4];
@@ -1008,6 +1015,7 @@ extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int 
     a.y_cstride = y_cstride;
     a.y_coffset = y_coffset;
     a.y_fp32 = y_fp32;
+    a.y_keep = 0;
     a.relu = relu;
     a.slope = 0.f;
     a.status = d_status;

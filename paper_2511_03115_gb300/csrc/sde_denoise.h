@@ -37,6 +37,7 @@ struct ConvArgs {
     int D, H, W, Cin, Cout;
     int nvox;  // D*H*W
     int y_cstride, y_coffset, y_fp32, relu;
+    int y_keep;   // FP32 output only: > 0 stores just output channels 0 .. y_keep-1 (<= 16), dense [n][D H W][y_keep]
     float slope;  // with relu: y = x > 0 ? x : slope * x (0: ReLU, > 0: leaky ReLU)
     unsigned int* status;
 };

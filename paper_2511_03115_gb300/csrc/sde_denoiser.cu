@@ -88,9 +88,11 @@ __device__ __forceinline__ void st8(bf16* p, const float (&f)[8]) {
 
 // Two resolutions: the fine grid F (D, H, W even) and the coarse grid C = F / 2.  The
 // resampling kernels run one thread per (coarse voxel, 8-channel group) on the launch grid
-// (ceil(Wc G / 256), Hc, Dc batch) with 256 threads, G = C/8 a power of two, and move 16
-// bytes per access: no integer division per element.  Channel counts, strides and offsets
-// are multiples of 8 (offsets and strides below are in channels).
+// (ceil(Wc G / 256), Hc, Dc batch) with 256 threads, x fastest across threads, and move 16
+// bytes per access: a warp reads 32 consecutive coarse voxels of one group (512 contiguous
+// bytes) and writes or reads their fine children as 32-byte pairs along x (1 KB contiguous
+// per (dz, dy)).  Channel counts, strides and offsets are multiples of 8 (offsets and
+// strides below are in channels).
 struct Grid2 {
     Pcg F, C;
 };
@@ -102,8 +104,8 @@ struct CoarseIdx {
 __device__ __forceinline__ bool coarse_idx(const Grid2& g, int G, CoarseIdx& c) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.C.W * G) return false;
-    c.q = t & (G - 1);
-    c.xc = t >> (__ffs(G) - 1);
+    c.q = t / g.C.W;
+    c.xc = t - c.q * g.C.W;
     c.yc = blockIdx.y;
     c.zc = blockIdx.z % g.C.D;
     c.b = blockIdx.z / g.C.D;
@@ -175,10 +177,10 @@ __global__ void k_upsample2_bwd(const bf16* __restrict__ din, int ics, int ico, 
     st8(dout + 8 * coarse_unit(g, c, C >> 3, c.q), acc);
 }
 
-// Launch geometry of the coarse-voxel kernels (C/8 must be a power of two).
+// Launch geometry of the coarse-voxel kernels.
 static bool coarse_grid(const Grid2& g, int C, int batch, dim3& grid) {
     const int G = C >> 3;
-    if (C % 8 || G <= 0 || (G & (G - 1)) || (g.F.D | g.F.H | g.F.W) & 1) return false;
+    if (C % 8 || G <= 0 || (g.F.D | g.F.H | g.F.W) & 1) return false;
     const long long z = (long long)g.C.D * batch;
     if (z > 65535 || g.C.H > 65535) return false;
     grid = dim3((unsigned)((g.C.W * G + 255) / 256), (unsigned)g.C.H, (unsigned)z);
@@ -238,7 +240,7 @@ __global__ void k_loss(const float* __restrict__ dose_low, const float* __restri
         const int v = (int)(i - (size_t)b * V);
         const float s = scale_of(maxbits, b);
         const float t = target[i] * target_scale * s;
-        const float diff = dose_low[i] * s + out[i * 16] - t;
+        const float diff = dose_low[i] * s + out[i] - t;
         const float w = 1.f / (fabsf(t) + kLossKappa);
         local += w * diff * diff;
         __nv_bfloat162 p[4];
@@ -257,7 +259,7 @@ __global__ void k_output(const float* __restrict__ dose_low, const float* __rest
     const size_t n = V * batch;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float s = scale_of(maxbits, (int)(i / V));
-        dose_out[i] = dose_low[i] + out[i * 16] / s;
+        dose_out[i] = dose_low[i] + out[i] / s;
     }
 }
 
@@ -435,7 +437,7 @@ struct HostRng {
 // One convolution of layer l at grid D x H x W: the forward one, or with flip the data
 // gradient (dy convolved with the flipped weights, Cin and Cout exchanged).
 int conv(sde_denoiser* d, const bf16* x, int batch, int D, int H, int W, const Layer& l, bool flip, int Cout,
-         void* y, int cstride, int coffset, bool fp32, bool relu, const float* bias) {
+         void* y, int cstride, int coffset, bool fp32, bool relu, const float* bias, int keep = 0) {
     unsigned int* status = nullptr;
     int rc = fail(denoise_status_word(&status), "status word");
     if (rc) return rc;
@@ -454,6 +456,7 @@ int conv(sde_denoiser* d, const bf16* x, int batch, int D, int H, int W, const L
     a.y_cstride = cstride;
     a.y_coffset = coffset;
     a.y_fp32 = fp32 ? 1 : 0;
+    a.y_keep = keep;
     a.relu = relu ? 1 : 0;
     a.slope = kLeak;
     a.status = status;
@@ -525,7 +528,8 @@ int forward(sde_denoiser* d, const float* dose_low, const float* rho, int batch)
     k_upsample2<<<grid, 256, 0, d->st>>>(d->d2, 64, g1, d->cat1, 96, 0);
     DN_TRY(conv(d, d->cat1, batch, D, H, W, L[8], false, 32, d->d1a, 32, 0, false, true, L[8].b32));
     DN_TRY(conv(d, d->d1a, batch, D, H, W, L[9], false, 32, d->d1, 32, 0, false, true, L[9].b32));
-    DN_TRY(conv(d, d->d1, batch, D, H, W, L[10], false, 16, d->out, 16, 0, true, false, L[10].b32));
+    // only output channel 0 is the network's output (the other 15 of the padded layer are unused)
+    DN_TRY(conv(d, d->d1, batch, D, H, W, L[10], false, 16, d->out, 16, 0, true, false, L[10].b32, 1));
     return fail(cudaGetLastError(), "forward launch");
 }
 
@@ -684,7 +688,7 @@ extern "C" int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int 
         if (!rc) rc = dalloc(d, a.p, a.n);
         if (!rc) rc = fail(cudaMemset(*a.p, 0, a.n * sizeof(bf16)), "memset");
     }
-    if (!rc) rc = dalloc(d, &d->out, d->V1 * B * 16);  // FP32 output, plain channels-last
+    if (!rc) rc = dalloc(d, &d->out, d->V1 * B);  // FP32 output channel 0, plain [n][voxel]
     if (!rc) rc = dalloc(d, &d->maxbits, B);
     if (!rc) rc = dalloc(d, &d->loss_acc, (size_t)1);
     if (!rc) rc = dalloc(d, &d->gcounts, (size_t)2);
