@@ -356,7 +356,6 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
     if (warp == kConvWorkers + 1) {
         if (lane == 0) {  // producer
             const int Gin = Cin >> 3;
-            const uint32_t run = (uint32_t)(Yb * P * 16);  // one (channel group, plane) part of a brick
             int k = 0;
             if (b.wres) {
                 umma::mbar_arrive_expect_tx(wfull, (uint32_t)nchunk * w_chunk);
@@ -366,6 +365,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
             for (int item = blockIdx.x; ok && item < b.items; item += gridDim.x) {
                 const BrickItem t = brick_item(b, D, item);
                 const __nv_bfloat16* wpart = a.wpk + (size_t)t.part * nchunk * 27 * Cp * 16;
+                // one (channel group, plane) part of the brick: padded rows y0 .. y0+Yb-1, fewer in a
+                // last row block that passes H (the rows it leaves stale feed only outputs y >= H,
+                // which the epilogue drops)
+                const int rows = Yb < H + 2 - t.y0 ? Yb : H + 2 - t.y0;
+                const uint32_t run = (uint32_t)(rows * P * 16);
+                const uint32_t slot = (uint32_t)(Yb * P * 16);
                 for (int c = 0; c < nchunk; ++c, ++k) {
                     const int s = k % kPipeStages, u = k / kPipeStages;
                     if (u >= 1 && !pipe_wait(&empty[s], (uint32_t)(u - 1) & 1u, abort_flag)) {
@@ -376,7 +381,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                     umma::mbar_arrive_expect_tx(&full[s], 6u * run + (b.wres ? 0u : w_chunk));
                     for (int gg = 0; gg < 2; ++gg)
                         for (int zb = 0; zb < 3; ++zb)  // rows y0-1 .. y0+Ty of plane z+zb-1, columns -1 .. W
-                            umma::bulk_g2s(st + 128u + (uint32_t)(gg * b.plane) + (uint32_t)zb * run,
+                            umma::bulk_g2s(st + 128u + (uint32_t)(gg * b.plane) + (uint32_t)zb * slot,
                                            a.x + 8 * pg.unit(t.n, Gin, 2 * c + gg, t.z + zb - 1, t.y0 - 1, -1), run,
                                            &full[s]);
                     if (!b.wres)
@@ -502,12 +507,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                 if (b.rowtile) {
                     yy = t.y0 + m / tpr;
                     xx = 128 * (m % tpr) + 32 * quarter + lane;
+                    valid = yy < H;
                 } else {
                     const int q = P + 128 * m + 32 * quarter + lane;  // position in brick plane zb = 1
                     const int yb = q / P, xp = q - yb * P;
                     yy = t.y0 + yb - 1;
                     xx = xp - 1;
-                    valid = yb >= 1 && yb <= b.Ty && xp >= 1 && xp <= W;
+                    valid = yb >= 1 && yb <= b.Ty && xp >= 1 && xp <= W && yy < H;
                 }
                 // fold: out[x] = D[x-1][co] + D[x][Cp + co] + D[x+1][2 Cp + co]; x - 1 and x + 1 of the
                 // quarter's edge lanes belong to the neighbouring quarter (another warp of the group),
@@ -797,7 +803,8 @@ cudaError_t flip_weights_launch(const __nv_bfloat16* w, __nv_bfloat16* wd, int C
 }
 
 // Work decomposition of the pipelined brick kernel for one layer shape: output channels
-// split into parts of Cp, weights resident or streamed, rows per item Ty (a divisor of H),
+// split into parts of Cp, weights resident or streamed, rows per item Ty (the last row block
+// may pass H),
 // and for 128-voxel rows the x-tap fold, chosen by a cost model measured on GB300: a
 // tcgen05.mma (M = 128, K = 16) costs ~56 cycles up to N = 64, 64 at N = 128 and N / 2
 // beyond, whatever its operands; bulk copies of brick runs move ~64 bytes per cycle per SM;
@@ -821,7 +828,7 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
         for (int fold = 0; fold <= (W == 128 && 3 * Cp <= 256 ? 1 : 0); ++fold)
             for (int wres = 0; wres <= (nsplit == 1 ? 1 : 0); ++wres)
                 for (int Ty = 1; Ty <= H; ++Ty) {
-                    if (H % Ty) continue;
+                    const int nyb = (H + Ty - 1) / Ty;
                     const int tiles = rowtile ? Ty * (W / 128) : (Ty * P + 127) / 128;
                     const int cols = tiles * Cp * (fold ? 3 : 1);  // accumulator columns per item
                     if (cols > 512) break;
@@ -839,7 +846,7 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
                     const double epi = tiles * (Cp / 8.0) * (fold ? 25.0 : 10.0);
                     double item = (mma > load ? mma : load) + 0.25 * (mma > load ? load : mma);
                     item = nacc == 2 ? (item > epi ? item : epi) : item + epi;
-                    const double cost = item / ((double)Ty * W) * nsplit;  // per output voxel, all parts
+                    const double cost = item * nyb / ((double)H * W) * nsplit;  // per output voxel, all parts
                     if (cost < best) {
                         best = cost;
                         found = true;
@@ -850,7 +857,7 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
                         bp.tiles = tiles;
                         bp.rowtile = rowtile ? 1 : 0;
                         bp.fold = fold;
-                        bp.nyb = H / Ty;
+                        bp.nyb = nyb;
                         bp.P = P;
                         bp.Yb = Ty + 2;
                         bp.Cp = Cp;
@@ -862,7 +869,7 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
                         bp.nacc = nacc;
                         bp.xch = (int)xch;
                         bp.tcols = tcols;
-                        bp.items = batch * nsplit * (H / Ty) * D;
+                        bp.items = batch * nsplit * nyb * D;
                         *out = bp;
                         *smem_out = smem;
                     }

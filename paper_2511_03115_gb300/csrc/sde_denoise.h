@@ -45,11 +45,11 @@ struct ConvArgs {
 // Work decomposition and shared-memory layout of the pipelined brick convolution
 // (host-chosen per layer shape).  A work item is (sample, Cout part, row block, z plane).
 struct BrickPlan {
-    int Ty;       // output rows (y) per work item, all x of one z plane; divides H
+    int Ty;       // output rows (y) per work item, all x of one z plane (the last block may pass H)
     int tiles;    // M tiles of 128 positions per work item
     int rowtile;  // 1: W is a multiple of 128 and each tile is 128 x of one output row
     int fold;     // 1 (row tiles only): the three x taps of a (z, y) tap pair in one MMA of N = 3 Cp
-    int nyb;      // H / Ty
+    int nyb;      // ceil(H / Ty)
     int P;        // W + 2: brick row pitch in positions
     int Yb;       // Ty + 2: brick rows per plane
     int Cp;       // output channels per work item
