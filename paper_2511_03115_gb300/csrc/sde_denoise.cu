@@ -805,13 +805,16 @@ cudaError_t flip_weights_launch(const __nv_bfloat16* w, __nv_bfloat16* wd, int C
 // Work decomposition of the pipelined brick kernel for one layer shape: output channels
 // split into parts of Cp, weights resident or streamed, rows per item Ty (the last row block
 // may pass H),
-// and for 128-voxel rows the x-tap fold, chosen by a cost model measured on GB300: a
-// tcgen05.mma (M = 128, K = 16) costs ~56 cycles up to N = 64, 64 at N = 128 and N / 2
-// beyond, whatever its operands; bulk copies of brick runs move ~64 bytes per cycle per SM;
-// the epilogue (~20 cycles per 8 columns of a tile and lane quarter, about 2.5 times that
-// folded, two warps per quarter) overlaps the MMAs only with two accumulators; copies and
-// MMAs overlap, but not perfectly (a quarter of the shorter one shows).
-static double mma_cycles(int N) { return N <= 64 ? 56.0 : (N <= 128 ? 64.0 : N / 2.0); }
+// and for 128-voxel rows the x-tap fold, chosen by a cost model calibrated on GB300 with
+// per-role cycle counters in this kernel: a tcgen05.mma (M = 128, K = 16) takes ~64 cycles
+// of the issuing thread at N = 32, ~85 at N = 64, ~90 at N = 96 and about N / 2 from
+// N = 192; bulk copies of brick runs move ~64 bytes per cycle per SM; the epilogue takes
+// ~700 cycles per tile and 8 columns (~850 folded) on each of its two warp groups and
+// overlaps the MMAs only with two accumulators; copies and MMAs overlap, but not perfectly
+// (a quarter of the shorter one shows).
+static double mma_cycles(int N) {
+    return N <= 32 ? 64.0 : (N <= 64 ? 85.0 : (N <= 96 ? 90.0 : (N <= 192 ? 96.0 + (N - 128) / 2.0 : N / 2.0)));
+}
 
 static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickPlan* out, size_t* smem_out) {
     const int P = W + 2;
@@ -826,7 +829,7 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
         if (Cp > 256) continue;
         const size_t w_bytes = (size_t)27 * Cp * 32;
         for (int fold = 0; fold <= (W == 128 && 3 * Cp <= 256 ? 1 : 0); ++fold)
-            for (int wres = 0; wres <= (nsplit == 1 ? 1 : 0); ++wres)
+            for (int wres = nsplit == 1 ? 1 : 0; wres >= 0; --wres)  // ties keep the weights resident
                 for (int Ty = 1; Ty <= H; ++Ty) {
                     const int nyb = (H + Ty - 1) / Ty;
                     const int tiles = rowtile ? Ty * (W / 128) : (Ty * P + 127) / 128;
@@ -843,7 +846,7 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
                     if (smem > smem_cap || plane >= (1u << 18)) break;
                     const double mma = (double)nchunk * tiles * (fold ? 9 * mma_cycles(3 * Cp) : 27 * mma_cycles(Cp));
                     const double load = (double)nchunk * (6 * run + (wres ? 0 : w_bytes)) / 64.0;
-                    const double epi = tiles * (Cp / 8.0) * (fold ? 25.0 : 10.0);
+                    const double epi = ((tiles + 1) / 2) * (Cp / 8.0) * (fold ? 850.0 : 700.0);
                     double item = (mma > load ? mma : load) + 0.25 * (mma > load ? load : mma);
                     item = nacc == 2 ? (item > epi ? item : epi) : item + epi;
                     const double cost = item * nyb / ((double)H * W) * nsplit;  // per output voxel, all parts
