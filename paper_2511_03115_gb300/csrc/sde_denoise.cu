@@ -609,7 +609,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                                 const int gy = (a.y_coffset + cbase + c + 8 * h) >> 3;
                                 __nv_bfloat16* yo =
                                     static_cast<__nv_bfloat16*>(a.y) + 8 * pg.unit(t.n, Gy, gy, t.z, yy, xx);
-                                *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<uint4*>(pk);
+                                const uint4 val = *reinterpret_cast<uint4*>(pk);
+                                *reinterpret_cast<uint4*>(yo) = val;
+                                if (a.y_up) {  // the eight children on the doubled grid
+                                    const Pcg pf{2 * D, 2 * H, 2 * W};
+                                    const int gu = (a.y_up_coffset + cbase + c + 8 * h) >> 3;
+                                    __nv_bfloat16* yu = static_cast<__nv_bfloat16*>(a.y_up);
+#pragma unroll
+                                    for (int d = 0; d < 8; ++d)
+                                        *reinterpret_cast<uint4*>(
+                                            yu + 8 * pf.unit(t.n, a.y_up_cstride >> 3, gu, 2 * t.z + (d >> 2),
+                                                             2 * yy + ((d >> 1) & 1), 2 * xx + (d & 1))) = val;
+                                }
                             }
                         }
                     }
@@ -1026,6 +1037,8 @@ extern "C" int sde_conv3d_forward(const void* d_x, int batch, int D, int H, int 
     a.y_coffset = y_coffset;
     a.y_fp32 = y_fp32;
     a.y_keep = 0;
+    a.y_up = nullptr;
+    a.y_up_cstride = a.y_up_coffset = 0;
     a.relu = relu;
     a.slope = 0.f;
     a.status = d_status;

@@ -38,6 +38,11 @@ struct ConvArgs {
     int nvox;  // D*H*W
     int y_cstride, y_coffset, y_fp32, relu;
     int y_keep;   // FP32 output only: > 0 stores just output channels 0 .. y_keep-1 (<= 16), dense [n][D H W][y_keep]
+    // BF16 output only, optional: also store every output voxel to its eight children in a padded
+    // channel-group-major tensor on the grid 2D x 2H x 2W (nearest-neighbour upsampling), at
+    // channel y_up_coffset of y_up_cstride
+    void* y_up;
+    int y_up_cstride, y_up_coffset;
     float slope;  // with relu: y = x > 0 ? x : slope * x (0: ReLU, > 0: leaky ReLU)
     unsigned int* status;
 };

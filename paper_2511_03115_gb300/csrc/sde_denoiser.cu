@@ -153,17 +153,8 @@ __global__ void k_avgpool2_bwd(const bf16* __restrict__ dout, const bf16* __rest
     }
 }
 
-// out (channels oco .. oco+C of ocs, fine) = in[parent] (C channels, coarse): nearest-
-// neighbour upsampling; each coarse group is read once and written to its 8 children.
-__global__ void k_upsample2(const bf16* __restrict__ in, int C, Grid2 g, bf16* __restrict__ out, int ocs, int oco) {
-    CoarseIdx c;
-    if (!coarse_idx(g, C >> 3, c)) return;
-    const uint4 val = *reinterpret_cast<const uint4*>(in + 8 * coarse_unit(g, c, C >> 3, c.q));
-    for (int d = 0; d < 8; ++d)
-        *reinterpret_cast<uint4*>(out + 8 * fine_unit(g, c, ocs >> 3, (oco >> 3) + c.q, d)) = val;
-}
-
-// dout (C channels, coarse) = sum over the 8 children of din (channels ico .. ico+C of ics)
+// dout (C channels, coarse) = sum over the 8 children of din (channels ico .. ico+C of ics):
+// the adjoint of the nearest-neighbour upsampling that the convolution epilogue does
 __global__ void k_upsample2_bwd(const bf16* __restrict__ din, int ics, int ico, int C, Grid2 g,
                                 bf16* __restrict__ dout) {
     CoarseIdx c;
@@ -437,7 +428,8 @@ struct HostRng {
 // One convolution of layer l at grid D x H x W: the forward one, or with flip the data
 // gradient (dy convolved with the flipped weights, Cin and Cout exchanged).
 int conv(sde_denoiser* d, const bf16* x, int batch, int D, int H, int W, const Layer& l, bool flip, int Cout,
-         void* y, int cstride, int coffset, bool fp32, bool relu, const float* bias, int keep = 0) {
+         void* y, int cstride, int coffset, bool fp32, bool relu, const float* bias, int keep = 0,
+         bf16* up = nullptr, int up_cstride = 0, int up_coffset = 0) {
     unsigned int* status = nullptr;
     int rc = fail(denoise_status_word(&status), "status word");
     if (rc) return rc;
@@ -457,6 +449,9 @@ int conv(sde_denoiser* d, const bf16* x, int batch, int D, int H, int W, const L
     a.y_coffset = coffset;
     a.y_fp32 = fp32 ? 1 : 0;
     a.y_keep = keep;
+    a.y_up = up;
+    a.y_up_cstride = up_cstride;
+    a.y_up_coffset = up_coffset;
     a.relu = relu ? 1 : 0;
     a.slope = kLeak;
     a.status = status;
@@ -519,13 +514,12 @@ int forward(sde_denoiser* d, const float* dose_low, const float* rho, int batch)
     coarse_grid(g2, 64, batch, grid);
     k_avgpool2<<<grid, 256, 0, d->st>>>(d->cat2, 192, 128, 64, g2, d->p2);
     DN_TRY(conv(d, d->p2, batch, D3, H3, W3, L[4], false, 128, d->b1, 128, 0, false, true, L[4].b32));
-    DN_TRY(conv(d, d->b1, batch, D3, H3, W3, L[5], false, 128, d->b2, 128, 0, false, true, L[5].b32));
-    coarse_grid(g2, 128, batch, grid);
-    k_upsample2<<<grid, 256, 0, d->st>>>(d->b2, 128, g2, d->cat2, 192, 0);
+    // b2, and its nearest-neighbour upsampling into channels 0..127 of cat2, from one epilogue
+    DN_TRY(conv(d, d->b1, batch, D3, H3, W3, L[5], false, 128, d->b2, 128, 0, false, true, L[5].b32, 0, d->cat2,
+                192, 0));
     DN_TRY(conv(d, d->cat2, batch, D2, H2, W2, L[6], false, 64, d->d2a, 64, 0, false, true, L[6].b32));
-    DN_TRY(conv(d, d->d2a, batch, D2, H2, W2, L[7], false, 64, d->d2, 64, 0, false, true, L[7].b32));
-    coarse_grid(g1, 64, batch, grid);
-    k_upsample2<<<grid, 256, 0, d->st>>>(d->d2, 64, g1, d->cat1, 96, 0);
+    DN_TRY(conv(d, d->d2a, batch, D2, H2, W2, L[7], false, 64, d->d2, 64, 0, false, true, L[7].b32, 0, d->cat1,
+                96, 0));
     DN_TRY(conv(d, d->cat1, batch, D, H, W, L[8], false, 32, d->d1a, 32, 0, false, true, L[8].b32));
     DN_TRY(conv(d, d->d1a, batch, D, H, W, L[9], false, 32, d->d1, 32, 0, false, true, L[9].b32));
     // only output channel 0 is the network's output (the other 15 of the padded layer are unused)
