@@ -653,6 +653,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
 // NaN or Inf: the few positions B reads just outside the staged data (before the first
 // plane, between planes, after the last) are zeroed once at start and never written.
 // ----------------------------------------------------------------------------
+// The weight-gradient MMAs of one K step for taps T0 .. T1-1 (fully unrolled): the
+// accumulator of tap t starts at column (t - T0) Nc, B's start field is the K step's plus
+// the tap's brick offset.
+template <int T0, int T1>
+__device__ __forceinline__ void wgrad_taps(uint32_t tbase, int Nc, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
+                                           uint32_t b_hi, uint32_t idesc, uint32_t accum, const int (&toff)[27]) {
+#pragma unroll
+    for (int t = T0; t < T1; ++t)
+        umma::mma_bf16_lohi(tbase + (uint32_t)((t - T0) * Nc), a_lo, a_hi, b_lo + (uint32_t)toff[t], b_hi, idesc,
+                            accum);
+}
+
 __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -718,14 +730,21 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
                     const uint32_t b_lo = (uint32_t)b0 + (uint32_t)(fB + 16 * ks);
                     // each tap's accumulator starts at its first MMA: item 0, K step 0
                     const uint32_t accum = (j > 0 || ks > 0) ? 1u : 0u;
-                    // unrolled over all taps (this pass's range selected by a uniform predicate):
-                    // one add per instruction; fB + offset >= -1, one position before the brick
-                    // at most (dy is zero there), so the start field never borrows
-#pragma unroll
-                    for (int t = 0; t < 27; ++t)
-                        if (t >= t0 && t < t1)
+                        // unrolled over this pass's taps: one add per instruction; fB + offset >= -1,
+                    // one position before the brick at most (dy is zero there), so the start
+                    // field never borrows
+                    if (t0 == 0 && t1 == 27)
+                        wgrad_taps<0, 27>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                    else if (t0 == 0 && t1 == 14)
+                        wgrad_taps<0, 14>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                    else if (t0 == 14 && t1 == 27)
+                        wgrad_taps<14, 27>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                    else
+                        for (int t = t0; t < t1; ++t)
                             umma::mma_bf16_lohi(tbase + (uint32_t)((t - t0) * Nc), a_lo, a_hi,
-                                                b_lo + (uint32_t)toff[t], b_hi, idesc, accum);
+                                                b_lo + (uint32_t)(((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P +
+                                                                  (t % 3 - 1)),
+                                                b_hi, idesc, accum);
                 }
                 umma::mma_commit(&empty[s]);
             }
@@ -938,7 +957,7 @@ cudaError_t conv3d_launch(const ConvArgs& a, int batch, cudaStream_t st) {
 // fit; the cost model (~56 cycles per MMA; bulk copies ~64 bytes per cycle per SM) picks
 // among them.  Measured alternative, slower on the denoiser's
 // layers: one input plane per pass with the nine taps of one dz (more rows per item).
-static bool wgrad_plan(const WgradArgs& a, WgradPlan* out, size_t* smem_out) {
+static bool wgrad_plan(const WgradArgs& a, int sms, WgradPlan* out, size_t* smem_out) {
     const int P = a.W + 2;
     double best = 1e300;
     bool found = false;
@@ -968,7 +987,9 @@ static bool wgrad_plan(const WgradArgs& a, WgradPlan* out, size_t* smem_out) {
                 const int nyb = a.H / Ty;
                 const int items = a.batch * nyb * a.D;
                 const int passes = (a.Cin / Nc) * ngroups;
-                int G = (152 + passes - 1) / passes;
+                // CTAs per pass: all passes in one wave on the SMs (a CTA past it would run its
+                // whole share again after the others)
+                int G = sms / passes > 1 ? sms / passes : 1;
                 if (G > items) G = items;
                 *out = WgradPlan{Ty, nyb, P, Ty + 2, Nc, ntap, ngroups, kst, (int)plane_dy, (int)plane_x,
                                  (int)x_off, (int)stage, items, G};
@@ -982,7 +1003,11 @@ static bool wgrad_plan(const WgradArgs& a, WgradPlan* out, size_t* smem_out) {
 cudaError_t wgrad_launch(const WgradArgs& a, cudaStream_t st) {
     WgradPlan wp{};
     size_t wsmem = 0;
-    if (!wgrad_plan(a, &wp, &wsmem)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 != cudaSuccess) return e0;
+    if (!wgrad_plan(a, sms, &wp, &wsmem)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)wp.G, (unsigned)((a.Cin / wp.Nc) * wp.ngroups));
