@@ -195,22 +195,33 @@ __global__ void k_relu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y, in
     }
 }
 
-// db[c] += sum over voxels of dy (padded channel-group-major, C channels; the border is
-// zero and adds nothing); units = batch x C/8 x padded voxels
-__global__ void k_bias_grad(const bf16* __restrict__ dy, int units, int vp, int C, float* __restrict__ db) {
-    extern __shared__ float s_acc[];
-    for (int c = threadIdx.x; c < C; c += blockDim.x) s_acc[c] = 0.f;
-    __syncthreads();
-    const int G = C >> 3;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < units; i += gridDim.x * blockDim.x) {
-        const int q = (i / vp) % G;
-        float f[8];
-        ld8(dy + (size_t)8 * i, f);
-        for (int e = 0; e < 8; ++e)
-            if (f[e] != 0.f) atomicAdd(&s_acc[8 * q + e], f[e]);
+// db[8q + e] += sum over voxels of channel 8q + e of dy (padded channel-group-major, G = C/8
+// groups; the border is zero and adds nothing).  Launch grid (nx, G), 256 threads: block
+// column q sums group q in registers, reduces by warp shuffles and shared memory, and adds
+// one value per channel.
+__global__ void k_bias_grad(const bf16* __restrict__ dy, int batch, int vp, int G, float* __restrict__ db) {
+    __shared__ float red[8][8];  // [warp][channel of the group]
+    const int q = blockIdx.y;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int b = 0; b < batch; ++b) {
+        const bf16* base = dy + 8 * (((size_t)b * G + q) * vp);
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < vp; v += gridDim.x * blockDim.x) {
+            float f[8];
+            ld8(base + (size_t)8 * v, f);
+            for (int e = 0; e < 8; ++e) acc[e] += f[e];
+        }
     }
+    for (int e = 0; e < 8; ++e)
+        for (int off = 16; off > 0; off >>= 1) acc[e] += __shfl_down_sync(0xffffffffu, acc[e], off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int e = 0; e < 8; ++e) red[warp][e] = acc[e];
     __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&db[c], s_acc[c]);
+    if (threadIdx.x < 8) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        atomicAdd(&db[8 * q + threadIdx.x], t);
+    }
 }
 
 // Loss and its gradient: pred = dose_low s + out[0]; diff = pred - t with t = target c s
@@ -477,7 +488,9 @@ int wgrad(sde_denoiser* d, const bf16* x, const bf16* dy, const Layer& l, int ba
     rc = fail(wgrad_launch(a, d->st), "wgrad launch");
     if (rc) return rc;
     const int vp = (int)Pcg{D, H, W}.vp();
-    k_bias_grad<<<kBlocks, 256, l.Cout * sizeof(float), d->st>>>(dy, batch * (l.Cout >> 3) * vp, vp, l.Cout, l.gb);
+    const int G = l.Cout >> 3;
+    const dim3 grid((unsigned)(kBlocks / G > 1 ? kBlocks / G : 1), (unsigned)G);
+    k_bias_grad<<<grid, 256, 0, d->st>>>(dy, batch, vp, G, l.gb);
     return fail(cudaGetLastError(), "bias grad launch");
 }
 
