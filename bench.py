@@ -377,7 +377,7 @@ def time_to_dose(torch, S, seeds=(100_000, 100_001, 100_002, 100_003), ladder=(3
     st = torch.cuda.current_stream()
     rows = []
     for seed in seeds:
-        r = DN.transport_doses(seed)
+        r = DN.transport_doses(seed, timing=True)
         ref = S.scale_(r["high"], DN.N_LOW / DN.N_HIGH)
         net.infer(r["low"], r["density"])  # warm
         a = torch.cuda.Event(enable_timing=True)
@@ -420,8 +420,9 @@ def time_to_dose(torch, S, seeds=(100_000, 100_001, 100_002, 100_003), ladder=(3
             "max_err_low": mean("max_err_low"), "plain_1e7_ms": mean("t_high_ms"), "plain_ladder": plain,
             "plain_ms_at_95": first_pass["ms"] if first_pass else None,
             "plain_histories_at_95": first_pass["histories"] if first_pass else None,
-            "note": "device time (CUDA events) of transport + dose conversion (+ inference); gamma 2%/0.5mm, "
-                    "1% threshold, local, vs the 1e7-history plain dose; held-out seeds of the denoiser workload"}
+            "note": "device time (CUDA events) of transport + dose conversion (+ inference) on a warm handle "
+                    "(one untimed run of the same size first, both arms); gamma 2%/0.5mm, 1% threshold, local, "
+                    "vs the 1e7-history plain dose; held-out seeds of the denoiser workload"}
 
 
 def denoiser_roofline(torch, S, peaks):
