@@ -6,7 +6,7 @@ data, then a full inference and a training step, and prints one line per layer w
 the achieved TFLOP/s (2 x voxels x 27 x Cin x Cout per forward; each call also packs its
 weights for the tensor core, which the network does once per weight update).  ``--shape D H W Cin
 Cout`` runs only that convolution ``--reps`` times (a small case for a profiler), or with
-``--wgrad`` its weight gradient.
+``--wgrad`` its weight gradient; ``--infer`` times only the whole-network inference.
 """
 from __future__ import annotations
 
@@ -54,9 +54,22 @@ def main():
     ap.add_argument("--shape", type=int, nargs=5, default=None, metavar=("D", "H", "W", "CIN", "COUT"))
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--wgrad", action="store_true", help="with --shape: run the weight gradient")
+    ap.add_argument("--infer", action="store_true",
+                    help="only the whole-network inference: 4 warm-up calls, then --reps timed ones")
     args = ap.parse_args()
     torch.cuda.init()
     st = torch.cuda.current_stream()
+    if args.infer:
+        net = S.Denoiser(192, 128, 128, batch_max=1, seed=1)
+        low = torch.rand(192, 128, 128, device="cuda")
+        rho = torch.ones_like(low)
+        for _ in range(4):
+            net.infer(low, rho)
+        ms = _time(lambda: net.infer(low, rho), args.reps, st)
+        S.denoise_status()
+        net.close()
+        print(json.dumps({"infer_ms": ms, "reps": args.reps}))
+        return
     if args.shape:
         D, H, W, ci, co = args.shape
         x, w, b, y = _tensors(D, H, W, ci, co)
