@@ -202,11 +202,11 @@ namespace {
 //
 // Persistent and warp-specialised: one thread of the producer warp streams (brick,
 // weight) chunks into a ring of shared-memory stages (each stage's "full" barrier
-// completes when the bytes of its copies have landed); one thread of the MMA warp issues
-// tcgen05.mma into one of two tensor-memory accumulators and releases stages and
-// accumulators through tcgen05.commit; the kConvWorkers epilogue warps turn a finished
-// accumulator into output (bias, leaky ReLU, BF16 or FP32 store) while the tensor core
-// works on the next item.  Every wait is bounded; a timeout sets a shared abort flag that
+// completes when the bytes of its copies have landed); one thread in each of two MMA
+// warps issues tcgen05.mma for the M tiles of its parity into one of two tensor-memory
+// accumulators, and both release stages and accumulators through tcgen05.commit; the
+// kConvWorkers epilogue warps turn a finished accumulator into output (bias, leaky ReLU,
+// BF16 or FP32 store) while the tensor core works on the next item.  Every wait is bounded; a timeout sets a shared abort flag that
 // ends all roles' loops, and the producer waits for its copies in flight before the CTA
 // exits.
 // ----------------------------------------------------------------------------
@@ -226,10 +226,10 @@ __device__ __forceinline__ bool pipe_wait(uint64_t* m, uint32_t parity, volatile
 }
 
 // Epilogue warps of the brick convolution; two share each tensor-memory lane quarter
-// (warp & 3).  The MMA warp and the producer warp follow them.
+// (warp & 3).  The two MMA warps and the producer warp follow them.
 constexpr int kConvWorkers = 8;
 constexpr int kConvWorkerThreads = 32 * kConvWorkers;
-constexpr int kConvThreads = kConvWorkerThreads + 64;
+constexpr int kConvThreads = kConvWorkerThreads + 96;
 
 // AND of a predicate over the NT worker threads of a kernel (its warps 0 .. NT/32 - 1),
 // named barrier 1.
@@ -257,18 +257,18 @@ __device__ __forceinline__ int tile_base(int m, bool rowtile, int P, int Yb, int
 // offset), B's steps by one tap tile (Cp x 16 BF16 = 2 Cp units of 16 bytes).  The start
 // fields stay within 14 bits (shared addresses below 256 KB, lowest start one position
 // into the stage), so adding to the low word never carries or borrows into the others.
-template <int TILES>
+template <int TILES, int PAR>
 __device__ __forceinline__ void conv_chunk_mma(uint32_t dacc, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
                                                uint32_t b_hi, uint32_t idesc, int Cp, const int (&toff)[27],
                                                bool rowtile, int P, int Yb, int tpr, uint32_t first_accum) {
     int tb[TILES];
 #pragma unroll
-    for (int m = 0; m < TILES; ++m) tb[m] = tile_base(m, rowtile, P, Yb, tpr);
+    for (int m = PAR; m < TILES; m += 2) tb[m] = tile_base(m, rowtile, P, Yb, tpr);
 #pragma unroll
     for (int t = 0; t < 27; ++t) {
         const uint32_t bl = b_lo + (uint32_t)(2 * Cp * t);
 #pragma unroll
-        for (int m = 0; m < TILES; ++m)
+        for (int m = PAR; m < TILES; m += 2)
             umma::mma_bf16_lohi(dacc + (uint32_t)(m * Cp), a_lo + (uint32_t)(tb[m] + toff[t]), a_hi, bl, b_hi, idesc,
                                 t > 0 ? 1u : first_accum);
     }
@@ -278,18 +278,18 @@ __device__ __forceinline__ void conv_chunk_mma(uint32_t dacc, uint32_t a_lo, uin
 // B is the three consecutive x-tap tiles of the pair and whose A is the pair's dx = 0
 // window; accumulator column block j then holds the window's product with the dx = j - 1
 // weights, and the epilogue adds the blocks shifted by one position.
-template <int TILES>
+template <int TILES, int PAR>
 __device__ __forceinline__ void conv_chunk_mma_fold(uint32_t dacc, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
                                                     uint32_t b_hi, uint32_t idesc, int Cp, const int (&toff)[27],
                                                     int P, int Yb, uint32_t first_accum) {
     int tb[TILES];
 #pragma unroll
-    for (int m = 0; m < TILES; ++m) tb[m] = tile_base(m, true, P, Yb, 1);
+    for (int m = PAR; m < TILES; m += 2) tb[m] = tile_base(m, true, P, Yb, 1);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const uint32_t bl = b_lo + (uint32_t)(6 * Cp * q);  // taps 3q .. 3q+2
 #pragma unroll
-        for (int m = 0; m < TILES; ++m)
+        for (int m = PAR; m < TILES; m += 2)
             umma::mma_bf16_lohi(dacc + (uint32_t)(3 * m * Cp), a_lo + (uint32_t)(tb[m] + toff[3 * q + 1]), a_hi, bl,
                                 b_hi, idesc, q > 0 ? 1u : first_accum);
     }
@@ -333,10 +333,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
     if (tid == 0) {
         for (int s = 0; s < kPipeStages; ++s) {
             umma::mbar_init(&full[s], 1);
-            umma::mbar_init(&empty[s], 1);
+            umma::mbar_init(&empty[s], 2);  // one commit per MMA thread
         }
         for (int s = 0; s < 2; ++s) {
-            umma::mbar_init(&tfull[s], 1);
+            umma::mbar_init(&tfull[s], 2);
             umma::mbar_init(&tempty[s], kConvWorkerThreads);
         }
         umma::mbar_init(wfull, 1);
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
     const uint32_t s_wres = s_stage0 + (uint32_t)(kPipeStages * b.stage);
     const Pcg pg{D, H, W};
 
-    if (warp == kConvWorkers + 1) {
+    if (warp == kConvWorkers + 2) {
         if (lane == 0) {  // producer
             const int Gin = Cin >> 3;
             int k = 0;
@@ -395,7 +395,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
             if (b.wres) umma::mbar_wait(wfull, 0u, kWaitCycles);
         }
         __syncwarp();
-    } else if (warp == kConvWorkers) {
+    } else if (warp >= kConvWorkers) {
+        // two MMA threads (one thread can issue a tcgen05.mma only every ~65 cycles, two are
+        // bound by the operand reads from shared memory): issuer iss takes the M tiles of its
+        // parity, so each accumulator column range has one issuer
+        const int iss = warp - kConvWorkers;
         if (lane == 0) {
             const uint32_t idesc = umma::idesc_bf16_f32(128, b.fold ? 3 * Cp : Cp);
             int toff[27];  // tap (dz, dy, dx) -> brick position offset (dz Yb + dy) P + dx
@@ -427,7 +431,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                         switch (b.tiles) {
 #define SDE_CONV_FOLD(T)                                                                             \
     case T:                                                                                          \
-        conv_chunk_mma_fold<T>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, P, Yb, first); \
+        if (iss) conv_chunk_mma_fold<T, 1>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, P, Yb, first); \
+        else conv_chunk_mma_fold<T, 0>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, P, Yb, first); \
         break;
                             SDE_CONV_FOLD(1)
                             SDE_CONV_FOLD(2)
@@ -436,7 +441,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
 #undef SDE_CONV_FOLD
                             default:
                                 for (int q = 0; q < 9; ++q)
-                                    for (int m = 0; m < b.tiles; ++m)
+                                    for (int m = iss; m < b.tiles; m += 2)
                                         umma::mma_bf16_lohi(dacc + (uint32_t)(3 * m * Cp),
                                                             a_lo + (uint32_t)(tile_base(m, true, P, Yb, 1) +
                                                                               ((q / 3 - 1) * Yb + (q % 3 - 1)) * P),
@@ -447,7 +452,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                         switch (b.tiles) {
 #define SDE_CONV_TILES(T)                                                                          \
     case T:                                                                                        \
-        conv_chunk_mma<T>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, rt, P, Yb, tpr, first); \
+        if (iss) conv_chunk_mma<T, 1>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, rt, P, Yb, tpr, first); \
+        else conv_chunk_mma<T, 0>(dacc, a_lo, a_hi, b_lo, b_hi, idesc, Cp, toff, rt, P, Yb, tpr, first); \
         break;
                             SDE_CONV_TILES(1)
                             SDE_CONV_TILES(2)
@@ -460,7 +466,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
 #undef SDE_CONV_TILES
                             default:
                                 for (int t = 0; t < 27; ++t)
-                                    for (int m = 0; m < b.tiles; ++m)
+                                    for (int m = iss; m < b.tiles; m += 2)
                                         umma::mma_bf16_lohi(dacc + (uint32_t)(m * Cp),
                                                             a_lo + (uint32_t)(tile_base(m, rt, P, Yb, tpr) +
                                                                               ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P +
