@@ -843,13 +843,19 @@ cudaError_t flip_weights_launch(const __nv_bfloat16* w, __nv_bfloat16* wd, int C
 // may pass H),
 // and for 128-voxel rows the x-tap fold, chosen by a cost model calibrated on GB300 with
 // per-role cycle counters in this kernel: a tcgen05.mma (M = 128, K = 16) takes ~64 cycles
-// of the issuing thread at N = 32, ~85 at N = 64, ~90 at N = 96 and about N / 2 from
-// N = 192; bulk copies of brick runs move ~64 bytes per cycle per SM; the epilogue takes
+// of one issuing thread at N = 32, ~85 at N = 64, ~90 at N = 96 and about N / 2 from
+// N = 192, less with two issuers (mma_pair_factor); bulk copies of brick runs move ~64 bytes per cycle per SM; the epilogue takes
 // ~700 cycles per tile and 8 columns (~850 folded) on each of its two warp groups and
 // overlaps the MMAs only with two accumulators; copies and MMAs overlap, but not perfectly
 // (a quarter of the shorter one shows).
 static double mma_cycles(int N) {
     return N <= 32 ? 64.0 : (N <= 64 ? 85.0 : (N <= 96 ? 90.0 : (N <= 192 ? 96.0 + (N - 128) / 2.0 : N / 2.0)));
+}
+// Time per MMA with two issuers relative to one (microbenchmark: 65 cycles from one thread,
+// (4 KB of A + N x 32 bytes of B) / 128 bytes per cycle from two, at least the dense peak).
+static double mma_pair_factor(int N) {
+    const double two = (4096.0 + 32.0 * N) / 128.0, peak = 2.0 * 128 * N * 16 / 8192.0;
+    return (two > peak ? two : peak) / 65.0 < 1.0 ? (two > peak ? two : peak) / 65.0 : 1.0;
 }
 
 static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickPlan* out, size_t* smem_out) {
@@ -880,7 +886,11 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
                     const size_t xch = kPipeHeader + kPipeStages * stage + (wres ? nchunk * w_bytes : 0);
                     const size_t smem = xch + (fold ? (size_t)128 * Cp : 0);
                     if (smem > smem_cap || plane >= (1u << 18)) break;
-                    const double mma = (double)nchunk * tiles * (fold ? 9 * mma_cycles(3 * Cp) : 27 * mma_cycles(Cp));
+                    // two issuers share the tiles: pairs of tiles at the two-issuer rate, an odd
+                    // last tile at one issuer's
+                    const int Nmma = fold ? 3 * Cp : Cp;
+                    const double per_tile = (fold ? 9 : 27) * mma_cycles(Nmma);
+                    const double mma = (double)nchunk * per_tile * ((tiles / 2) * 2 * mma_pair_factor(Nmma) + tiles % 2);
                     const double load = (double)nchunk * (6 * run + (wres ? 0 : w_bytes)) / 64.0;
                     const double epi = ((tiles + 1) / 2) * (Cp / 8.0) * (fold ? 850.0 : 700.0);
                     double item = (mma > load ? mma : load) + 0.25 * (mma > load ? load : mma);
