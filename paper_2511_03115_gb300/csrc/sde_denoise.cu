@@ -659,19 +659,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
 // NaN or Inf: the few positions B reads just outside the staged data (before the first
 // plane, between planes, after the last) are zeroed once at start and never written.
 // ----------------------------------------------------------------------------
-// The weight-gradient MMAs of one K step for taps T0 .. T1-1 (fully unrolled): the
-// accumulator of tap t starts at column (t - T0) Nc, B's start field is the K step's plus
-// the tap's brick offset.
-template <int T0, int T1>
+// The weight-gradient MMAs of one K step for taps T0 .. T1-1 (fully unrolled) of a pass
+// whose first tap is P0: the accumulator of tap t starts at column (t - P0) Nc, B's start
+// field is the K step's plus the tap's brick offset.
+template <int P0, int T0, int T1>
 __device__ __forceinline__ void wgrad_taps(uint32_t tbase, int Nc, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
                                            uint32_t b_hi, uint32_t idesc, uint32_t accum, const int (&toff)[27]) {
 #pragma unroll
     for (int t = T0; t < T1; ++t)
-        umma::mma_bf16_lohi(tbase + (uint32_t)((t - T0) * Nc), a_lo, a_hi, b_lo + (uint32_t)toff[t], b_hi, idesc,
+        umma::mma_bf16_lohi(tbase + (uint32_t)((t - P0) * Nc), a_lo, a_hi, b_lo + (uint32_t)toff[t], b_hi, idesc,
                             accum);
 }
 
-__global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b) {
+__global__ void __launch_bounds__(192, 1) k_wgrad_brick(WgradArgs a, WgradPlan b) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Cin = a.Cin, Cout = a.Cout, W = a.W, H = a.H, D = a.D, Nc = b.Nc;
@@ -701,9 +701,9 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
     if (tid == 0) {
         for (int s = 0; s < kPipeStages; ++s) {
             umma::mbar_init(&full[s], 1);
-            umma::mbar_init(&empty[s], 1);
+            umma::mbar_init(&empty[s], 2);  // one commit per MMA thread
         }
-        umma::mbar_init(dfull, 1);
+        umma::mbar_init(dfull, 2);
         *abort_flag = 0;
     }
     umma::fence_before_sync();
@@ -712,7 +712,9 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
     const uint32_t tbase = *slot;
     const int fB = (Yb + 1) * P;  // brick position under output position 0 of the item
 
-    if (warp == 4) {
+    if (warp >= 4) {
+        // two MMA threads split each pass's taps (each tap has its own accumulator columns)
+        const int iss = warp - 4;
         if (lane == 0) {
             const uint32_t idesc = umma::idesc_bf16_f32(128, Nc, 1, 1);
             int toff[27];  // tap (dz, dy, dx) -> brick position offset (dz Yb + dy) P + dx
@@ -739,14 +741,17 @@ __global__ void __launch_bounds__(160, 1) k_wgrad_brick(WgradArgs a, WgradPlan b
                         // unrolled over this pass's taps: one add per instruction; fB + offset >= -1,
                     // one position before the brick at most (dy is zero there), so the start
                     // field never borrows
-                    if (t0 == 0 && t1 == 27)
-                        wgrad_taps<0, 27>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
-                    else if (t0 == 0 && t1 == 14)
-                        wgrad_taps<0, 14>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
-                    else if (t0 == 14 && t1 == 27)
-                        wgrad_taps<14, 27>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
-                    else
-                        for (int t = t0; t < t1; ++t)
+                    if (t0 == 0 && t1 == 27) {
+                        if (iss) wgrad_taps<0, 14, 27>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                        else wgrad_taps<0, 0, 14>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                    } else if (t0 == 0 && t1 == 14) {
+                        if (iss) wgrad_taps<0, 7, 14>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                        else wgrad_taps<0, 0, 7>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                    } else if (t0 == 14 && t1 == 27) {
+                        if (iss) wgrad_taps<14, 21, 27>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                        else wgrad_taps<14, 14, 21>(tbase, Nc, a_lo, a_hi, b_lo, b_hi, idesc, accum, toff);
+                    } else
+                        for (int t = t0 + iss; t < t1; t += 2)
                             umma::mma_bf16_lohi(tbase + (uint32_t)((t - t0) * Nc), a_lo, a_hi,
                                                 b_lo + (uint32_t)(((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P +
                                                                   (t % 3 - 1)),
@@ -1027,7 +1032,7 @@ cudaError_t wgrad_launch(const WgradArgs& a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_wgrad_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)wp.G, (unsigned)((a.Cin / wp.Nc) * wp.ngroups));
-    k_wgrad_brick<<<grid, 160, wsmem, st>>>(a, wp);
+    k_wgrad_brick<<<grid, 192, wsmem, st>>>(a, wp);
     return cudaGetLastError();
 }
 
