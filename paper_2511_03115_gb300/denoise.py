@@ -177,7 +177,8 @@ def evaluate(net, seeds, dd=0.02, dta_mm=0.5, threshold=0.01, ladder=True, n_low
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
-    ap.add_argument("--train", type=int, default=64, help="training pairs (seeds 0..n-1)")
+    ap.add_argument("--train", type=int, default=64, help="training pairs (seeds first-seed .. first-seed+n-1)")
+    ap.add_argument("--first-seed", type=int, default=0, help="seed of the first training pair (below 100000)")
     ap.add_argument("--epochs", type=int, default=2)
     ap.add_argument("--eval", type=int, default=8, help="held-out pairs (seeds 100000..)")
     ap.add_argument("--lr", type=float, default=1e-4)
@@ -190,7 +191,9 @@ def main():
     torch = _torch()
     torch.cuda.init()
     t0 = time.time()
-    pairs = generate(range(args.train), args.n_low, args.n_high)
+    if args.first_seed + args.train > 100_000:
+        raise SystemExit("training seeds must stay below the held-out seeds (100000 on)")
+    pairs = generate(range(args.first_seed, args.first_seed + args.train), args.n_low, args.n_high)
     t_gen = time.time() - t0
     net = S.Denoiser(SHAPE[2], SHAPE[1], SHAPE[0], batch_max=1, seed=1)
     if args.load:
@@ -205,7 +208,7 @@ def main():
     if args.save:
         np.save(args.save, net.get_params())
     agg, rows = evaluate(net, range(100_000, 100_000 + args.eval), n_low=args.n_low, n_high=args.n_high)
-    report = {"train_pairs": args.train, "epochs": args.epochs, "n_low": args.n_low, "n_high": args.n_high, "generate_s": t_gen, "train_s": t_train,
+    report = {"train_pairs": args.train, "first_seed": args.first_seed, "epochs": args.epochs, "n_low": args.n_low, "n_high": args.n_high, "generate_s": t_gen, "train_s": t_train,
               "train_step_ms": 1e3 * t_train / max(1, args.train * args.epochs), "losses": losses,
               "params": net.num_params(), "eval": agg, "rows": rows}
     print(json.dumps(report))
