@@ -439,14 +439,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                             SDE_CONV_FOLD(3)
                             SDE_CONV_FOLD(4)
 #undef SDE_CONV_FOLD
-                            default:
-                                for (int q = 0; q < 9; ++q)
-                                    for (int m = iss; m < b.tiles; m += 2)
-                                        umma::mma_bf16_lohi(dacc + (uint32_t)(3 * m * Cp),
-                                                            a_lo + (uint32_t)(tile_base(m, true, P, Yb, 1) +
-                                                                              ((q / 3 - 1) * Yb + (q % 3 - 1)) * P),
-                                                            a_hi, b_lo + (uint32_t)(6 * Cp * q), b_hi, idesc,
-                                                            q > 0 ? 1u : first);
+                            default:  // the plan keeps folded items to <= 4 tiles
+                                *abort_flag = 1;
                         }
                     } else {
                         switch (b.tiles) {
@@ -464,15 +458,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
                             SDE_CONV_TILES(7)
                             SDE_CONV_TILES(8)
 #undef SDE_CONV_TILES
-                            default:
-                                for (int t = 0; t < 27; ++t)
-                                    for (int m = iss; m < b.tiles; m += 2)
-                                        umma::mma_bf16_lohi(dacc + (uint32_t)(m * Cp),
-                                                            a_lo + (uint32_t)(tile_base(m, rt, P, Yb, tpr) +
-                                                                              ((t / 9 - 1) * Yb + ((t / 3) % 3 - 1)) * P +
-                                                                              (t % 3 - 1)),
-                                                            a_hi, b_lo + (uint32_t)(2 * Cp * t), b_hi, idesc,
-                                                            t > 0 ? 1u : first);
+                            default:  // the plan keeps items to <= 8 tiles
+                                *abort_flag = 1;
                         }
                     }
                     umma::mma_commit(&empty[s]);
@@ -881,7 +868,7 @@ static bool brick_plan(int D, int H, int W, int Cin, int Cout, int batch, BrickP
                     const int nyb = (H + Ty - 1) / Ty;
                     const int tiles = rowtile ? Ty * (W / 128) : (Ty * P + 127) / 128;
                     const int cols = tiles * Cp * (fold ? 3 : 1);  // accumulator columns per item
-                    if (cols > 512) break;
+                    if (cols > 512 || tiles > (fold ? 4 : 8)) break;  // the MMA loops are unrolled up to these
                     const int nacc = 2 * cols <= 512 ? 2 : 1;
                     const size_t run = (size_t)(Ty + 2) * P * 16;
                     const size_t plane = (3 * run + 127) / 128 * 128;
