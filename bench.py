@@ -60,6 +60,17 @@ TRANSPORT_DRAM = {  # workload -> {"src": sha256 prefix, "bytes": per launch, "n
                          "(1 pass; profiles/k_transport_plan2000.md)"},
 }
 
+# L2 reduction (tally `red.add.u64`) rate of the transport kernel, from ncu on the plan's first
+# 2e6 histories; reported only while the transport sources match the hash it was taken on.
+TRANSPORT_ATOMICS = {
+    "plan2000": {"src": "d72694a2b6303fff", "l2_red_pct_of_peak": 14.50, "busiest_l2_slice_pct": 17.24,
+                 "red_sectors": 434_135_824, "euler_steps": 525_487_490,
+                 "note": "ncu lts__t_sectors_srcunit_tex_op_red (.sum, .avg/.max pct_of_peak_sustained_elapsed) of "
+                         "k_transport in `bench.py --histories 2000000 --no-autotune --steps 1 --warmup 1 "
+                         "--e2e-steps 0 --no-denoiser --no-cpu-baseline --no-secondary` "
+                         "(profiles/k_transport_plan2000.md)"},
+}
+
 WORKLOADS = {
     "plan2000": ("plan2000: 2000 spots on a 5 mm grid, E U(70,200) MeV, lognormal(0,0.7) weights, "
                  "1e8 protons per GPU, 200x200x300 mm at 1 mm, water + 30 random spheres (tissue/bone, "
@@ -570,6 +581,12 @@ def main():
     traffic_rec = TRANSPORT_DRAM.get(args.workload)
     traffic = traffic_rec["bytes"] if traffic_rec and traffic_rec["src"] == src and count == traffic_rec.get(
         "histories", count) else None
+    atom_rec = TRANSPORT_ATOMICS.get(args.workload)
+    atomics = ({"bound": "l2_red", "pct_of_peak": atom_rec["l2_red_pct_of_peak"],
+                "busiest_slice_pct_of_peak": atom_rec["busiest_l2_slice_pct"],
+                "red_sectors_per_euler_step": atom_rec["red_sectors"] / atom_rec["euler_steps"],
+                "note": atom_rec["note"], "transport_src": src}
+               if atom_rec and atom_rec["src"] == src else None)
     line = {
         "metric": METRIC,
         "value": value,
@@ -603,9 +620,11 @@ def main():
                      "traffic_note": (traffic_rec or {}).get("note") if traffic is not None else
                      "null: no ncu capture of this transport source (hash %s) for this workload" % src,
                      "kernel": "k_transport (+ single-block spot prep)", "kernel_ms": Tk,
-                     "ops_per_step": ALGO_OPS_PER_STEP, "transport_src": src,
+                     "ops_per_step": ALGO_OPS_PER_STEP, "euler_steps_per_s": steps_per_launch / (Tk * 1e-3),
+                     "transport_src": src,
                      "peak_note": f"{sms} SMs (device attribute) x {LANE_OPS_PER_CLK_PER_SM} lane-ops/clk x "
                                   f"{clk_mhz:.0f} MHz (measured max SM clock)"},
+        "tally_atomics": atomics,
         "clocks": clocks,
         "balance_exact": bal["incident"] == bal["deposited"] + bal["escaped"] + bal["removed"],
         "combine": combine,
