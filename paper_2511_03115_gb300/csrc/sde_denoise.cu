@@ -200,8 +200,8 @@ namespace {
 // otherwise M tiles of 128 consecutive positions cover the Ty rows including their
 // padding columns and the epilogue drops the rows that are not output voxels.
 //
-// Persistent and warp-specialised: one thread of the producer warp streams (brick,
-// weight) chunks into a ring of shared-memory stages (each stage's "full" barrier
+// Persistent and warp-specialised: the producer warp streams (brick, weight) chunks into
+// a ring of shared-memory stages, one bulk copy per lane (each stage's "full" barrier
 // completes when the bytes of its copies have landed); one thread in each of two MMA
 // warps issues tcgen05.mma for the M tiles of its parity into one of two tensor-memory
 // accumulators, and both release stages and accumulators through tcgen05.commit; the
@@ -354,40 +354,47 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv3d_brick(ConvArgs a, Br
     const Pcg pg{D, H, W};
 
     if (warp == kConvWorkers + 2) {
-        if (lane == 0) {  // producer
-            const int Gin = Cin >> 3;
-            int k = 0;
-            if (b.wres) {
-                umma::mbar_arrive_expect_tx(wfull, (uint32_t)nchunk * w_chunk);
-                umma::bulk_g2s(s_wres, a.wpk, (uint32_t)nchunk * w_chunk, wfull);
-            }
-            bool ok = true;
-            for (int item = blockIdx.x; ok && item < b.items; item += gridDim.x) {
-                const BrickItem t = brick_item(b, D, item);
-                const __nv_bfloat16* wpart = a.wpk + (size_t)t.part * nchunk * 27 * Cp * 16;
-                // one (channel group, plane) part of the brick: padded rows y0 .. y0+Yb-1, fewer in a
-                // last row block that passes H (the rows it leaves stale feed only outputs y >= H,
-                // which the epilogue drops)
-                const int rows = Yb < H + 2 - t.y0 ? Yb : H + 2 - t.y0;
-                const uint32_t run = (uint32_t)(rows * P * 16);
-                const uint32_t slot = (uint32_t)(Yb * P * 16);
-                for (int c = 0; c < nchunk; ++c, ++k) {
-                    const int s = k % kPipeStages, u = k / kPipeStages;
-                    if (u >= 1 && !pipe_wait(&empty[s], (uint32_t)(u - 1) & 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
-                    umma::mbar_arrive_expect_tx(&full[s], 6u * run + (b.wres ? 0u : w_chunk));
-                    for (int gg = 0; gg < 2; ++gg)
-                        for (int zb = 0; zb < 3; ++zb)  // rows y0-1 .. y0+Ty of plane z+zb-1, columns -1 .. W
-                            umma::bulk_g2s(st + 128u + (uint32_t)(gg * b.plane) + (uint32_t)zb * slot,
-                                           a.x + 8 * pg.unit(t.n, Gin, 2 * c + gg, t.z + zb - 1, t.y0 - 1, -1), run,
-                                           &full[s]);
-                    if (!b.wres)
-                        umma::bulk_g2s(st + (uint32_t)b.w_off, wpart + (size_t)c * 27 * Cp * 16, w_chunk, &full[s]);
+        // producer warp: lane 0 waits for a free stage and posts the bytes it will receive, then
+        // lanes 0-5 issue the six brick runs and lane 6 the weight chunk (one thread can issue
+        // a bulk copy only every ~100 cycles, which made the copies the bottleneck of the
+        // 96-channel layer)
+        const int Gin = Cin >> 3;
+        int k = 0;
+        if (b.wres && lane == 0) {
+            umma::mbar_arrive_expect_tx(wfull, (uint32_t)nchunk * w_chunk);
+            umma::bulk_g2s(s_wres, a.wpk, (uint32_t)nchunk * w_chunk, wfull);
+        }
+        bool ok = true;
+        for (int item = blockIdx.x; ok && item < b.items; item += gridDim.x) {
+            const BrickItem t = brick_item(b, D, item);
+            const __nv_bfloat16* wpart = a.wpk + (size_t)t.part * nchunk * 27 * Cp * 16;
+            // one (channel group, plane) part of the brick: padded rows y0 .. y0+Yb-1, fewer in a
+            // last row block that passes H (the rows it leaves stale feed only outputs y >= H,
+            // which the epilogue drops)
+            const int rows = Yb < H + 2 - t.y0 ? Yb : H + 2 - t.y0;
+            const uint32_t run = (uint32_t)(rows * P * 16);
+            const uint32_t slot = (uint32_t)(Yb * P * 16);
+            for (int c = 0; c < nchunk; ++c, ++k) {
+                const int s = k % kPipeStages, u = k / kPipeStages;
+                bool got = true;
+                if (lane == 0 && u >= 1) got = pipe_wait(&empty[s], (uint32_t)(u - 1) & 1u, abort_flag);
+                if (!__shfl_sync(0xffffffffu, got, 0)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = s_stage0 + (uint32_t)(s * b.stage);
+                if (lane == 0) umma::mbar_arrive_expect_tx(&full[s], 6u * run + (b.wres ? 0u : w_chunk));
+                __syncwarp();
+                if (lane < 6) {  // rows y0-1 .. y0+Ty of plane z+zb-1, columns -1 .. W
+                    const int gg = lane / 3, zb = lane - 3 * gg;
+                    umma::bulk_g2s(st + 128u + (uint32_t)(gg * b.plane) + (uint32_t)zb * slot,
+                                   a.x + 8 * pg.unit(t.n, Gin, 2 * c + gg, t.z + zb - 1, t.y0 - 1, -1), run, &full[s]);
+                } else if (lane == 6 && !b.wres) {
+                    umma::bulk_g2s(st + (uint32_t)b.w_off, wpart + (size_t)c * 27 * Cp * 16, w_chunk, &full[s]);
                 }
             }
+        }
+        if (lane == 0) {
             // no copy may still be writing shared memory when the CTA exits: wait for the
             // last kPipeStages chunks (earlier ones were consumed before their stage was reused)
             for (int kk = k > kPipeStages ? k - kPipeStages : 0; kk < k; ++kk)
