@@ -332,3 +332,34 @@ def test_learned_dose_against_an_fp64_oracle_dose(sde_gpu, oracle_lib):
     print({k: {"gamma": round(g, 4), "max_err": round(e, 4)} for k, (g, e) in res.items()})
     assert res["learned"][0] > res["low_1e5"][0] + 0.02
     assert res["learned"][1] < res["low_1e5"][1]
+
+
+def test_batched_inference_equals_single_samples(sde_gpu):
+    """A batch of two doses (one density map) gives, sample by sample, exactly the doses of
+    two single-sample inferences: per-sample offsets of every padded activation, the input
+    scaling and the output stage; random weights so that the network is far from the
+    identity."""
+    import numpy as np
+    import torch
+    S = sde_gpu
+    shape = (8, 16, 32)
+    rng = np.random.default_rng(11)
+    one = S.Denoiser(*shape, batch_max=1, seed=7)
+    two = S.Denoiser(*shape, batch_max=2, seed=7)
+    p = one.get_params()
+    p = (p + 0.05 * rng.standard_normal(p.shape)).astype(np.float32)
+    one.set_params(p)
+    two.set_params(p)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    low = torch.rand((2,) + shape, device="cuda", generator=g)
+    low[1] *= 3.0  # a different per-sample scale
+    rho = 0.5 + torch.rand(shape, device="cuda", generator=g)
+    both = two.infer(low, rho)
+    S.denoise_status()
+    for b in range(2):
+        single = one.infer(low[b].contiguous(), rho)
+        S.denoise_status()
+        assert torch.equal(both[b], single), b
+    assert not torch.equal(both, low)
+    one.close()
+    two.close()
