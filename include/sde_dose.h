@@ -322,16 +322,18 @@ int sde_denoise_status(void* stream);
  * the output is the dose (Gy).  Internally the dose is scaled by 1/max of the
  * low-history dose of each sample and the network predicts a correction that
  * is added to it; the output layer starts at zero, so an untrained network
- * returns its input.  D, H, W must be multiples of 4, (D/4)(H/4)(W/4) a
- * multiple of 128 and D H W batch_max below 2^31 / 24 (SDE_EINVAL otherwise).
- * The handle owns its device memory (weights, optimiser state, activations and
- * gradients for batch_max samples). */
+ * returns its input.  D, H, W must be multiples of 4, W <= 256 and
+ * (D+2)(H+2)(W+2) batch_max below 2^31 / 24 (SDE_EINVAL otherwise).  The handle
+ * owns its device memory (weights, optimiser state, and the activations and
+ * gradients of batch_max samples in the convolutions' padded channel-group-major
+ * layout). */
 typedef struct sde_denoiser sde_denoiser;
 int sde_denoiser_create(sde_denoiser** out, int D, int H, int W, int batch_max, uint64_t seed);
 void sde_denoiser_destroy(sde_denoiser* d);
 int sde_denoiser_set_stream(sde_denoiser* d, void* cuda_stream);
 int sde_denoiser_num_params(const sde_denoiser* d, uint64_t* n);
-/* Inference: d_dose_out[batch][D*H*W] (device).  Asynchronous. */
+/* Inference: d_dose_low and d_dose_out [batch][D*H*W], d_density [D*H*W] (one
+ * density map for the batch), device FP32.  Asynchronous. */
 int sde_denoiser_infer(sde_denoiser* d, const float* d_dose_low, const float* d_density, int batch,
                        float* d_dose_out);
 /* One Adam step on the squared error between the prediction and t =
