@@ -54,7 +54,7 @@ LANE_OPS_PER_CLK_PER_SM = 128  # 4 schedulers x 32 lanes, one instruction per cl
 # hash of the kernel's source files); otherwise the line reports null.
 TRANSPORT_SOURCES = ("sde_transport.cu", "sde_internal.cuh", "sde_transport.h")
 TRANSPORT_DRAM = {  # workload -> {"src": sha256 prefix, "bytes": per launch, "note": ...}
-    "plan2000": {"src": "d72694a2b6303fff", "bytes": 2_353_582_336 + 2_251_225_344, "histories": 100_000_000,
+    "plan2000": {"src": "2c263b682767634b", "bytes": 1_496_984_320 + 1_409_387_520, "histories": 100_000_000,
                  "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first timed launch of "
                          "`bench.py --steps 2 --warmup 1 --no-denoiser --no-cpu-baseline --no-secondary` "
                          "(1 pass; profiles/k_transport_plan2000.md)"},
@@ -63,8 +63,8 @@ TRANSPORT_DRAM = {  # workload -> {"src": sha256 prefix, "bytes": per launch, "n
 # L2 reduction (tally `red.add.u64`) rate of the transport kernel, from ncu on the plan's first
 # 2e6 histories; reported only while the transport sources match the hash it was taken on.
 TRANSPORT_ATOMICS = {
-    "plan2000": {"src": "d72694a2b6303fff", "l2_red_pct_of_peak": 14.50, "busiest_l2_slice_pct": 17.24,
-                 "red_sectors": 434_135_824, "euler_steps": 525_487_490,
+    "plan2000": {"src": "2c263b682767634b", "l2_red_pct_of_peak": 14.78, "busiest_l2_slice_pct": 16.77,
+                 "red_sectors": 433_046_965, "euler_steps": 525_487_490,
                  "note": "ncu lts__t_sectors_srcunit_tex_op_red (.sum, .avg/.max pct_of_peak_sustained_elapsed) of "
                          "k_transport in `bench.py --histories 2000000 --no-autotune --steps 1 --warmup 1 "
                          "--e2e-steps 0 --no-denoiser --no-cpu-baseline --no-secondary` "
