@@ -19,7 +19,7 @@ KAPPA = 0.6
 
 
 def test_branching_per_voxel_parity_on_the_slab_phantom(sde_gpu, oracle_lib):
-    """configs[1] phantom at 0.5 mm with secondaries (bone and lung slabs change the
+    """Slab phantom (150 MeV beam) at 0.5 mm with secondaries (bone and lung slabs change the
     secondaries' ranges): GPU 16 x 640 000 against the oracle 16 x 62 500."""
     wl = slab150()
     g, _ = _gpu_moments(sde_gpu, wl, GPU_BATCH, range(B), secondary_fraction=KAPPA)

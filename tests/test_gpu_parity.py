@@ -65,7 +65,7 @@ def _check_range(g, o, hz, density, tol_mm=0.05):
 
 
 def test_water100_dose_parity(sde_gpu, oracle_lib):
-    """configs[0] workload: 100 MeV pencil beam in water, 40x40x120 mm at 1 mm, per voxel:
+    """Water workload: 100 MeV pencil beam in water, 40x40x120 mm at 1 mm, per voxel:
     GPU 16 x 640 000 histories against the oracle 16 x 20 000."""
     wl = water100()
     g, gi = _gpu_moments(sde_gpu, wl, GPU_BATCH, range(B))
@@ -120,7 +120,7 @@ def test_tally_is_independent_of_launch_shape(sde_gpu):
 
 
 def test_slab150_per_voxel_parity(sde_gpu, oracle_lib):
-    """configs[1] phantom (water / bone-like / lung-like / water slabs) at its own 0.5 mm
+    """Slab phantom (water / bone-like / lung-like / water slabs) at its own 0.5 mm
     voxels: every voxel above 1 % of D_max, GPU 16 x 640 000 histories against the oracle
     16 x 62 500; distal R80/R90 of the energy depth curve."""
     wl = slab150()
@@ -131,7 +131,7 @@ def test_slab150_per_voxel_parity(sde_gpu, oracle_lib):
 
 
 def test_insert150_per_voxel_parity(sde_gpu, oracle_lib):
-    """configs[2] phantom (bone half-space x > 0, z 30-80 mm; edge on the beam axis) at its
+    """Insert phantom (bone half-space x > 0, z 30-80 mm; edge on the beam axis) at its
     own 1 mm voxels: every voxel above 1 % of D_max (which includes the lateral profiles at
     every depth), GPU 16 x 640 000 against the oracle 16 x 62 500; the bone side stops
     earlier on both sides; distal R80/R90 of the whole beam's energy depth curve."""
@@ -148,7 +148,7 @@ def test_insert150_per_voxel_parity(sde_gpu, oracle_lib):
 
 
 def test_plan2000_per_voxel_parity(sde_gpu, oracle_lib):
-    """configs[3]: the 2000-spot plan on the 200 x 200 x 300 sphere phantom at its own 1 mm
+    """The 2000-spot plan on the 200 x 200 x 300 sphere phantom at its own 1 mm
     voxels, all spots in one launch: every voxel above 1 % of D_max, GPU 16 x 640 000
     histories against the oracle 16 x 200 000 (each spot's count scaled in proportion: ~100
     histories per spot and batch, so the oracle's batch spread, not the GPU's, sets the
@@ -364,7 +364,7 @@ def test_sobp_plateau_in_water(sde_gpu):
 
 
 def test_insert150_gamma_at_one_million_protons(sde_gpu, oracle_lib):
-    """configs[2]: 3D gamma (2 %/0.5 mm, local, 1 % threshold) of the GPU dose against the
+    """Insert phantom: 3D gamma (2 %/0.5 mm, local, 1 % threshold) of the GPU dose against the
     oracle at 10^6 protons.  Both doses are noisy, so the pass rate is compared with the pass
     rate of the oracle against itself (another seed): equal distributions give equal rates."""
     wl = insert150(1_000_000)
