@@ -310,6 +310,29 @@ int sde_conv3d_wgrad(const void* d_x, const void* d_dy, float* d_dw, int batch, 
 /* d_wd[ci][26 - tap][co] = d_w[co][tap][ci] (BF16): weights of the data-gradient convolution. */
 int sde_conv3d_flip_weights(const void* d_w, void* d_wd, int Cin, int Cout, void* stream);
 
+/* Host-only inspection of the work decompositions the two convolution kernels launch
+ * (no CUDA call: usable without a GPU, e.g. to check a shape's shared-memory and
+ * tensor-memory layout before running it).
+ * sde_conv3d_plan: the plan of sde_conv3d_forward for this shape, as 17 ints in the
+ * order Ty, tiles, rowtile, fold, nyb, P, Yb, Cp, nsplit, plane, w_off, wres, stage,
+ * nacc, xch, tcols, items (rows per work item, 128-position M tiles per item, row
+ * tiles, x-tap fold, row blocks, brick row pitch W + 2, brick rows Ty + 2, output
+ * channels per part, parts, bytes between the two 8-channel planes of a chunk,
+ * weight offset in a stage, resident weights, bytes per stage, accumulators,
+ * offset of the fold's exchange buffer, tensor-memory columns, work items), and
+ * its dynamic shared memory in bytes.
+ * sde_conv3d_wgrad_plan: the plan of sde_conv3d_wgrad on a GPU with `sms`
+ * multiprocessors, as 14 ints: Ty, nyb, P, Yb, Nc, ntap, ngroups, kst, plane_dy,
+ * plane_x, x_off, stage, items, G (input channels and taps per pass, tap groups,
+ * 16-position K steps per item, plane pitches of the output-gradient rows and of
+ * the input brick, brick offset in a stage, CTAs per pass), and its dynamic shared
+ * memory.  Both fill min(n_fields, count) ints; SDE_EINVAL for a shape the
+ * convolution rejects or has no plan for. */
+int sde_conv3d_plan(int batch, int D, int H, int W, int Cin, int Cout, int32_t* fields, int n_fields,
+                    uint64_t* smem_bytes);
+int sde_conv3d_wgrad_plan(int batch, int D, int H, int W, int Cin, int Cout, int sms, int32_t* fields,
+                          int n_fields, uint64_t* smem_bytes);
+
 /* Wait for the stream and report (and clear) a timed-out tensor-core wait of any
  * denoiser kernel since the last call: SDE_EDEVICE, else SDE_OK. */
 int sde_denoise_status(void* stream);

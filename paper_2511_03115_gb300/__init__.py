@@ -34,7 +34,7 @@ EXPORTED = [
     "sde_conv3d_flip_weights", "sde_denoise_status", "sde_denoiser_create", "sde_denoiser_destroy",
     "sde_denoiser_set_stream", "sde_denoiser_num_params", "sde_denoiser_infer", "sde_denoiser_train_step",
     "sde_denoiser_gradients", "sde_denoiser_get_params", "sde_denoiser_set_params", "sde_gamma3d",
-    "sde_scale_f32",
+    "sde_scale_f32", "sde_conv3d_plan", "sde_conv3d_wgrad_plan",
 ]
 
 
@@ -156,6 +156,8 @@ def lib():
         L.sde_conv3d_forward.argtypes = [vp, i, i, i, i, i, vp, vp, i, vp, i, i, i, i, vp]
         L.sde_conv3d_wgrad.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp]
         L.sde_conv3d_flip_weights.argtypes = [vp, vp, i, i, vp]
+        L.sde_conv3d_plan.argtypes = [i, i, i, i, i, i, C.POINTER(C.c_int32), i, C.POINTER(u64)]
+        L.sde_conv3d_wgrad_plan.argtypes = [i, i, i, i, i, i, i, C.POINTER(C.c_int32), i, C.POINTER(u64)]
         L.sde_denoise_status.argtypes = [vp]
         L.sde_denoiser_create.argtypes = [C.POINTER(vp), i, i, i, i, u64]
         L.sde_denoiser_destroy.argtypes = [vp]
@@ -426,6 +428,30 @@ def conv3d(x, w, bias=None, relu=False, y=None, y_coffset=0, fp32=False, stream=
                                     None if bias is None else bias.data_ptr(), Cout, y.data_ptr(),
                                     cstride, y_coffset, int(fp32), int(relu), _sp(stream)))
     return y
+
+
+CONV_PLAN_FIELDS = ("Ty", "tiles", "rowtile", "fold", "nyb", "P", "Yb", "Cp", "nsplit", "plane", "w_off", "wres",
+                    "stage", "nacc", "xch", "tcols", "items")
+WGRAD_PLAN_FIELDS = ("Ty", "nyb", "P", "Yb", "Nc", "ntap", "ngroups", "kst", "plane_dy", "plane_x", "x_off", "stage",
+                     "items", "G")
+
+
+def conv3d_plan(batch, D, H, W, Cin, Cout):
+    """Work decomposition sde_conv3d_forward launches for this shape (host only, no GPU):
+    a dict of the plan's fields plus ``smem`` (dynamic shared memory in bytes)."""
+    f = (C.c_int32 * len(CONV_PLAN_FIELDS))()
+    sm = C.c_uint64()
+    _check(lib().sde_conv3d_plan(batch, D, H, W, Cin, Cout, f, len(f), C.byref(sm)))
+    return dict(zip(CONV_PLAN_FIELDS, list(f)), smem=sm.value)
+
+
+def conv3d_wgrad_plan(batch, D, H, W, Cin, Cout, sms=152):
+    """Work decomposition sde_conv3d_wgrad launches on a GPU with ``sms`` multiprocessors
+    (host only, no GPU): a dict of the plan's fields plus ``smem``."""
+    f = (C.c_int32 * len(WGRAD_PLAN_FIELDS))()
+    sm = C.c_uint64()
+    _check(lib().sde_conv3d_wgrad_plan(batch, D, H, W, Cin, Cout, sms, f, len(f), C.byref(sm)))
+    return dict(zip(WGRAD_PLAN_FIELDS, list(f)), smem=sm.value)
 
 
 def conv3d_wgrad(x, dy, dw, stream=None):

@@ -1124,3 +1124,44 @@ extern "C" int sde_conv3d_flip_weights(const void* d_w, void* d_wd, int Cin, int
 }
 
 extern "C" int sde_denoise_status(void* stream) { return denoise_check_status((cudaStream_t)stream); }
+
+// Host-only views of the two plans (no CUDA call).
+extern "C" int sde_conv3d_plan(int batch, int D, int H, int W, int Cin, int Cout, int32_t* fields, int n_fields,
+                               uint64_t* smem_bytes) {
+    BrickPlan bp{};
+    size_t smem = 0;
+    if (!conv_shape_ok(D, H, W, Cin, Cout, batch) || n_fields < 0 || (n_fields > 0 && !fields) ||
+        !brick_plan(D, H, W, Cin, Cout, batch, &bp, &smem)) {
+        set_last_error("sde_conv3d_plan: shape rejected by the convolution or without a plan");
+        return SDE_EINVAL;
+    }
+    const int32_t v[17] = {bp.Ty,    bp.tiles, bp.rowtile, bp.fold,  bp.nyb, bp.P,    bp.Yb,  bp.Cp,   bp.nsplit,
+                           bp.plane, bp.w_off, bp.wres,    bp.stage, bp.nacc, bp.xch, bp.tcols, bp.items};
+    for (int i = 0; i < n_fields && i < 17; ++i) fields[i] = v[i];
+    if (smem_bytes) *smem_bytes = smem;
+    return SDE_OK;
+}
+
+extern "C" int sde_conv3d_wgrad_plan(int batch, int D, int H, int W, int Cin, int Cout, int sms, int32_t* fields,
+                                     int n_fields, uint64_t* smem_bytes) {
+    WgradArgs a{};
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.Cin = Cin;
+    a.Cout = Cout;
+    a.nvox = D * H * W;
+    a.batch = batch;
+    WgradPlan wp{};
+    size_t smem = 0;
+    if (!conv_shape_ok(D, H, W, Cin, Cout, batch) || Cout > 128 || sms < 1 || n_fields < 0 ||
+        (n_fields > 0 && !fields) || !wgrad_plan(a, sms, &wp, &smem)) {
+        set_last_error("sde_conv3d_wgrad_plan: shape rejected by the weight gradient or without a plan");
+        return SDE_EINVAL;
+    }
+    const int32_t v[14] = {wp.Ty,       wp.nyb,     wp.P,     wp.Yb,    wp.Nc,    wp.ntap,  wp.ngroups,
+                           wp.kst,      wp.plane_dy, wp.plane_x, wp.x_off, wp.stage, wp.items, wp.G};
+    for (int i = 0; i < n_fields && i < 14; ++i) fields[i] = v[i];
+    if (smem_bytes) *smem_bytes = smem;
+    return SDE_OK;
+}
