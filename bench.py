@@ -71,6 +71,20 @@ TRANSPORT_ATOMICS = {
                          "(profiles/k_transport_plan2000.md)"},
 }
 
+# Instruction issue of the transport kernel (ncu --set full on the plan's first 2e6 histories,
+# same command as the L2 reduction figures); reported only while the sources match its hash.
+TRANSPORT_ISSUE = {
+    "plan2000": {"src": "2c263b682767634b", "issue_active_pct": 79.81, "lanes_per_warp_instruction": 24.86,
+                 "warp_instructions": 7_517_505_206, "euler_steps": 525_487_490,
+                 "pipe_pct": {"alu": 47.96, "fma": 41.16, "fp64": 25.43, "xu_cycles": 40.29, "lsu": 5.87},
+                 "eligible_warps_per_issue": 3.15,
+                 "note": "ncu smsp__issue_active (of active cycles), smsp__thread_inst_executed_per_inst_executed, "
+                         "smsp__inst_executed.sum, sm__pipe_*_cycles_active, smsp__average_warps_issue_stalled_"
+                         "not_selected_per_issue_active of k_transport in `bench.py --histories 2000000 --no-autotune "
+                         "--steps 1 --warmup 1 --e2e-steps 0 --no-denoiser --no-cpu-baseline --no-secondary` "
+                         "(profiles/k_transport_plan2000.md)"},
+}
+
 WORKLOADS = {
     "plan2000": ("plan2000: 2000 spots on a 5 mm grid, E U(70,200) MeV, lognormal(0,0.7) weights, "
                  "1e8 protons per GPU, 200x200x300 mm at 1 mm, water + 30 random spheres (tissue/bone, "
@@ -587,6 +601,14 @@ def main():
                 "red_sectors_per_euler_step": atom_rec["red_sectors"] / atom_rec["euler_steps"],
                 "note": atom_rec["note"], "transport_src": src}
                if atom_rec and atom_rec["src"] == src else None)
+    iss_rec = TRANSPORT_ISSUE.get(args.workload)
+    issue = ({"issue_active_pct": iss_rec["issue_active_pct"],
+              "lanes_per_warp_instruction": iss_rec["lanes_per_warp_instruction"],
+              "lane_instructions_per_euler_step":
+                  iss_rec["warp_instructions"] * iss_rec["lanes_per_warp_instruction"] / iss_rec["euler_steps"],
+              "pipe_pct": iss_rec["pipe_pct"], "eligible_warps_per_issue": iss_rec["eligible_warps_per_issue"],
+              "note": iss_rec["note"], "transport_src": src}
+             if iss_rec and iss_rec["src"] == src else None)
     line = {
         "metric": METRIC,
         "value": value,
@@ -625,6 +647,7 @@ def main():
                      "peak_note": f"{sms} SMs (device attribute) x {LANE_OPS_PER_CLK_PER_SM} lane-ops/clk x "
                                   f"{clk_mhz:.0f} MHz (measured max SM clock)"},
         "tally_atomics": atomics,
+        "transport_issue": issue,
         "clocks": clocks,
         "balance_exact": bal["incident"] == bal["deposited"] + bal["escaped"] + bal["removed"],
         "combine": combine,
